@@ -1,0 +1,83 @@
+"""Per-node sampled-row ID over a tree (oracle side).
+
+Test infrastructure (see ``oracle/__init__``).
+
+For every node at level >= 2 (each node's own far field, §4.1 steps 2-3 with
+x_c = the node centroid and xi = 1): sample s far-field rows uniformly
+(§2.2), evaluate K'(rows, node sources), compute its ID at relative
+tolerance tol (§2.1.3, App. A.1).
+
+Reading of "s = 2 x rank" (the rank is only known after the QR): start at
+s = s0 and run the pivoted QR in tolerance mode for at most s/2 steps; if the
+tolerance is not met, double s and start again. The sampler is prefix
+consistent, so the first s rows are kept. When every far-field row is already
+in the sample the QR may run to min(s, n) steps; the rank never exceeds
+r_cap = s_max / 2. A node that cannot meet the tolerance within those limits
+keeps its last ID with status TOL_NOT_REACHED.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .interp import interpolative_decomposition
+from .kernels import Kernel, kernel_block
+from .sampling import far_field_mask, sample_uniform_from_mask
+
+STATUS_OK = 0
+STATUS_FARFIELD_EMPTY = 5
+STATUS_TOL_NOT_REACHED = 7
+
+
+@dataclass
+class NodeResult:
+    node: int
+    s: int                  # rows actually sampled
+    rows: np.ndarray        # sampled positions (tree order)
+    rank: int
+    skel_perm: np.ndarray   # node-local column indices
+    T: np.ndarray
+    r22_rel: float
+    log_scale: float
+    far_count: int
+    status: int
+    attempts: list = field(default_factory=list)   # s values tried
+
+
+def rank_cap(s_eff: int, n: int, all_rows: bool, r_cap: int) -> int:
+    return min(n, r_cap, s_eff if all_rows else s_eff // 2)
+
+
+def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048, xi=1.0):
+    b, c = int(tree.begin[node]), int(tree.count[node])
+    far = far_field_mask(Xp, tree.centroid[node], tree.radius[node], xi, b, b + c)
+    far_count = int(far.sum())
+    X_node = Xp[b:b + c]
+    r_cap = s_max // 2
+    s = s0
+    tried = []
+    while True:
+        tried.append(s)
+        rows = sample_uniform_from_mask(far, s, seed, node)
+        if rows.size == 0:
+            return NodeResult(node, 0, rows, 0, np.arange(c), np.zeros((0, c)), 0.0, 0.0,
+                              far_count, STATUS_FARFIELD_EMPTY, tried)
+        all_rows = rows.size >= far_count
+        K, log_scale = kernel_block(kernel, Xp[rows], X_node)
+        cap = rank_cap(rows.size, c, all_rows, r_cap)
+        idr = interpolative_decomposition(K, cap, tol)
+        done = idr["r22_rel"] <= tol
+        if done or all_rows or 2 * s > s_max:
+            st = STATUS_OK if done else STATUS_TOL_NOT_REACHED
+            return NodeResult(node, int(rows.size), rows, idr["rank"], idr["skel_perm"], idr["T"],
+                              idr["r22_rel"], log_scale, far_count, st, tried)
+        s *= 2
+
+
+def compress_tree(Xp, tree, kernel: Kernel, tol, seed=0, min_level=2, s0=128, s_max=2048,
+                  nodes=None):
+    """Compress every node at level >= min_level (or just ``nodes``)."""
+    if nodes is None:
+        nodes = [i for i in range(tree.n_nodes) if tree.level[i] >= min_level]
+    return [compress_node(Xp, tree, i, kernel, tol, seed, s0, s_max) for i in nodes]
