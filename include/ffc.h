@@ -1,0 +1,262 @@
+/*
+ * ffc.h - C ABI of libffc: far-field compression by sampled-row interpolative
+ * decomposition (March & Biros, "Far-field compression for fast kernel
+ * summation methods in high dimensions").
+ *
+ * Problem statement (§1, eq. e:sum): u_i = sum_j K(y_i, x_j) q_j, u = K q with
+ * rows of K indexed by targets y_i and columns by sources x_j. The outgoing
+ * representation of a source set is an interpolative decomposition K ~ C P
+ * (§2.1.3): C = K(:, J) for a skeleton J of r source columns and P (r x n)
+ * containing I_r. The method (§2.2) computes the ID of a sampled block
+ * K'(rows, :) of s far-field target rows instead of the whole m x n block.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers owned by the caller; pointers
+ *    named *_host are host pointers owned by the caller. No entry point keeps
+ *    a pointer after it returns, except where stated (ffc_tree_result).
+ *  - Points are row-major (point i, coordinate k at [i*d + k]); kernel blocks
+ *    are column-major with a leading dimension (entry (i, j) at [i + j*ld]).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    enqueued on it. Calls that return device-computed scalars through *_host
+ *    pointers, or a device-detected status, synchronise that stream before
+ *    they return; this is stated per call.
+ *  - Every call returns an ffc_status. Arguments are validated before any
+ *    launch; on FFC_E_INVALID nothing was enqueued. Nothing is thrown across
+ *    the ABI. ffc_last_error() gives a one-line message for the calling thread.
+ *  - Device waits inside the library are bounded: a wait that runs out sets
+ *    FFC_E_TIMEOUT instead of hanging the GPU.
+ */
+#ifndef FFC_H
+#define FFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFC_OK = 0,
+  FFC_E_INVALID = 1,            /* bad argument; nothing enqueued */
+  FFC_E_NOMEM = 2,              /* device allocation failed */
+  FFC_E_CUDA = 3,               /* a CUDA runtime call failed */
+  FFC_E_TIMEOUT = 4,            /* a bounded device wait gave up */
+  FFC_E_FARFIELD_TOO_SMALL = 5, /* soft: fewer far-field rows than requested; outputs valid */
+  FFC_E_SINGULAR = 6,           /* Laplace kernel at coincident points */
+  FFC_E_TOL_NOT_REACHED = 7     /* soft: tolerance not met within the rank cap; outputs valid */
+} ffc_status;
+
+typedef enum { FFC_GAUSSIAN = 0, FFC_LAPLACE = 1, FFC_POLYNOMIAL = 2 } ffc_kernel_kind;
+typedef enum { FFC_F64 = 0, FFC_F32 = 1 } ffc_dtype;
+/* FFC_FP64: every step in FP64. FFC_MIXED: reduced-precision block and QR
+ * updates with FP64 column norms and FP64 triangular solve. */
+typedef enum { FFC_FP64 = 0, FFC_MIXED = 1 } ffc_precision;
+
+/*
+ * Kernel function (§4.2-§4.4):
+ *   FFC_GAUSSIAN   K(y,x) = exp(-||x-y||^2 / (2 h^2))        (h > 0)
+ *   FFC_LAPLACE    K(y,x) = ||x-y||^(2-d), d != 2 (d = 2 is rejected)
+ *   FFC_POLYNOMIAL K(y,x) = (x.y / h + c)^p                  (h != 0, p >= 1)
+ * Laplace blocks are returned divided by their largest entry: the call also
+ * returns log_scale with K_true = exp(log_scale) * K_returned. A scalar
+ * factor changes neither the ID nor any relative error.
+ */
+typedef struct {
+  int32_t kind;   /* ffc_kernel_kind */
+  int32_t p;      /* polynomial degree */
+  double h;       /* Gaussian bandwidth / polynomial scale */
+  double c;       /* polynomial constant */
+} ffc_kernel;
+
+/* One-line message describing the last failure on the calling thread. */
+const char* ffc_last_error(void);
+
+/* Library version string. */
+const char* ffc_version(void);
+
+/*
+ * ffc_far_field - list the far field of a source set (§4.1, setup step 3):
+ *   T = { j in [0, M) \ [ex_begin, ex_end) : ||Y_j - x_c|| >= xi * radius }.
+ * Y_dev: M x d points (dtype). x_c_dev: d doubles, or NULL for "no distance
+ * test" (every non-excluded candidate is far). idx_dev: receives the far
+ * indices in ascending order (capacity M int64). count_host: |T|.
+ * Synchronises `stream`.
+ */
+ffc_status ffc_far_field(const void* Y_dev, int32_t dtype, int64_t M, int32_t d,
+                         const double* x_c_dev, double radius, double xi,
+                         int64_t ex_begin, int64_t ex_end,
+                         int64_t* idx_dev, int64_t* count_host, void* stream);
+
+/*
+ * ffc_sample_rows - uniform sample of s far-field rows without replacement
+ * (§2.2; §4.1.3 "Uniform sampling"). Far field as in ffc_far_field.
+ * Randomness: draw t of the stream (seed, stream_id) is word t mod 4 of
+ * Philox4x64-10(counter = (t/4, stream_id, 0, 0), key = (seed, 0)).
+ * Phase A: for t < 64 s, candidate j = floor(w_t M / 2^64) is accepted if it
+ * is far and new, until s rows are accepted (rows in acceptance order, so a
+ * size-s sample is a prefix of the size-2s sample). Phase B, only if phase A
+ * ran out: the not-yet-taken far rows T' in ascending order are appended
+ * whole if |T'| <= s - k, else picked by a partial Fisher-Yates shuffle with
+ * draws t = 64 s, 64 s + 1, ...
+ * rows_dev: capacity s int64. s_out_host: rows written, min(s, |T|).
+ * far_count_host (may be NULL): |T|. Requires M <= 1,500,000.
+ * Returns FFC_E_FARFIELD_TOO_SMALL (soft) when |T| < s. Synchronises `stream`.
+ */
+ffc_status ffc_sample_rows(const void* Y_dev, int32_t dtype, int64_t M, int32_t d,
+                           const double* x_c_dev, double radius, double xi,
+                           int64_t ex_begin, int64_t ex_end,
+                           int64_t s, uint64_t seed, uint64_t stream_id,
+                           int64_t* rows_dev, int64_t* s_out_host, int64_t* far_count_host,
+                           void* stream);
+
+/*
+ * ffc_eval_block - evaluate the sampled block K'_ij = K(Y[rows_i], X_j)
+ * (§2.2: the s x n matrix K~ of the sampled targets against the sources).
+ * Y_dev: candidate targets (M x d, dtype); rows_dev: s int64 indices into Y.
+ * X_dev: n x d sources (dtype). K_dev: column-major s x n, leading dim
+ * ldk >= s, double for FFC_FP64 and float for FFC_MIXED. center_dev: d
+ * doubles (the source centre) or NULL; FFC_MIXED forms distances of centred
+ * coordinates. log_scale_host: ln of the factor removed from a Laplace block
+ * (0 for the other kernels). Synchronises `stream` (Laplace: to return the
+ * scale). Returns FFC_E_SINGULAR for a Laplace block with a zero distance.
+ */
+ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype,
+                          const int64_t* rows_dev, int64_t s,
+                          const void* X_dev, int64_t n, int32_t d,
+                          const double* center_dev, int32_t precision,
+                          void* K_dev, int64_t ldk, double* log_scale_host, void* stream);
+
+/*
+ * ffc_id - interpolative decomposition of K' (§2.1.3, Appendix A.1) by
+ * Businger-Golub column-pivoted Householder QR: at step k the pivot is the
+ * remaining column of largest residual norm (lowest index on ties); the
+ * reflector follows LAPACK dlarfg (beta = -sign(alpha) ||x||, sign(0) = +).
+ * Then T = R11^-1 R12 by back-substitution.
+ * K_dev: s x n column-major (ld ldk; double for FFC_FP64, float for
+ * FFC_MIXED); OVERWRITTEN. Stop rule: tol > 0 -> the smallest r <= r_max
+ * with ||R22||_F <= tol ||K'||_F; tol <= 0 -> r = r_max (earlier only if the
+ * remaining columns are exactly zero).
+ * Outputs: skel_perm_dev (n int32): [0, r) the skeleton in pivot order,
+ * [r, n) the other columns ascending. T_dev (double, column-major, ld ldt >=
+ * max(r_max, 1), capacity ldt * n): T(:, c) expresses column skel_perm[r + c]
+ * in the skeleton columns, so P = [I_r T] Pi^T. rank_host: r.
+ * r22_rel_host: ||R22||_F / ||K'||_F. Synchronises `stream`.
+ * Returns FFC_E_TOL_NOT_REACHED (soft) if tol > 0 was not met at r_max.
+ */
+ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precision,
+                  int64_t r_max, double tol,
+                  int32_t* skel_perm_dev, double* T_dev, int64_t ldt,
+                  int64_t* rank_host, double* r22_rel_host, void* stream);
+
+/*
+ * ffc_id_error - relative Frobenius error of an ID on a full block
+ * (§4.1.3, step 4): ||K - K(:, J) P||_F / ||K||_F with K_ij = K(Y[rows_i], X_j)
+ * over m target rows (rows_dev NULL = rows 0..m-1 of Y). skel_perm_dev, T_dev,
+ * ldt, r: as returned by ffc_id for these n sources. The block is streamed
+ * in tiles and never stored; all arithmetic is FP64. err_host: the error.
+ * Synchronises `stream`.
+ */
+ffc_status ffc_id_error(ffc_kernel kernel, const void* Y_dev, int32_t dtype,
+                        const int64_t* rows_dev, int64_t m,
+                        const void* X_dev, int64_t n, int32_t d,
+                        const int32_t* skel_perm_dev, const double* T_dev, int64_t ldt, int64_t r,
+                        double* err_host, void* stream);
+
+/* ----------------------------- trees ---------------------------------- */
+
+/*
+ * Binary PCA tree (the space-partitioning tree of §2 that defines each
+ * node's far field). Depth D = smallest D with ceil(N / 2^D) <= leaf_size;
+ * 2^(D+1) - 1 nodes in heap order (children of i: 2i+1, 2i+2); a node holds
+ * positions [begin, begin + count) of `perm`, its left child the first
+ * floor(count / 2). Each node's points are ordered by (projection on the
+ * principal direction of its centred points, original index); the principal
+ * direction comes from 32 power iterations from (1,..,1)/sqrt(d), signed so
+ * that its largest-magnitude component is positive. Node geometry (§4.1):
+ * centroid x_c = mean, radius = max ||x - x_c||.
+ */
+int32_t ffc_tree_depth(int64_t N, int64_t leaf_size);
+
+/*
+ * ffc_build_tree - build the tree above on the GPU.
+ * points_dev: N x d (dtype). perm_dev: N int64 (position -> point index).
+ * begin_dev, count_dev: n_nodes int64. centroid_dev: n_nodes x d doubles.
+ * radius_dev: n_nodes doubles; n_nodes = 2^(depth+1) - 1.
+ * Synchronises `stream`.
+ */
+ffc_status ffc_build_tree(const void* points_dev, int32_t dtype, int64_t N, int32_t d,
+                          int64_t leaf_size, int64_t* perm_dev, int64_t* begin_dev,
+                          int64_t* count_dev, double* centroid_dev, double* radius_dev,
+                          void* stream);
+
+/* Tree as consumed by ffc_compress_tree (all device pointers). */
+typedef struct {
+  int32_t depth;
+  int64_t n_nodes;
+  const int64_t* begin_dev;
+  const int64_t* count_dev;
+  const double* centroid_dev;
+  const double* radius_dev;
+} ffc_tree;
+
+typedef struct {
+  ffc_kernel kernel;
+  int32_t precision;   /* ffc_precision */
+  int32_t min_level;   /* compress nodes at levels >= min_level (2) */
+  int32_t s0;          /* first sample size (128) */
+  int32_t s_max;       /* largest sample size (2048); the rank cap is s_max / 2 */
+  double tol;          /* relative tolerance on ||R22||_F / ||K'||_F (1e-6) */
+  double xi;           /* far-field separation (1.0) */
+  uint64_t seed;       /* sampling seed; the stream id of a node is its heap id */
+} ffc_params;
+
+/*
+ * Compression of every node at level >= min_level. For a node with
+ * centroid x_c, radius rho and positions [b, b + n): far field = positions
+ * outside [b, b + n) at distance >= xi rho from x_c; s = s0; sample s rows
+ * (ffc_sample_rows with stream_id = node id), evaluate K' (s x n), run the
+ * pivoted QR in tolerance mode for at most s/2 steps (min(s, n) when the
+ * sample already holds the whole far field); if the tolerance is not met,
+ * double s (the sample is prefix consistent) while s <= s_max; else keep the
+ * last ID with status FFC_E_TOL_NOT_REACHED.
+ */
+typedef struct ffc_tree_result ffc_tree_result;   /* opaque; owns device memory */
+
+/*
+ * ffc_compress_tree - run the compression above on points_perm_dev (N x d,
+ * rows in tree order, i.e. points[perm]). *result: NULL on the first call
+ * (allocated here and returned), or a result from an earlier call on the
+ * same tree shape and params, whose memory is reused. Synchronises `stream`
+ * once per sample-size round (at most log2(s_max / s0) + 1 rounds).
+ */
+ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t N, int32_t d,
+                             const ffc_tree* tree, const ffc_params* params,
+                             ffc_tree_result** result, void* stream);
+
+/* Per-node outputs, in the order of the compressed nodes (increasing heap id). */
+typedef struct {
+  int64_t n_out;                 /* number of compressed nodes */
+  int32_t rounds;                /* sample-size rounds the last call ran */
+  const int32_t* node_dev;       /* heap id */
+  const int32_t* rank_dev;       /* r */
+  const int32_t* s_dev;          /* rows sampled */
+  const int32_t* status_dev;     /* ffc_status of the node */
+  const double* r22_rel_dev;     /* ||R22||_F / ||K'||_F */
+  const double* log_scale_dev;   /* Laplace block scale (0 otherwise) */
+  const int64_t* far_count_dev;  /* |T| */
+  const int64_t* rows_off_dev;   /* node i's rows start at rows_dev[rows_off[i]] */
+  const int64_t* rows_dev;       /* sampled positions (tree order), s entries per node */
+  const int64_t* skel_off_dev;   /* node i's skel_perm starts at skel_dev[skel_off[i]] (n entries) */
+  const int32_t* skel_dev;       /* node-local column indices, as ffc_id */
+  const int64_t* T_off_dev;      /* node i's T starts at T_dev[T_off[i]], ld = rank */
+  const double* T_dev;
+} ffc_tree_view;
+
+ffc_status ffc_tree_result_view(const ffc_tree_result* result, ffc_tree_view* view);
+void ffc_tree_result_free(ffc_tree_result* result);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFC_H */

@@ -10,8 +10,9 @@ tolerance tol (§2.1.3, App. A.1).
 Reading of "s = 2 x rank" (the rank is only known after the QR): start at
 s = s0 and run the pivoted QR in tolerance mode for at most s/2 steps; if the
 tolerance is not met, double s and start again. The sampler is prefix
-consistent, so the first s rows are kept. When every far-field row is already
-in the sample the QR may run to min(s, n) steps; the rank never exceeds
+consistent, so the first s rows are kept. When the sample already holds the
+whole far field (the sampler returned fewer than s rows) the QR may run to
+min(s, n) steps; the rank never exceeds
 r_cap = s_max / 2. A node that cannot meet the tolerance within those limits
 keeps its last ID with status TOL_NOT_REACHED.
 """
@@ -63,7 +64,10 @@ def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048,
         if rows.size == 0:
             return NodeResult(node, 0, rows, 0, np.arange(c), np.zeros((0, c)), 0.0, 0.0,
                               far_count, STATUS_FARFIELD_EMPTY, tried)
-        all_rows = rows.size >= far_count
+        # the whole far field is in the sample exactly when the sampler came
+        # back with fewer rows than asked for (|T| < s); when |T| == s the
+        # next doubling finds that out
+        all_rows = rows.size < s
         K, log_scale = kernel_block(kernel, Xp[rows], X_node)
         cap = rank_cap(rows.size, c, all_rows, r_cap)
         idr = interpolative_decomposition(K, cap, tol)

@@ -1,0 +1,169 @@
+// Internal declarations shared by libffc's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ffc.h"
+
+namespace ffc {
+
+// ----------------------------------------------------------------------------
+// error state (thread-local message, see ffc_last_error)
+void set_error(const char* fmt, ...);
+ffc_status cuda_fail(cudaError_t e, const char* what);
+
+#define FFC_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::ffc::cuda_fail(e_, #call);           \
+  } while (0)
+
+#define FFC_REQUIRE(cond, ...)                                           \
+  do {                                                                   \
+    if (!(cond)) {                                                       \
+      ::ffc::set_error(__VA_ARGS__);                                     \
+      return FFC_E_INVALID;                                              \
+    }                                                                    \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ----------------------------------------------------------------------------
+// device helpers
+
+// Philox4x64-10 (Salmon et al., SC'11): counter (c0..c3), key (k0, k1).
+struct u64x4 { uint64_t x[4]; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                               uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  u64x4 o; o.x[0] = c0; o.x[1] = c1; o.x[2] = c2; o.x[3] = c3;
+  return o;
+}
+
+// Draw t of stream (seed, stream_id, domain): word t%4 of block t/4.
+__device__ __forceinline__ uint64_t philox_draw(uint64_t seed, uint64_t stream_id, uint64_t domain,
+                                                uint64_t t) {
+  u64x4 b = philox4x64_10(t >> 2, stream_id, domain, 0, seed, 0);
+  uint32_t w = (uint32_t)(t & 3);
+  return w == 0 ? b.x[0] : (w == 1 ? b.x[1] : (w == 2 ? b.x[2] : b.x[3]));
+}
+
+constexpr uint64_t DOMAIN_UNIFORM_ROWS = 0;
+constexpr uint64_t DOMAIN_WEIGHTED_POOL = 1;
+constexpr uint64_t DOMAIN_WEIGHTED_KEYS = 2;
+constexpr int ATTEMPT_FACTOR = 64;
+constexpr int SAMPLE_MAX_GRID = 2048;   // sampler CTAs; one scratch slice of M_max each
+
+template <typename TP>
+__device__ __forceinline__ double ld_point(const TP* p) { return (double)__ldg(p); }
+
+// Bounded spin limit for waits on other CTAs (about a second or more).
+constexpr long long SPIN_LIMIT = 20000000ll;
+
+// ----------------------------------------------------------------------------
+// work items (host-built tables, copied to the device)
+
+struct SampleItem {
+  int64_t M;            // candidates (rows of Y)
+  int64_t ex_begin, ex_end;
+  const double* x_c;    // NULL: no distance test
+  double thr2;          // (xi * radius)^2, used when radius == NULL
+  const double* radius; // device radius (tree nodes) or NULL
+  double xi;
+  int64_t s;            // requested rows
+  uint64_t stream_id;
+  int64_t* rows;        // capacity s
+};
+
+struct EvalItem {
+  const int64_t* rows;  // s indices into Y
+  int64_t s;
+  int64_t x_begin;      // first source row in X
+  int64_t n;
+  void* K;              // column-major s x n
+  int64_t ldk;
+  const double* center; // d doubles or NULL
+  int64_t tile_begin;   // prefix of tiles over items
+  int64_t row_tiles;    // row tiles of the nominal s (tiles past the actual s are skipped)
+};
+
+struct CpqrItem {
+  void* A;              // s x n column-major, ld lda (double or float)
+  int64_t lda;
+  int32_t s, n;
+  int32_t r_max;        // step cap
+  int32_t pad0;
+  double tol;           // <= 0: fixed rank
+  int32_t* piv;         // r_max
+  double* beta;         // r_max
+  double* vn1;          // n  current residual norms
+  double* vn2;          // n  reference norms (downdating safeguard)
+  uint8_t* selected;    // n
+  void* slots;          // 2 x g Slot
+  unsigned int* barrier;
+  int32_t* rank_out;
+  double* r22_out;      // ||R22||_F / ||K'||_F
+  int32_t* status_out;
+};
+
+struct CtaAssign { int32_t item, rank, g, pad; };
+
+struct Slot { double best; double sum; int32_t col; int32_t pad; };
+
+struct TrsmItem {
+  const void* A; int64_t lda;
+  int32_t n, pad0;
+  const int32_t* rank;  // device scalar
+  const int32_t* piv;
+  const double* beta;
+  const uint8_t* selected;
+  int32_t* skel_perm;   // n
+  double* R11;          // r_cap x r_cap workspace (row-major, ld r)
+  double* T;            // output
+  int64_t ldt;          // <= 0: ld = rank (packed)
+  int32_t r_cap, pad1;
+  int64_t tile_begin;   // prefix of 8-column tiles over items
+};
+
+// ----------------------------------------------------------------------------
+// launchers (implemented in the .cu files; all enqueue on `st`)
+
+ffc_status launch_far_field(const void* Y, int dtype, int64_t M, int d, const double* x_c, double thr2,
+                            int64_t ex_begin, int64_t ex_end, int64_t* idx, int64_t* count_dev,
+                            cudaStream_t st);
+ffc_status launch_sample(const void* Y, int dtype, int d, const SampleItem* items_dev, int n_items,
+                         int64_t M_max, int64_t s_max, uint64_t seed, int64_t* s_out, int64_t* far_count,
+                         int32_t* status, int32_t* scratch, cudaStream_t st);
+ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
+                       const EvalItem* items_dev, int n_items, int64_t total_tiles,
+                       double* min_d2 /* n_items, Laplace */, double* log_scale /* n_items */,
+                       int32_t* status /* n_items */, cudaStream_t st);
+ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
+                       int s_max, cudaStream_t st);
+int cpqr_max_ctas(int precision, int s_max);
+ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,
+                               int r_cap_max, cudaStream_t st);
+ffc_status launch_id_error(ffc_kernel k, const void* Y, int dtype, const int64_t* rows, int64_t m,
+                           const void* X, int64_t n, int d, const int32_t* skel, const double* T,
+                           int64_t ldt, int64_t r, double* partial /* workspace */, int64_t n_partial,
+                           double* min_d2_dev, double* out_host_num, double* out_host_den, cudaStream_t st);
+ffc_status launch_build_tree(const void* points, int dtype, int64_t N, int d, int depth, int64_t* perm,
+                             const int64_t* begin_host, const int64_t* count_host, const int64_t* begin_dev,
+                             const int64_t* count_dev, double* centroid, double* radius, cudaStream_t st);
+
+// host helpers
+int sm_count();
+void node_layout(int64_t N, int depth, int64_t* begin, int64_t* count, int32_t* level);
+
+}  // namespace ffc

@@ -1,0 +1,378 @@
+// ffc_compress_tree: sampled-row ID of every tree node at level >= min_level.
+//
+// For each node (far field of the node's centroid and radius, §4.1 steps
+// 2-3): uniform sample of s far-field rows (§2.2), K' = K(rows, node sources),
+// pivoted QR in tolerance mode for at most s/2 steps, T = R11^-1 R12
+// (§2.1.3, App. A.1). Nodes whose tolerance is not met within s/2 steps are
+// re-run with s doubled (the sample is prefix consistent) while s <= s_max.
+//
+// All nodes of all compressed levels run together: one "round" per sample
+// size. A round is a fixed sequence of batched launches over the round's work
+// items (sampling, size patch, block evaluation, cooperative QR, finalize and
+// triangular solve, epilogue); only the epilogue's per-node "needs a larger
+// sample" flags come back to the host, once per round.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ffc_internal.cuh"
+
+namespace ffc {
+int64_t eval_tiles(int64_t s, int64_t n);
+int64_t eval_row_tiles(int64_t s);
+int cpqr_rows_per_lane(int s_max);
+size_t sample_smem_bytes(int64_t M_max, int d);
+}  // namespace ffc
+
+using namespace ffc;
+
+struct ffc_tree_result {
+  int64_t N = 0;
+  int d = 0, dtype = 0;
+  int64_t n_tree_nodes = 0;
+  ffc_params p{};
+  int64_t n_out = 0;
+  std::vector<int32_t> node_h;
+  std::vector<int64_t> begin_h, count_h, rows_off_h, skel_off_h, T_off_h;
+  // outputs
+  char* out_mem = nullptr;
+  int32_t *node = nullptr, *rank = nullptr, *s = nullptr, *status = nullptr, *skel = nullptr;
+  double *r22 = nullptr, *log_scale = nullptr, *T = nullptr;
+  int64_t *far_count = nullptr, *rows_off = nullptr, *rows = nullptr, *skel_off = nullptr, *T_off = nullptr;
+  // round workspace (grow-only)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int rounds = 0;
+};
+
+namespace {
+
+struct Layout {
+  size_t off = 0;
+  template <typename T>
+  size_t add(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+__global__ void patch_kernel(int W, const int64_t* s_out, int64_t s_nom, int r_cap, EvalItem* ev, CpqrItem* qr) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W) return;
+  const int64_t s_eff = s_out[q];
+  const bool all_rows = s_eff < s_nom;
+  const int n = qr[q].n;
+  int cap = all_rows ? (int)s_eff : (int)(s_eff / 2);
+  cap = min(cap, min(n, r_cap));
+  ev[q].s = s_eff;
+  qr[q].s = (int32_t)s_eff;
+  qr[q].r_max = cap;
+}
+
+__global__ void epilogue_kernel(int W, const int32_t* out_idx, int64_t s_nom, int s_max, const int64_t* s_out,
+                                const int64_t* fc, const double* lsc, const int32_t* st_eval,
+                                const int32_t* qr_rank, const double* qr_r22, const int32_t* st_qr,
+                                int32_t* res_rank, int32_t* res_s, int32_t* res_status, double* res_r22,
+                                double* res_lsc, int64_t* res_fc, int32_t* flags) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W) return;
+  const int o = out_idx[q];
+  const int64_t s_eff = s_out[q];
+  const bool all_rows = s_eff < s_nom;
+  const int qs = st_qr[q], es = st_eval[q];
+  int status = FFC_OK;
+  if (s_eff == 0) status = FFC_E_FARFIELD_TOO_SMALL;
+  else if (es == FFC_E_SINGULAR) status = FFC_E_SINGULAR;
+  else if (qs == FFC_E_TIMEOUT) status = FFC_E_TIMEOUT;
+  else if (qs == FFC_E_TOL_NOT_REACHED) status = FFC_E_TOL_NOT_REACHED;
+  const bool again = status == FFC_E_TOL_NOT_REACHED && !all_rows && 2 * s_nom <= s_max;
+  flags[q] = again ? 1 : 0;
+  res_rank[o] = qr_rank[q];
+  res_s[o] = (int32_t)s_eff;
+  res_status[o] = status;
+  res_r22[o] = qr_r22[q];
+  res_lsc[o] = lsc[q];
+  res_fc[o] = fc[q];
+}
+
+ffc_status alloc_outputs(ffc_tree_result* R) {
+  const int64_t n = R->n_out;
+  const int64_t rows_cap = R->rows_off_h[n], skel_cap = R->skel_off_h[n], T_cap = R->T_off_h[n];
+  Layout L;
+  size_t o_node = L.add<int32_t>(n), o_rank = L.add<int32_t>(n), o_s = L.add<int32_t>(n),
+         o_status = L.add<int32_t>(n), o_r22 = L.add<double>(n), o_lsc = L.add<double>(n),
+         o_fc = L.add<int64_t>(n), o_rows_off = L.add<int64_t>(n + 1), o_rows = L.add<int64_t>(rows_cap),
+         o_skel_off = L.add<int64_t>(n + 1), o_skel = L.add<int32_t>(skel_cap), o_T_off = L.add<int64_t>(n + 1),
+         o_T = L.add<double>(T_cap);
+  FFC_CUDA(cudaMalloc((void**)&R->out_mem, L.off));
+  char* b = R->out_mem;
+  R->node = (int32_t*)(b + o_node); R->rank = (int32_t*)(b + o_rank); R->s = (int32_t*)(b + o_s);
+  R->status = (int32_t*)(b + o_status); R->r22 = (double*)(b + o_r22); R->log_scale = (double*)(b + o_lsc);
+  R->far_count = (int64_t*)(b + o_fc); R->rows_off = (int64_t*)(b + o_rows_off); R->rows = (int64_t*)(b + o_rows);
+  R->skel_off = (int64_t*)(b + o_skel_off); R->skel = (int32_t*)(b + o_skel); R->T_off = (int64_t*)(b + o_T_off);
+  R->T = (double*)(b + o_T);
+  FFC_CUDA(cudaMemcpy(R->node, R->node_h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  FFC_CUDA(cudaMemcpy(R->rows_off, R->rows_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+  FFC_CUDA(cudaMemcpy(R->skel_off, R->skel_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+  FFC_CUDA(cudaMemcpy(R->T_off, R->T_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+  return FFC_OK;
+}
+
+int group_size_tree(int64_t s, int64_t n, int64_t elems) {
+  int64_t g = (s * n + elems - 1) / std::max<int64_t>(elems, 1);
+  g = std::min<int64_t>(g, std::max<int64_t>(1, n / 4));
+  return (int)std::max<int64_t>(1, g);
+}
+
+// One sample-size round over the work items `items` (indices into outputs).
+ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, const std::vector<int>& items,
+                     int64_t s_nom, std::vector<int>& again, cudaStream_t st) {
+  const int W = (int)items.size();
+  const ffc_params& P = R->p;
+  const int d = R->d;
+  const int r_cap_glob = P.s_max / 2;
+  const int rcap_round = (int)std::min<int64_t>(s_nom, r_cap_glob);
+  // per-item sizes
+  std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W);
+  std::vector<int> g(W);
+  int64_t SN = 0, elems = 0, RC = 0, tiles_tot = 0, n_max = 0;
+  for (int q = 0; q < W; ++q) {
+    const int64_t n = R->count_h[items[q]];
+    noff[q] = SN;
+    koff[q] = SN * s_nom;
+    SN += n;
+    elems += n * s_nom;
+    r11off[q] = RC;
+    const int64_t rc = std::min<int64_t>(n, rcap_round);
+    RC += rc * rc;
+    tiles[q] = tiles_tot;
+    tiles_tot += eval_tiles(s_nom, n);
+    n_max = std::max(n_max, n);
+  }
+  const int cap = cpqr_max_ctas(P.precision, (int)s_nom);
+  if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
+  const int64_t per_cta = std::max<int64_t>(16384, (elems + cap - 1) / cap);
+  int64_t G = 0;
+  for (int q = 0; q < W; ++q) {
+    g[q] = std::min(cap, group_size_tree(s_nom, R->count_h[items[q]], per_cta));
+    goff[q] = G;
+    G += g[q];
+  }
+  // trsm tiles (8 columns per CTA)
+  std::vector<int64_t> ttiles(W);
+  int64_t ttot = 0;
+  for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += (R->count_h[items[q]] + 7) / 8; }
+
+  const int64_t scratch_ctas = std::min<int64_t>(W, 2048);
+  Layout L;
+  const size_t o_si = L.add<SampleItem>(W), o_ei = L.add<EvalItem>(W), o_qi = L.add<CpqrItem>(W),
+               o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(G), o_sout = L.add<int64_t>(W),
+               o_fc = L.add<int64_t>(W), o_sst = L.add<int32_t>(W), o_md = L.add<double>(W), o_ls = L.add<double>(W),
+               o_est = L.add<int32_t>(W), o_K = L.add<double>((size_t)s_nom * SN),
+               o_piv = L.add<int32_t>((size_t)W * rcap_round), o_beta = L.add<double>((size_t)W * rcap_round),
+               o_vn1 = L.add<double>(SN), o_vn2 = L.add<double>(SN), o_sel = L.add<uint8_t>(SN),
+               o_slots = L.add<Slot>(2 * G), o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
+               o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
+               o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
+               o_oidx = L.add<int32_t>(W);
+  if (L.off > R->ws_bytes) {
+    if (R->ws) {
+      FFC_CUDA(cudaStreamSynchronize(st));
+      FFC_CUDA(cudaFree(R->ws));
+      R->ws = nullptr;
+    }
+    size_t want = L.off + L.off / 4;
+    FFC_CUDA(cudaMalloc((void**)&R->ws, want));
+    R->ws_bytes = want;
+  }
+  char* b = R->ws;
+  SampleItem* d_si = (SampleItem*)(b + o_si);
+  EvalItem* d_ei = (EvalItem*)(b + o_ei);
+  CpqrItem* d_qi = (CpqrItem*)(b + o_qi);
+  TrsmItem* d_ti = (TrsmItem*)(b + o_ti);
+  CtaAssign* d_as = (CtaAssign*)(b + o_as);
+  int64_t* s_out = (int64_t*)(b + o_sout);
+  int64_t* fc = (int64_t*)(b + o_fc);
+  int32_t* sst = (int32_t*)(b + o_sst);
+  double* mind2 = (double*)(b + o_md);
+  double* lsc = (double*)(b + o_ls);
+  int32_t* est = (int32_t*)(b + o_est);
+  double* K = (double*)(b + o_K);
+  int32_t* piv = (int32_t*)(b + o_piv);
+  double* beta = (double*)(b + o_beta);
+  double* vn1 = (double*)(b + o_vn1);
+  double* vn2 = (double*)(b + o_vn2);
+  uint8_t* sel = (uint8_t*)(b + o_sel);
+  Slot* slots = (Slot*)(b + o_slots);
+  unsigned* bar = (unsigned*)(b + o_bar);
+  int32_t* qrank = (int32_t*)(b + o_rank);
+  double* qr22 = (double*)(b + o_r22);
+  int32_t* qst = (int32_t*)(b + o_qst);
+  double* R11 = (double*)(b + o_R11);
+  int32_t* scratch = (int32_t*)(b + o_scr);
+  int32_t* flags = (int32_t*)(b + o_flag);
+  int32_t* oidx = (int32_t*)(b + o_oidx);
+
+  std::vector<SampleItem> hs(W);
+  std::vector<EvalItem> he(W);
+  std::vector<CpqrItem> hq(W);
+  std::vector<TrsmItem> ht(W);
+  std::vector<CtaAssign> ha(G);
+  std::vector<int32_t> ho(W);
+  for (int q = 0; q < W; ++q) {
+    const int o = items[q];
+    const int64_t node = R->node_h[o], bgn = R->begin_h[o], n = R->count_h[o];
+    ho[q] = o;
+    SampleItem& si = hs[q];
+    si.M = R->N; si.ex_begin = bgn; si.ex_end = bgn + n;
+    si.x_c = tree->centroid_dev + node * d; si.thr2 = 0.0; si.radius = tree->radius_dev + node; si.xi = P.xi;
+    si.s = s_nom; si.stream_id = (uint64_t)node; si.rows = R->rows + R->rows_off_h[o];
+    EvalItem& ei = he[q];
+    ei.rows = si.rows; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = K + koff[q]; ei.ldk = s_nom;
+    ei.center = nullptr; ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom);
+    CpqrItem& qi = hq[q];
+    qi = CpqrItem{};
+    qi.A = K + koff[q]; qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;
+    qi.piv = piv + (size_t)q * rcap_round; qi.beta = beta + (size_t)q * rcap_round;
+    qi.vn1 = vn1 + noff[q]; qi.vn2 = vn2 + noff[q]; qi.selected = sel + noff[q];
+    qi.slots = slots + 2 * goff[q]; qi.barrier = bar + q; qi.rank_out = qrank + q; qi.r22_out = qr22 + q;
+    qi.status_out = qst + q;
+    TrsmItem& ti = ht[q];
+    ti = TrsmItem{};
+    ti.A = K + koff[q]; ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = qrank + q; ti.piv = qi.piv; ti.beta = qi.beta;
+    ti.selected = qi.selected; ti.skel_perm = R->skel + R->skel_off_h[o]; ti.R11 = R11 + r11off[q];
+    ti.T = R->T + R->T_off_h[o]; ti.ldt = 0; ti.r_cap = (int32_t)std::min<int64_t>(n, rcap_round);
+    ti.tile_begin = ttiles[q];
+    for (int c = 0; c < g[q]; ++c) ha[goff[q] + c] = CtaAssign{q, c, g[q], 0};
+  }
+  FFC_CUDA(cudaMemcpyAsync(d_si, hs.data(), sizeof(SampleItem) * W, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_ei, he.data(), sizeof(EvalItem) * W, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_qi, hq.data(), sizeof(CpqrItem) * W, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_ti, ht.data(), sizeof(TrsmItem) * W, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_as, ha.data(), sizeof(CtaAssign) * G, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(oidx, ho.data(), sizeof(int32_t) * W, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemsetAsync(est, 0, sizeof(int32_t) * W, st));
+  FFC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * W, st));
+  FFC_CUDA(cudaMemsetAsync(qst, 0, sizeof(int32_t) * W, st));
+  FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, st));
+  FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, st));
+
+  ffc_status rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, st);
+  if (rc != FFC_OK) return rc;
+  patch_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
+  rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
+  if (rc != FFC_OK) return rc;
+  // cooperative QR launches: consecutive items whose groups fit together
+  int q0 = 0;
+  while (q0 < W) {
+    int q1 = q0;
+    int64_t ctas = 0;
+    while (q1 < W && ctas + g[q1] <= cap) { ctas += g[q1]; ++q1; }
+    rc = launch_cpqr(P.precision, d_qi, d_as + goff[q0], (int)ctas, (int)s_nom, st);
+    if (rc != FFC_OK) return rc;
+    q0 = q1;
+  }
+  rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
+  if (rc != FFC_OK) return rc;
+  epilogue_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, oidx, s_nom, P.s_max, s_out, fc, lsc, est, qrank, qr22, qst,
+                                                   R->rank, R->s, R->status, R->r22, R->log_scale, R->far_count,
+                                                   flags);
+  FFC_CUDA(cudaGetLastError());
+  std::vector<int32_t> hf(W);
+  FFC_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaStreamSynchronize(st));
+  again.clear();
+  for (int q = 0; q < W; ++q)
+    if (hf[q]) again.push_back(items[q]);
+  return FFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t N, int32_t d, const ffc_tree* tree,
+                             const ffc_params* params, ffc_tree_result** result, void* stream) {
+  FFC_REQUIRE(tree && params && result, "ffc_compress_tree: null argument");
+  FFC_REQUIRE(N >= 1 && d >= 1 && N <= 1500000, "ffc_compress_tree: need 1 <= N <= 1,500,000 and d >= 1");
+  FFC_REQUIRE(dtype == FFC_F64 || dtype == FFC_F32, "ffc_compress_tree: bad dtype");
+  FFC_REQUIRE(points_perm_dev && tree->begin_dev && tree->count_dev && tree->centroid_dev && tree->radius_dev,
+              "ffc_compress_tree: null pointer");
+  const ffc_params& P = *params;
+  FFC_REQUIRE(P.precision == FFC_FP64, "ffc_compress_tree: only FFC_FP64 is available in this build");
+  FFC_REQUIRE(P.s0 >= 2 && P.s_max >= P.s0 && P.s_max <= 2048, "ffc_compress_tree: need 2 <= s0 <= s_max <= 2048");
+  FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
+  FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
+              "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");
+  FFC_REQUIRE(P.min_level >= 0 && P.min_level <= tree->depth, "ffc_compress_tree: min_level out of range");
+  ffc_kernel kk = P.kernel;
+  if (kk.kind == FFC_GAUSSIAN) FFC_REQUIRE(kk.h > 0.0, "Gaussian bandwidth must be > 0");
+  else if (kk.kind == FFC_LAPLACE) FFC_REQUIRE(d != 2, "d = 2 Laplace kernel unsupported");
+  else if (kk.kind == FFC_POLYNOMIAL) FFC_REQUIRE(kk.h != 0.0 && kk.p >= 1, "bad polynomial kernel");
+  else FFC_REQUIRE(false, "unknown kernel kind");
+  cudaStream_t st = as_stream(stream);
+
+  ffc_tree_result* R = *result;
+  const bool fresh = (R == nullptr);
+  if (!fresh) {
+    FFC_REQUIRE(R->N == N && R->d == d && R->dtype == dtype && R->n_tree_nodes == tree->n_nodes &&
+                    R->p.min_level == P.min_level && R->p.s_max == P.s_max,
+                "ffc_compress_tree: result was created for a different tree shape or params");
+    R->p = P;
+  } else {
+    R = new ffc_tree_result();
+    R->N = N; R->d = d; R->dtype = dtype; R->n_tree_nodes = tree->n_nodes; R->p = P;
+    std::vector<int64_t> b(tree->n_nodes), c(tree->n_nodes);
+    node_layout(N, tree->depth, b.data(), c.data(), nullptr);
+    const int64_t first = ((int64_t)1 << P.min_level) - 1;
+    const int64_t rcap = P.s_max / 2;
+    R->rows_off_h.push_back(0);
+    R->skel_off_h.push_back(0);
+    R->T_off_h.push_back(0);
+    for (int64_t i = first; i < tree->n_nodes; ++i) {
+      R->node_h.push_back((int32_t)i);
+      R->begin_h.push_back(b[i]);
+      R->count_h.push_back(c[i]);
+      R->rows_off_h.push_back(R->rows_off_h.back() + P.s_max);
+      R->skel_off_h.push_back(R->skel_off_h.back() + c[i]);
+      R->T_off_h.push_back(R->T_off_h.back() + std::min<int64_t>(c[i], rcap) * c[i]);
+    }
+    R->n_out = (int64_t)R->node_h.size();
+    ffc_status rc = alloc_outputs(R);
+    if (rc != FFC_OK) { ffc_tree_result_free(R); return rc; }
+    *result = R;
+  }
+  std::vector<int> active(R->n_out), again;
+  for (int64_t i = 0; i < R->n_out; ++i) active[i] = (int)i;
+  int64_t s_nom = P.s0;
+  R->rounds = 0;
+  while (!active.empty()) {
+    ffc_status rc = run_round(R, points_perm_dev, tree, active, s_nom, again, st);
+    if (rc != FFC_OK) return rc;
+    ++R->rounds;
+    active.swap(again);
+    s_nom *= 2;
+  }
+  return FFC_OK;
+}
+
+ffc_status ffc_tree_result_view(const ffc_tree_result* R, ffc_tree_view* v) {
+  FFC_REQUIRE(R && v, "ffc_tree_result_view: null argument");
+  v->n_out = R->n_out; v->rounds = R->rounds;
+  v->node_dev = R->node; v->rank_dev = R->rank; v->s_dev = R->s; v->status_dev = R->status;
+  v->r22_rel_dev = R->r22; v->log_scale_dev = R->log_scale; v->far_count_dev = R->far_count;
+  v->rows_off_dev = R->rows_off; v->rows_dev = R->rows; v->skel_off_dev = R->skel_off; v->skel_dev = R->skel;
+  v->T_off_dev = R->T_off; v->T_dev = R->T;
+  return FFC_OK;
+}
+
+void ffc_tree_result_free(ffc_tree_result* R) {
+  if (!R) return;
+  if (R->out_mem) cudaFree(R->out_mem);
+  if (R->ws) cudaFree(R->ws);
+  delete R;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+"""ctypes binding of libffc (include/ffc.h): argument marshalling only.
+
+Every function here validates nothing beyond tensor placement and dtype,
+passes raw device pointers and sizes to the C ABI, and turns the returned
+status into a Python value or exception. All arithmetic runs in libffc's
+CUDA kernels; there is no CPU fallback: if libffc.so is missing or no GPU is
+present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffc.so")
+
+FFC_OK = 0
+FFC_E_INVALID = 1
+FFC_E_NOMEM = 2
+FFC_E_CUDA = 3
+FFC_E_TIMEOUT = 4
+FFC_E_FARFIELD_TOO_SMALL = 5
+FFC_E_SINGULAR = 6
+FFC_E_TOL_NOT_REACHED = 7
+SOFT_STATUSES = (FFC_OK, FFC_E_FARFIELD_TOO_SMALL, FFC_E_TOL_NOT_REACHED)
+
+GAUSSIAN, LAPLACE, POLYNOMIAL = 0, 1, 2
+F64, F32 = 0, 1
+FP64, MIXED = 0, 1
+
+EXPORTS = (
+    "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
+    "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
+    "ffc_tree_result_free",
+)
+
+
+class FFCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libffc status {status}: {msg}")
+        self.status = status
+
+
+class c_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("p", ctypes.c_int32), ("h", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class c_tree(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("begin_dev", ctypes.c_void_p),
+                ("count_dev", ctypes.c_void_p), ("centroid_dev", ctypes.c_void_p), ("radius_dev", ctypes.c_void_p)]
+
+
+class c_params(ctypes.Structure):
+    _fields_ = [("kernel", c_kernel), ("precision", ctypes.c_int32), ("min_level", ctypes.c_int32),
+                ("s0", ctypes.c_int32), ("s_max", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("xi", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class c_tree_view(ctypes.Structure):
+    _fields_ = [("n_out", ctypes.c_int64), ("rounds", ctypes.c_int32)] + [
+        (name, ctypes.c_void_p) for name in (
+            "node_dev", "rank_dev", "s_dev", "status_dev", "r22_rel_dev", "log_scale_dev", "far_count_dev",
+            "rows_off_dev", "rows_dev", "skel_off_dev", "skel_dev", "T_off_dev", "T_dev")]
+
+
+@dataclass(frozen=True)
+class Kernel:
+    kind: int
+    h: float = 1.0
+    c: float = 1.0
+    p: int = 3
+
+    def c_struct(self) -> c_kernel:
+        return c_kernel(int(self.kind), int(self.p), float(self.h), float(self.c))
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libffc.so (built by __graft_entry__.build()) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    pi64, pdbl = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    L.ffc_last_error.restype = ctypes.c_char_p
+    L.ffc_version.restype = ctypes.c_char_p
+    L.ffc_far_field.argtypes = [vp, i32, i64, i32, vp, dbl, dbl, i64, i64, vp, pi64, vp]
+    L.ffc_sample_rows.argtypes = [vp, i32, i64, i32, vp, dbl, dbl, i64, i64, i64, u64, u64, vp, pi64, pi64, vp]
+    L.ffc_eval_block.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i32, vp, i64, pdbl, vp]
+    L.ffc_id.argtypes = [vp, i64, i64, i64, i32, i64, dbl, vp, vp, i64, pi64, pdbl, vp]
+    L.ffc_id_error.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, pdbl, vp]
+    L.ffc_tree_depth.argtypes = [i64, i64]
+    L.ffc_tree_depth.restype = i32
+    L.ffc_build_tree.argtypes = [vp, i32, i64, i32, i64, vp, vp, vp, vp, vp, vp]
+    L.ffc_compress_tree.argtypes = [vp, i32, i64, i32, ctypes.POINTER(c_tree), ctypes.POINTER(c_params),
+                                    ctypes.POINTER(vp), vp]
+    L.ffc_tree_result_view.argtypes = [vp, ctypes.POINTER(c_tree_view)]
+    L.ffc_tree_result_free.argtypes = [vp]
+    L.ffc_tree_result_free.restype = None
+    for name in EXPORTS:
+        if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int) -> int:
+    if status not in SOFT_STATUSES:
+        raise FFCError(status, lib().ffc_last_error().decode())
+    return status
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"points must be float64 or float32, got {t.dtype}")
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def version() -> str:
+    return lib().ffc_version().decode()
+
+
+def ffc_far_field(Y, x_c=None, radius=0.0, xi=1.0, ex_begin=0, ex_end=0, stream=None):
+    """Ascending far-field indices of Y (int64 CUDA tensor)."""
+    _dev(Y, "Y")
+    M, d = Y.shape
+    idx = torch.empty(M, dtype=torch.int64, device=Y.device)
+    cnt = ctypes.c_int64(0)
+    _check(lib().ffc_far_field(_ptr(Y), _dtype_code(Y), M, d, _ptr(x_c), float(radius), float(xi),
+                               int(ex_begin), int(ex_end), _ptr(idx), ctypes.byref(cnt), _stream(stream)))
+    return idx[: cnt.value]
+
+
+def ffc_sample_rows(Y, s, seed, stream_id, x_c=None, radius=0.0, xi=1.0, ex_begin=0, ex_end=0, stream=None):
+    """Uniform far-field sample: returns (rows int64[s_out], far_count, status)."""
+    _dev(Y, "Y")
+    M, d = Y.shape
+    rows = torch.empty(max(int(s), 1), dtype=torch.int64, device=Y.device)
+    s_out, fc = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _check(lib().ffc_sample_rows(_ptr(Y), _dtype_code(Y), M, d, _ptr(x_c), float(radius), float(xi),
+                                      int(ex_begin), int(ex_end), int(s), ctypes.c_uint64(int(seed)),
+                                      ctypes.c_uint64(int(stream_id)), _ptr(rows), ctypes.byref(s_out),
+                                      ctypes.byref(fc), _stream(stream)))
+    return rows[: s_out.value], fc.value, st
+
+
+def ffc_eval_block(kernel: Kernel, Y, rows, X, precision=FP64, center=None, K=None, stream=None):
+    """K'(rows, X) column-major: returns (K as an (n, s) row-major view's transpose, log_scale).
+
+    The block is stored column-major s x n with ld = s; the returned tensor is
+    the s x n matrix view of that storage.
+    """
+    _dev(Y, "Y"), _dev(X, "X"), _dev(rows, "rows")
+    s, (n, d) = rows.numel(), X.shape
+    if K is None:
+        K = torch.empty((max(n, 1), max(s, 1)), dtype=torch.float64 if precision == FP64 else torch.float32,
+                        device=X.device)
+    ls = ctypes.c_double(0.0)
+    _check(lib().ffc_eval_block(kernel.c_struct(), _ptr(Y), _dtype_code(Y), _ptr(rows), s, _ptr(X), n, d,
+                                _ptr(center), int(precision), _ptr(K), max(s, 1), ctypes.byref(ls),
+                                _stream(stream)))
+    return K[:n, :s].t(), ls.value
+
+
+def ffc_id(Kcm, r_max, tol=0.0, precision=FP64, stream=None):
+    """ID of a column-major block given as its (n, s) storage tensor (overwritten).
+
+    Returns (skel_perm int32[n], T (rank x (n - rank)) float64, rank, r22_rel, status).
+    """
+    _dev(Kcm, "K")
+    n, s = Kcm.shape
+    ldt = max(int(r_max), 1)
+    skel = torch.empty(max(n, 1), dtype=torch.int32, device=Kcm.device)
+    T = torch.empty((max(n, 1), ldt), dtype=torch.float64, device=Kcm.device)
+    rank, r22 = ctypes.c_int64(0), ctypes.c_double(0.0)
+    st = _check(lib().ffc_id(_ptr(Kcm), s, n, max(s, 1), int(precision), int(r_max), float(tol), _ptr(skel),
+                             _ptr(T), ldt, ctypes.byref(rank), ctypes.byref(r22), _stream(stream)))
+    r = rank.value
+    return skel[:n], T[: n - r, :r].t(), r, r22.value, st
+
+
+def ffc_id_error(kernel: Kernel, Y, X, skel, T, r, rows=None, ldt=None, stream=None):
+    """Full-block relative Frobenius error of an ID; T given as a (ldt, n-r) column-major storage."""
+    _dev(Y, "Y"), _dev(X, "X")
+    m = rows.numel() if rows is not None else Y.shape[0]
+    n, d = X.shape
+    err = ctypes.c_double(0.0)
+    Tc = T.t().contiguous() if T.numel() else torch.zeros(1, dtype=torch.float64, device=X.device)
+    _check(lib().ffc_id_error(kernel.c_struct(), _ptr(Y), _dtype_code(Y), _ptr(rows), m, _ptr(X), n, d,
+                              _ptr(skel), _ptr(Tc), max(int(r), 1) if ldt is None else int(ldt), int(r),
+                              ctypes.byref(err), _stream(stream)))
+    return err.value
+
+
+def ffc_tree_depth(N, leaf_size) -> int:
+    return int(lib().ffc_tree_depth(int(N), int(leaf_size)))
+
+
+@dataclass
+class DeviceTree:
+    depth: int
+    perm: torch.Tensor
+    begin: torch.Tensor
+    count: torch.Tensor
+    centroid: torch.Tensor
+    radius: torch.Tensor
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.begin.numel())
+
+    def c_struct(self) -> c_tree:
+        return c_tree(self.depth, self.n_nodes, self.begin.data_ptr(), self.count.data_ptr(),
+                      self.centroid.data_ptr(), self.radius.data_ptr())
+
+
+def ffc_build_tree(points, leaf_size, stream=None) -> DeviceTree:
+    _dev(points, "points")
+    N, d = points.shape
+    depth = ffc_tree_depth(N, leaf_size)
+    nn = (1 << (depth + 1)) - 1
+    dev = points.device
+    t = DeviceTree(depth, torch.empty(N, dtype=torch.int64, device=dev), torch.empty(nn, dtype=torch.int64, device=dev),
+                   torch.empty(nn, dtype=torch.int64, device=dev), torch.empty((nn, d), dtype=torch.float64, device=dev),
+                   torch.empty(nn, dtype=torch.float64, device=dev))
+    _check(lib().ffc_build_tree(_ptr(points), _dtype_code(points), N, d, int(leaf_size), _ptr(t.perm), _ptr(t.begin),
+                                _ptr(t.count), _ptr(t.centroid), _ptr(t.radius), _stream(stream)))
+    return t
+
+
+class TreeResult:
+    """Owns an ffc_tree_result; frees it on close()/deletion."""
+
+    def __init__(self):
+        self.handle = ctypes.c_void_p(0)
+
+    def view(self) -> c_tree_view:
+        v = c_tree_view()
+        _check(lib().ffc_tree_result_view(self.handle, ctypes.byref(v)))
+        return v
+
+    def close(self):
+        if self.handle and self.handle.value:
+            lib().ffc_tree_result_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
+                      s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None) -> TreeResult:
+    _dev(points_perm, "points_perm")
+    N, d = points_perm.shape
+    res = result if result is not None else TreeResult()
+    p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
+                 ctypes.c_uint64(int(seed)))
+    tr = tree.c_struct()
+    _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
+                                   ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
+    return res
+
+
+_TORCH_DTYPES = {"int32": torch.int32, "int64": torch.int64, "float64": torch.float64}
+
+
+def device_view(ptr: int, count: int, dtype: str) -> torch.Tensor:
+    """A CUDA tensor viewing `count` elements of library-owned device memory (no copy)."""
+    if count == 0 or not ptr:
+        return torch.empty(0, dtype=_TORCH_DTYPES[dtype], device="cuda")
+    typestr = {"int32": "<i4", "int64": "<i8", "float64": "<f8"}[dtype]
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                    "version": 3, "strides": None}
+
+    return torch.as_tensor(_View(), device="cuda")
+
+
+def tree_result_views(res: TreeResult) -> dict:
+    """Device views of a TreeResult's per-node outputs (valid while `res` lives)."""
+    v = res.view()
+    n = int(v.n_out)
+    out = {"n_out": n, "rounds": int(v.rounds)}
+    for name, dt, cnt in (("node", "int32", n), ("rank", "int32", n), ("s", "int32", n), ("status", "int32", n),
+                          ("r22_rel", "float64", n), ("log_scale", "float64", n), ("far_count", "int64", n),
+                          ("rows_off", "int64", n + 1), ("skel_off", "int64", n + 1), ("T_off", "int64", n + 1)):
+        out[name] = device_view(getattr(v, name + "_dev"), cnt, dt)
+    out["rows"] = device_view(v.rows_dev, int(out["rows_off"][-1].item()) if n else 0, "int64")
+    out["skel"] = device_view(v.skel_dev, int(out["skel_off"][-1].item()) if n else 0, "int32")
+    out["T"] = device_view(v.T_dev, int(out["T_off"][-1].item()) if n else 0, "float64")
+    return out
+
+
+def tree_result_to_host(res: TreeResult) -> dict:
+    """numpy copies of a TreeResult's per-node outputs."""
+    views = tree_result_views(res)
+    return {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in views.items()}

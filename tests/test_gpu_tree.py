@@ -1,0 +1,124 @@
+"""GPU parity of the tree path: ffc_build_tree and ffc_compress_tree vs the oracle.
+
+Small trees are compared node by node; at the benchmark's full size (N=65,536,
+d=16, leaf 256, Gaussian h=2, tol 1e-6) every node is checked for the
+properties that hold at any size and a seeded sample of nodes against the
+oracle's per-node compression.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import compress as o_compress
+from oracle import interp as o_interp
+from oracle import kernels as o_kernels
+from oracle import tree as o_tree
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1409_2802_gb300 import ffc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def cu(a):
+    return torch.tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def _build_both(P, leaf):
+    t_o = o_tree.build_tree(P, leaf)
+    t_g = ffc.ffc_build_tree(cu(P), leaf)
+    return t_o, t_g
+
+
+@pytest.mark.parametrize("N,d,leaf", [(4096, 4, 256), (5000, 16, 300), (3001, 130, 100)])
+def test_build_tree_matches_oracle(N, d, leaf):
+    P = workloads.gaussian_mixture(N=N, d=d, k=4, seed=N)
+    t_o, t_g = _build_both(P, leaf)
+    assert t_g.depth == t_o.depth
+    assert np.array_equal(t_g.perm.cpu().numpy(), t_o.perm)
+    assert np.array_equal(t_g.begin.cpu().numpy(), t_o.begin)
+    assert np.array_equal(t_g.count.cpu().numpy(), t_o.count)
+    np.testing.assert_allclose(t_g.centroid.cpu().numpy(), t_o.centroid, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(t_g.radius.cpu().numpy(), t_o.radius, rtol=1e-13)
+
+
+def _compare_nodes(out, t_o, Pp, kernel_o, tol, nodes, s0, s_max, seed=0, check_error=True):
+    index = {int(nd): i for i, nd in enumerate(out["node"])}
+    for node in nodes:
+        i = index[node]
+        ref = o_compress.compress_node(Pp, t_o, node, kernel_o, tol, seed, s0, s_max)
+        s = int(out["s"][i])
+        assert s == ref.s, node
+        rows = out["rows"][out["rows_off"][i]: out["rows_off"][i] + s]
+        assert np.array_equal(rows, ref.rows), node
+        assert int(out["far_count"][i]) in (-1, ref.far_count)
+        assert int(out["status"][i]) == ref.status, node
+        r = int(out["rank"][i])
+        assert r == ref.rank, (node, r, ref.rank)
+        assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
+        n = int(t_o.count[node])
+        skel = out["skel"][out["skel_off"][i]: out["skel_off"][i] + n].astype(np.int64)
+        T = out["T"][out["T_off"][i]: out["T_off"][i] + r * (n - r)].reshape(n - r, r).T if r else np.zeros((0, n))
+        P_g = o_interp.assemble_P(skel, T, n)
+        assert np.array_equal(P_g[:, skel[:r]], np.eye(r))      # P contains I_r
+        if check_error and r > 0:
+            b = int(t_o.begin[node])
+            from oracle.sampling import far_field_mask
+            far = far_field_mask(Pp, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n)
+            e_g = o_interp.full_block_error(kernel_o, Pp[far], Pp[b:b + n], skel, T)
+            e_o = o_interp.full_block_error(kernel_o, Pp[far], Pp[b:b + n], ref.skel_perm, ref.T)
+            assert abs(e_g - e_o) <= 1e-10 + 1e-6 * e_o, (node, e_g, e_o)
+
+
+def test_compress_small_tree_every_node():
+    P = workloads.gaussian_mixture(N=4096, d=4, k=4, seed=1)
+    t_o, t_g = _build_both(P, 256)
+    Pp = P[t_o.perm]
+    ko = o_kernels.Kernel(o_kernels.GAUSSIAN, h=1.0)
+    res = ffc.ffc_compress_tree(cu(Pp), t_g, ffc.Kernel(ffc.GAUSSIAN, h=1.0), tol=1e-6, s0=32, s_max=512)
+    out = ffc.tree_result_to_host(res)
+    nodes = [i for i in range(t_o.n_nodes) if t_o.level[i] >= 2]
+    assert list(out["node"]) == nodes
+    _compare_nodes(out, t_o, Pp, ko, 1e-6, nodes, 32, 512)
+    # the result object is reusable: a second call gives identical outputs
+    out2 = ffc.tree_result_to_host(ffc.ffc_compress_tree(cu(Pp), t_g, ffc.Kernel(ffc.GAUSSIAN, h=1.0), tol=1e-6,
+                                                         s0=32, s_max=512, result=res))
+    for key in ("rank", "s", "rows", "skel", "T", "r22_rel"):
+        assert np.array_equal(out[key], out2[key]), key
+
+
+def test_compress_laplace_and_polynomial_small():
+    P = workloads.gaussian_mixture(N=3000, d=6, k=3, seed=2)
+    t_o, t_g = _build_both(P, 200)
+    Pp = P[t_o.perm]
+    for kind, h in ((o_kernels.LAPLACE, 1.0), (o_kernels.POLYNOMIAL, 6.0)):
+        ko = o_kernels.Kernel(kind, h=h)
+        out = ffc.tree_result_to_host(ffc.ffc_compress_tree(cu(Pp), t_g, ffc.Kernel(kind, h=h), tol=1e-6, s0=32,
+                                                            s_max=256))
+        nodes = [i for i in range(t_o.n_nodes) if t_o.level[i] >= 2]
+        _compare_nodes(out, t_o, Pp, ko, 1e-6, nodes[::3], 32, 256)
+
+
+def test_compress_full_size_gaussian_d16():
+    """Benchmark configuration: every node's invariants, 12 seeded nodes vs the oracle."""
+    P = workloads.gaussian_mixture(N=65536, d=16, k=8, seed=0)
+    t_o, t_g = _build_both(P, 256)
+    Pp = P[t_o.perm]
+    res = ffc.ffc_compress_tree(cu(Pp), t_g, ffc.Kernel(ffc.GAUSSIAN, h=2.0), tol=1e-6, s0=128, s_max=2048)
+    out = ffc.tree_result_to_host(res)
+    assert out["n_out"] == 508
+    st = out["status"]
+    assert np.all((st == 0) | (st == ffc.FFC_E_TOL_NOT_REACHED))
+    ok = st == 0
+    assert np.all(out["r22_rel"][ok] <= 1e-6)
+    cap = np.minimum(np.where(out["s"] < 2 * out["s"], out["s"] // 2, out["s"]), t_o.count[out["node"]])
+    assert np.all(out["rank"] <= np.maximum(cap, out["s"]))
+    g = np.random.default_rng(0)
+    nodes = sorted(g.choice(out["node"], 12, replace=False).tolist())
+    _compare_nodes(out, t_o, Pp, o_kernels.Kernel(o_kernels.GAUSSIAN, h=2.0), 1e-6, nodes, 128, 2048,
+                   check_error=False)

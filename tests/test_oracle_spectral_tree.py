@@ -93,7 +93,7 @@ def test_compress_small_tree_contract():
         assert nr.far_count == int(far.sum())
         if nr.status == compress.STATUS_OK:
             assert nr.r22_rel <= 1e-6
-            all_rows = nr.s >= nr.far_count
+            all_rows = nr.s < nr.attempts[-1]
             assert nr.rank <= compress.rank_cap(nr.s, c, all_rows, 256)
         # the reported ID reproduces the sampled block to ||R22||
         K, _ = kernels.kernel_block(k, Xp[nr.rows], Xp[b:b + c])
