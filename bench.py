@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark: tree nodes compressed per second by sampled-row ID on one GB300.
+
+Workload (one "step" = one full ffc_compress_tree call over every node at
+level >= 2): N = 65,536 points in d = 16 from an 8-component Gaussian mixture
+(means uniform in [-5, 5]^16, sigma 1), PCA median-split tree with leaf size
+256 (levels 2..8, 508 nodes, n = 16,384 .. 256), Gaussian kernel h = 2,
+tolerance 1e-6 on ||R22||_F / ||K'||_F, s = 128 doubling to at most 2,048.
+Synthetic data; the tree is built once on the GPU before timing (support).
+
+Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events
+on the launching stream; a 512 MB buffer is written between steps to flush
+the 129 MB L2 (outside the events). Clocks are sampled with nvidia-smi
+during the timed steps. `value` is nodes / second over the timed steps;
+`e2e` repeats the measurement through host buffers (pinned H2D of the
+permuted points and tree, compression, D2H of every node's rank, status,
+residual, skeleton and interpolation matrix). `cpu_baseline` times the FP64
+oracle on a seeded, time-bounded sample of the same nodes in a
+single-threaded subprocess; `--impl reference` times that oracle per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "tree_compress_gaussian_mixture_N65536_d16",
+    "N": 65536, "d": 16, "components": 8, "data_seed": 0, "leaf_size": 256, "kernel": "gaussian", "h": 2.0,
+    "tol": 1e-6, "s0": 128, "s_max": 2048, "min_level": 2, "xi": 1.0, "sample_seed": 0,
+}
+METRIC = "nodes compressed/sec at ID rel. error <=1e-6; chosen form vs plain FP64 GPU"
+UNIT = "nodes/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 FMA rate of a GB300 (nominal 1.25 TFLOP/s dense FP64); the QR of the
+# plain path is bound by it.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_inputs(torch, dev):
+    import workloads
+    from paper_1409_2802_gb300 import ffc
+    W = WORKLOAD
+    rank, _, _ = _env_rank()
+    P = workloads.gaussian_mixture(N=W["N"], d=W["d"], k=W["components"], seed=W["data_seed"] + rank)
+    Pd = torch.tensor(P, device=dev)
+    tree = ffc.ffc_build_tree(Pd, W["leaf_size"])
+    Pp = Pd[tree.perm].contiguous()
+    return P, tree, Pp
+
+
+def precision_code(ffc, name):
+    return ffc.FP64 if name == "fp64" else ffc.MIXED
+
+
+def run_gpu_steps(torch, ffc, Pp, tree, precision, steps, warmup, flush_buf, stream, result=None):
+    W = WORKLOAD
+    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
+
+    def step(res):
+        return ffc.ffc_compress_tree(Pp, tree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
+                                     s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
+                                     stream=stream)
+
+    res = result
+    for _ in range(warmup):
+        res = step(res)
+    res.profile_enable(True)
+    res.profile_reset()
+    times = []
+    for _ in range(steps):
+        flush_buf.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(res)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    prof = res.profile()
+    res.profile_enable(False)
+    return res, times, prof
+
+
+def run_e2e(torch, ffc, P_host_perm, tree, precision, steps, warmup, stream):
+    """Same metric through host buffers: pinned H2D inputs, compress, D2H results, every step."""
+    W = WORKLOAD
+    dev = P_host_perm.device if P_host_perm.is_cuda else torch.device("cuda")
+    hP = P_host_perm.cpu().pin_memory()
+    tree_host = {n: getattr(tree, n).cpu().pin_memory() for n in ("begin", "count", "centroid", "radius")}
+    dP = torch.empty_like(hP, device=dev)
+    dT = {n: torch.empty_like(v, device=dev) for n, v in tree_host.items()}
+    dtree = ffc.DeviceTree(tree.depth, tree.perm, dT["begin"], dT["count"], dT["centroid"], dT["radius"])
+    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
+    res = None
+    h2d = hP.numel() * hP.element_size() + sum(v.numel() * v.element_size() for v in tree_host.values())
+    d2h_bytes = []
+
+    def step(res):
+        with torch.cuda.stream(stream):
+            dP.copy_(hP, non_blocking=True)
+            for n in dT:
+                dT[n].copy_(tree_host[n], non_blocking=True)
+        res = ffc.ffc_compress_tree(dP, dtree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
+                                    s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
+                                    stream=stream)
+        with torch.cuda.stream(stream):
+            v = ffc.tree_result_views(res)
+            out = {kk: v[kk].to("cpu", non_blocking=False) for kk in ("rank", "s", "status", "r22_rel", "skel", "T_off",
+                                                                       "T")}
+        d2h_bytes.append(sum(t.numel() * t.element_size() for t in out.values()))
+        return res
+
+    for _ in range(warmup):
+        res = step(res)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        res = step(res)
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    n_nodes = ffc.tree_result_views(res)["n_out"]
+    return {"value": n_nodes * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(statistics.mean(d2h_bytes[-steps:])), "wall_s": wall}
+
+
+# --------------------------------------------------------------------------- oracle legs
+
+def oracle_setup():
+    import workloads
+    from oracle import tree as o_tree
+    W = WORKLOAD
+    P = workloads.gaussian_mixture(N=W["N"], d=W["d"], k=W["components"], seed=W["data_seed"])
+    t = o_tree.build_tree(P, W["leaf_size"])
+    return P[t.perm], t
+
+
+def oracle_nodes_in_order(t, seed=12345):
+    import numpy as np
+    nodes = np.array([i for i in range(t.n_nodes) if t.level[i] >= WORKLOAD["min_level"]])
+    return list(np.random.default_rng(seed).permutation(nodes))
+
+
+def oracle_compress(Pp, t, node):
+    from oracle import compress as o_compress
+    from oracle.kernels import GAUSSIAN, Kernel
+    W = WORKLOAD
+    return o_compress.compress_node(Pp, t, int(node), Kernel(GAUSSIAN, h=W["h"]), W["tol"], W["sample_seed"],
+                                    W["s0"], W["s_max"], W["xi"])
+
+
+def cpu_leg() -> int:
+    """Child process: compress nodes in a seeded random order, one JSON line per finished node."""
+    Pp, t = oracle_setup()
+    order = oracle_nodes_in_order(t)
+    print(json.dumps({"ready": True, "of": len(order)}), flush=True)
+    t0 = time.perf_counter()
+    for i, node in enumerate(order):
+        oracle_compress(Pp, t, node)
+        print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
+    return 0
+
+
+class OracleStream:
+    """The FP64 oracle compressing nodes in a seeded random order in a single-threaded child process.
+
+    The child prints one line per finished node; the parent reads the count of
+    finished nodes at any time. The node in progress when a window closes
+    counts as time spent, so a window's throughput is finished nodes / window.
+    """
+
+    def __init__(self):
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+            env.pop(k, None)
+        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", "1"], env=env,
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.of, self.ready_t, self.done = None, None, 0
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            try:
+                msg = json.loads(line)
+            except ValueError:
+                continue
+            if msg.get("ready"):
+                self.of = msg["of"]
+                self.ready_t = time.perf_counter()
+            elif "done" in msg:
+                self.done = msg["done"]
+
+    def wait_ready(self, timeout=900.0) -> bool:
+        end = time.perf_counter() + timeout
+        while self.ready_t is None and self.proc.poll() is None and time.perf_counter() < end:
+            time.sleep(0.05)
+        return self.ready_t is not None
+
+    def window(self, seconds: float):
+        """Sleep through one window; returns (nodes finished in it, its length)."""
+        d0, t0 = self.done, time.perf_counter()
+        end = t0 + seconds
+        while self.proc.poll() is None and time.perf_counter() < end:
+            time.sleep(0.05)
+        return self.done - d0, time.perf_counter() - t0
+
+    def close(self):
+        self.proc.kill()
+        self.proc.wait()
+
+
+def finish_cpu_baseline(o: "OracleStream", min_seconds: float) -> dict:
+    """Close the oracle stream started at the beginning of the run (one core, concurrent with the GPU work)."""
+    try:
+        if not o.wait_ready():
+            return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "oracle setup failed"}
+        remaining = o.ready_t + min_seconds - time.perf_counter()
+        if remaining > 0:
+            o.window(remaining)
+        el = time.perf_counter() - o.ready_t
+        done = o.done
+    finally:
+        o.close()
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{done} of {o.of} nodes finished in a {el:.1f} s window (seeded random node order; the "
+                       f"node still running at the end counts as time spent), one thread (OMP/OpenBLAS = 1), "
+                       f"running on a host core while the GPU steps ran")}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the FP64 CPU oracle; each step is one fixed time window of its node stream."""
+    if rank != 0:
+        return 0
+    win = min(20.0, max(2.0, 150.0 / (args.steps + args.warmup)))
+    o = OracleStream()
+    try:
+        if not o.wait_ready():
+            print(json.dumps({"impl": "reference", "unavailable": "oracle setup failed"}))
+            return 0
+        for _ in range(args.warmup):
+            o.window(win)
+        done, el = 0, 0.0
+        for _ in range(args.steps):
+            dn, t = o.window(win)
+            done += dn
+            el += t
+    finally:
+        o.close()
+    value = done / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "step": f"{win:.1f} s window of the oracle's node stream",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"{done} nodes finished over {args.steps} windows of {win:.1f} s "
+                                   f"(seeded random node order), one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--cpu-seconds", type=float, default=30.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--_cpu-leg", type=float, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args._cpu_leg is not None:
+        return cpu_leg()
+
+    rank, world, local = _env_rank()
+    oracle = OracleStream() if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.impl == "ours") else None
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1409_2802_gb300 import ffc
+    ffc.lib()
+    P, tree, Pp = build_inputs(torch, dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prec = precision_code(ffc, args.precision)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    res = None
+    # first call allocates; it is part of warm-up
+    clocks.start()
+    res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, prec, args.steps, args.warmup, flush, stream)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    views = ffc.tree_result_views(res)
+    n_nodes = int(views["n_out"])
+    value = n_nodes * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant phase, from the library's live CUDA-event timing
+    peaks, peak_src = load_peaks()
+    phase_ms = prof["ms"]
+    dominant = max(phase_ms, key=phase_ms.get)
+    qr_ms = phase_ms["qr"] / max(args.steps, 1)
+    qr_tflops = prof["qr_flops"] / args.steps / (qr_ms / 1e3) / 1e12 if qr_ms > 0 else 0.0
+    roofline = {
+        "kernel": "cpqr_fp64_kernel (pivoted QR)", "bound": "alu", "achieved": qr_tflops,
+        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": qr_tflops / FP64_PEAK_TFLOPS,
+        "traffic": None, "peak_source": "nominal FP64 rate of GB300 (derived, see DESIGN.md)",
+        "dominant_phase": dominant, "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "qr_bytes_per_step": prof["qr_bytes"] / args.steps,
+        "qr_hbm_gbs": prof["qr_bytes"] / args.steps / (qr_ms / 1e3) / 1e9 if qr_ms > 0 else 0.0,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_src,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == ffc.FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "precision": args.precision, "nodes": n_nodes,
+                   "levels": "2..8", "kernel": "gaussian h=2", "tol": WORKLOAD["tol"], "s": "128 doubling to 2048",
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "clocks": clk, "gpu_launches": int(prof["launches"]),
+        "roofline": roofline,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(torch, ffc, Pp, tree, prec, max(3, args.steps // 2), 2, stream)
+    if oracle is not None:
+        line["cpu_baseline"] = finish_cpu_baseline(oracle, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

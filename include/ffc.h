@@ -255,6 +255,35 @@ typedef struct {
 ffc_status ffc_tree_result_view(const ffc_tree_result* result, ffc_tree_view* view);
 void ffc_tree_result_free(ffc_tree_result* result);
 
+/*
+ * Phase timing of ffc_compress_tree (tracing). When enabled on a result,
+ * each later ffc_compress_tree call records CUDA events on its stream around
+ * every phase of every round and adds the elapsed times (milliseconds) into
+ * the profile; ffc_tree_profile_reset zeroes it. Phases: 0 sampling,
+ * 1 block evaluation, 2 pivoted QR, 3 finalize + triangular solve,
+ * 4 bookkeeping (size patch, epilogue, table uploads). `launches` counts
+ * the library's kernel launches, `qr_flops` the algorithmic flops of the QR
+ * steps taken, sum over steps k of 4 (s - k)(n - k) (one dot product and
+ * one update per remaining element), `eval_flops` 3 s n d per block
+ * (difference, square, add per coordinate; 2 s n d for the polynomial).
+ */
+typedef struct {
+  int32_t enabled;
+  int32_t calls;        /* ffc_compress_tree calls accumulated */
+  int32_t rounds;       /* sample-size rounds accumulated */
+  int32_t pad;
+  int64_t launches;     /* kernel launches accumulated */
+  int64_t qr_launches;  /* of which QR launches */
+  double ms[5];         /* per phase, accumulated */
+  double qr_flops;      /* accumulated */
+  double eval_flops;    /* accumulated */
+  double qr_bytes;      /* one read + one write of every QR block, accumulated */
+} ffc_tree_profile;
+
+ffc_status ffc_tree_profile_enable(ffc_tree_result* result, int32_t enabled);
+ffc_status ffc_tree_profile_reset(ffc_tree_result* result);
+ffc_status ffc_tree_profile_get(const ffc_tree_result* result, ffc_tree_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,10 +40,17 @@ struct ffc_tree_result {
   int32_t *node = nullptr, *rank = nullptr, *s = nullptr, *status = nullptr, *skel = nullptr;
   double *r22 = nullptr, *log_scale = nullptr, *T = nullptr;
   int64_t *far_count = nullptr, *rows_off = nullptr, *rows = nullptr, *skel_off = nullptr, *T_off = nullptr;
+  // T is solved into per-node slots of capacity min(n, s_max/2) x n (T, T_off: capacity offsets) and
+  // packed at the end of each call into Tp (node i at Tp_off[i], r_i x (n_i - r_i), ld r_i)
+  double* Tp = nullptr;
+  int64_t *Tp_off = nullptr, *count_dev = nullptr;
   // round workspace (grow-only)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int rounds = 0;
+  // tracing
+  ffc_tree_profile prof{};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -97,6 +104,42 @@ __global__ void epilogue_kernel(int W, const int32_t* out_idx, int64_t s_nom, in
   res_fc[o] = fc[q];
 }
 
+// Packed offsets of T: node i holds rank_i x (n_i - rank_i) doubles.
+__global__ void pack_offsets_kernel(int64_t n_out, const int32_t* rank, const int64_t* count, int64_t* off) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n_out; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < n_out ? (int64_t)rank[i] * (count[i] - rank[i]) : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+      const int64_t add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < n_out) off[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[n_out] = carry;
+}
+
+__global__ void pack_copy_kernel(int64_t n_out, const int64_t* cap_off, const int64_t* off, const double* src,
+                                 double* dst) {
+  const int64_t i = blockIdx.y;
+  if (i >= n_out) return;
+  const int64_t len = off[i + 1] - off[i];
+  const double* s = src + cap_off[i];
+  double* d = dst + off[i];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = s[e];
+}
+
 ffc_status alloc_outputs(ffc_tree_result* R) {
   const int64_t n = R->n_out;
   const int64_t rows_cap = R->rows_off_h[n], skel_cap = R->skel_off_h[n], T_cap = R->T_off_h[n];
@@ -105,7 +148,8 @@ ffc_status alloc_outputs(ffc_tree_result* R) {
          o_status = L.add<int32_t>(n), o_r22 = L.add<double>(n), o_lsc = L.add<double>(n),
          o_fc = L.add<int64_t>(n), o_rows_off = L.add<int64_t>(n + 1), o_rows = L.add<int64_t>(rows_cap),
          o_skel_off = L.add<int64_t>(n + 1), o_skel = L.add<int32_t>(skel_cap), o_T_off = L.add<int64_t>(n + 1),
-         o_T = L.add<double>(T_cap);
+         o_T = L.add<double>(T_cap), o_Tp = L.add<double>(T_cap), o_Tp_off = L.add<int64_t>(n + 1),
+         o_cnt = L.add<int64_t>(n);
   FFC_CUDA(cudaMalloc((void**)&R->out_mem, L.off));
   char* b = R->out_mem;
   R->node = (int32_t*)(b + o_node); R->rank = (int32_t*)(b + o_rank); R->s = (int32_t*)(b + o_s);
@@ -113,6 +157,8 @@ ffc_status alloc_outputs(ffc_tree_result* R) {
   R->far_count = (int64_t*)(b + o_fc); R->rows_off = (int64_t*)(b + o_rows_off); R->rows = (int64_t*)(b + o_rows);
   R->skel_off = (int64_t*)(b + o_skel_off); R->skel = (int32_t*)(b + o_skel); R->T_off = (int64_t*)(b + o_T_off);
   R->T = (double*)(b + o_T);
+  R->Tp = (double*)(b + o_Tp); R->Tp_off = (int64_t*)(b + o_Tp_off); R->count_dev = (int64_t*)(b + o_cnt);
+  FFC_CUDA(cudaMemcpy(R->count_dev, R->count_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
   FFC_CUDA(cudaMemcpy(R->node, R->node_h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   FFC_CUDA(cudaMemcpy(R->rows_off, R->rows_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
   FFC_CUDA(cudaMemcpy(R->skel_off, R->skel_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
@@ -259,33 +305,67 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, st));
 
+  const bool prof = R->prof.enabled != 0;
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[0], st));
   ffc_status rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, st);
   if (rc != FFC_OK) return rc;
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[1], st));
   patch_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
   rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
   if (rc != FFC_OK) return rc;
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
   // cooperative QR launches: consecutive items whose groups fit together
-  int q0 = 0;
+  int q0 = 0, qr_launches = 0;
   while (q0 < W) {
     int q1 = q0;
     int64_t ctas = 0;
     while (q1 < W && ctas + g[q1] <= cap) { ctas += g[q1]; ++q1; }
     rc = launch_cpqr(P.precision, d_qi, d_as + goff[q0], (int)ctas, (int)s_nom, st);
     if (rc != FFC_OK) return rc;
+    ++qr_launches;
     q0 = q1;
   }
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[3], st));
   rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
   if (rc != FFC_OK) return rc;
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[4], st));
   epilogue_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, oidx, s_nom, P.s_max, s_out, fc, lsc, est, qrank, qr22, qst,
                                                    R->rank, R->s, R->status, R->r22, R->log_scale, R->far_count,
                                                    flags);
   FFC_CUDA(cudaGetLastError());
-  std::vector<int32_t> hf(W);
+  if (prof) FFC_CUDA(cudaEventRecord(R->ev[5], st));
+  std::vector<int32_t> hf(W), hr(prof ? W : 0);
+  std::vector<int64_t> hsz(prof ? W : 0);
   FFC_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, st));
+  if (prof) {
+    FFC_CUDA(cudaMemcpyAsync(hr.data(), qrank, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, st));
+    FFC_CUDA(cudaMemcpyAsync(hsz.data(), s_out, sizeof(int64_t) * W, cudaMemcpyDeviceToHost, st));
+  }
   FFC_CUDA(cudaStreamSynchronize(st));
   again.clear();
   for (int q = 0; q < W; ++q)
     if (hf[q]) again.push_back(items[q]);
+  if (prof) {
+    ffc_tree_profile& pf = R->prof;
+    for (int ph = 0; ph < 5; ++ph) {
+      float ms = 0.f;
+      FFC_CUDA(cudaEventElapsedTime(&ms, R->ev[ph], R->ev[ph + 1]));
+      pf.ms[ph] += ms;
+    }
+    const int eval_launches = P.kernel.kind == FFC_LAPLACE ? 4 : 1;
+    pf.launches += 1 + 1 + eval_launches + qr_launches + 2 + 1;
+    pf.qr_launches += qr_launches;
+    pf.rounds += 1;
+    const double per_coord = P.kernel.kind == FFC_POLYNOMIAL ? 2.0 : 3.0;
+    for (int q = 0; q < W; ++q) {
+      const double s = (double)hsz[q], n = (double)R->count_h[items[q]];
+      double fl = 0.0;
+      for (int k = 0; k < hr[q]; ++k) fl += 4.0 * (s - k) * (n - k);
+      pf.qr_flops += fl;
+      pf.eval_flops += per_coord * s * n * d;
+      pf.qr_bytes += 2.0 * s * n * sizeof(double);
+    }
+  }
   return FFC_OK;
 }
 
@@ -348,6 +428,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   for (int64_t i = 0; i < R->n_out; ++i) active[i] = (int)i;
   int64_t s_nom = P.s0;
   R->rounds = 0;
+  if (R->prof.enabled) R->prof.calls += 1;
   while (!active.empty()) {
     ffc_status rc = run_round(R, points_perm_dev, tree, active, s_nom, again, st);
     if (rc != FFC_OK) return rc;
@@ -355,6 +436,10 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
     active.swap(again);
     s_nom *= 2;
   }
+  pack_offsets_kernel<<<1, 1024, 0, st>>>(R->n_out, R->rank, R->count_dev, R->Tp_off);
+  pack_copy_kernel<<<dim3(8, (unsigned)R->n_out), 256, 0, st>>>(R->n_out, R->T_off, R->Tp_off, R->T, R->Tp);
+  FFC_CUDA(cudaGetLastError());
+  if (R->prof.enabled) R->prof.launches += 2;
   return FFC_OK;
 }
 
@@ -364,7 +449,7 @@ ffc_status ffc_tree_result_view(const ffc_tree_result* R, ffc_tree_view* v) {
   v->node_dev = R->node; v->rank_dev = R->rank; v->s_dev = R->s; v->status_dev = R->status;
   v->r22_rel_dev = R->r22; v->log_scale_dev = R->log_scale; v->far_count_dev = R->far_count;
   v->rows_off_dev = R->rows_off; v->rows_dev = R->rows; v->skel_off_dev = R->skel_off; v->skel_dev = R->skel;
-  v->T_off_dev = R->T_off; v->T_dev = R->T;
+  v->T_off_dev = R->Tp_off; v->T_dev = R->Tp;
   return FFC_OK;
 }
 
@@ -372,7 +457,31 @@ void ffc_tree_result_free(ffc_tree_result* R) {
   if (!R) return;
   if (R->out_mem) cudaFree(R->out_mem);
   if (R->ws) cudaFree(R->ws);
+  for (auto& e : R->ev)
+    if (e) cudaEventDestroy(e);
   delete R;
+}
+
+ffc_status ffc_tree_profile_enable(ffc_tree_result* R, int32_t enabled) {
+  FFC_REQUIRE(R, "ffc_tree_profile_enable: null result");
+  if (enabled && !R->ev[0])
+    for (auto& e : R->ev) FFC_CUDA(cudaEventCreate(&e));
+  R->prof.enabled = enabled ? 1 : 0;
+  return FFC_OK;
+}
+
+ffc_status ffc_tree_profile_reset(ffc_tree_result* R) {
+  FFC_REQUIRE(R, "ffc_tree_profile_reset: null result");
+  const int32_t en = R->prof.enabled;
+  R->prof = ffc_tree_profile{};
+  R->prof.enabled = en;
+  return FFC_OK;
+}
+
+ffc_status ffc_tree_profile_get(const ffc_tree_result* R, ffc_tree_profile* out) {
+  FFC_REQUIRE(R && out, "ffc_tree_profile_get: null argument");
+  *out = R->prof;
+  return FFC_OK;
 }
 
 }  // extern "C"

@@ -34,8 +34,9 @@ FP64, MIXED = 0, 1
 EXPORTS = (
     "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
     "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
-    "ffc_tree_result_free",
+    "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
 )
+PROFILE_PHASES = ("sample", "eval", "qr", "trsm", "bookkeeping")
 
 
 class FFCError(RuntimeError):
@@ -64,6 +65,13 @@ class c_tree_view(ctypes.Structure):
         (name, ctypes.c_void_p) for name in (
             "node_dev", "rank_dev", "s_dev", "status_dev", "r22_rel_dev", "log_scale_dev", "far_count_dev",
             "rows_off_dev", "rows_dev", "skel_off_dev", "skel_dev", "T_off_dev", "T_dev")]
+
+
+class c_tree_profile(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int32), ("calls", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("launches", ctypes.c_int64), ("qr_launches", ctypes.c_int64),
+                ("ms", ctypes.c_double * 5), ("qr_flops", ctypes.c_double), ("eval_flops", ctypes.c_double),
+                ("qr_bytes", ctypes.c_double)]
 
 
 @dataclass(frozen=True)
@@ -105,6 +113,9 @@ def lib() -> ctypes.CDLL:
     L.ffc_tree_result_view.argtypes = [vp, ctypes.POINTER(c_tree_view)]
     L.ffc_tree_result_free.argtypes = [vp]
     L.ffc_tree_result_free.restype = None
+    L.ffc_tree_profile_enable.argtypes = [vp, i32]
+    L.ffc_tree_profile_reset.argtypes = [vp]
+    L.ffc_tree_profile_get.argtypes = [vp, ctypes.POINTER(c_tree_profile)]
     for name in EXPORTS:
         if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
             getattr(L, name).restype = ctypes.c_int
@@ -264,6 +275,19 @@ class TreeResult:
         v = c_tree_view()
         _check(lib().ffc_tree_result_view(self.handle, ctypes.byref(v)))
         return v
+
+    def profile_enable(self, enabled: bool = True):
+        _check(lib().ffc_tree_profile_enable(self.handle, 1 if enabled else 0))
+
+    def profile_reset(self):
+        _check(lib().ffc_tree_profile_reset(self.handle))
+
+    def profile(self) -> dict:
+        p = c_tree_profile()
+        _check(lib().ffc_tree_profile_get(self.handle, ctypes.byref(p)))
+        return {"calls": p.calls, "rounds": p.rounds, "launches": p.launches, "qr_launches": p.qr_launches,
+                "ms": dict(zip(PROFILE_PHASES, list(p.ms))), "qr_flops": p.qr_flops, "eval_flops": p.eval_flops,
+                "qr_bytes": p.qr_bytes}
 
     def close(self):
         if self.handle and self.handle.value:

@@ -126,24 +126,30 @@ def test_eval_laplace_singular_rejected():
 
 # ---------------------------------------------------------------- ID
 
-def _pivot_gaps_clear(Kblock, r, thr=1e-7):
-    """True if the oracle's pivot choice has no near tie in its first r steps."""
+def _determined_pivots(Kblock, r, thr=1e-7, floor=1e-11):
+    """How many of the oracle's first r pivots are fixed by the data.
+
+    A pivot is determined when the two largest residual norms differ by more
+    than thr (relative) and the largest is above floor * ||K||_F; past the
+    numerical rank the residual is rounding noise and any choice is correct.
+    """
     A = np.array(Kblock, dtype=np.float64)
     s, n = A.shape
+    fro = np.linalg.norm(A)
     selected = np.zeros(n, dtype=bool)
     from oracle.cpqr import householder
     for k in range(min(r, s, n)):
         free = np.flatnonzero(~selected)
         nr = np.sqrt(np.sum(A[k:, free] ** 2, axis=0))
         o = np.sort(nr)[::-1]
-        if o.size > 1 and (o[0] - o[1]) <= thr * o[0]:
-            return False
+        if o[0] <= floor * fro or (o.size > 1 and (o[0] - o[1]) <= thr * o[0]):
+            return k
         p = int(free[np.argmax(nr)])
         v, tau, beta = householder(A[k:, p])
         rest = free[free != p]
         A[k:, rest] -= tau * np.outer(v, v @ A[k:, rest])
         selected[p] = True
-    return True
+    return min(r, s, n)
 
 
 def _check_id(Ko, r_max, tol, ok=None, Y=None, X=None, gk=None):
@@ -154,11 +160,18 @@ def _check_id(Ko, r_max, tol, ok=None, Y=None, X=None, gk=None):
     skel, T = skel.cpu().numpy().astype(np.int64), T.cpu().numpy()
     assert r == ref["rank"]
     assert abs(r22 - ref["r22_rel"]) <= 1e-10
-    if _pivot_gaps_clear(Ko, r):
+    k_det = _determined_pivots(Ko, r)
+    assert np.array_equal(skel[:k_det], ref["skel_perm"][:k_det])
+    if k_det == r:
         assert np.array_equal(skel, ref["skel_perm"])
+        # T itself is only as well determined as R11 is conditioned (entries
+        # differ by ~ cond(R11) * eps); what the ID delivers, C P, must agree
+        # to rounding: ||K(:,J) (P_gpu - P_oracle)||_F / ||K||_F
         Pg = o_interp.assemble_P(skel, T, n)
         Po = o_interp.assemble_P(ref["skel_perm"], ref["T"], n)
-        assert np.max(np.abs(Pg - Po)) <= 1e-8 * max(1.0, np.max(np.abs(Po)))
+        J = skel[:r]
+        diff = np.linalg.norm(Ko[:, J] @ (Pg - Po)) / max(np.linalg.norm(Ko), 1e-300)
+        assert diff <= 1e-12, diff
     # the GPU ID reproduces the block to its own r22
     assert o_interp.reconstruction_error(Ko, skel, T) == pytest.approx(r22, rel=1e-6, abs=1e-14)
     if ok is not None:
