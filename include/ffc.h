@@ -149,6 +149,34 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
                   int64_t* rank_host, double* r22_rel_host, void* stream);
 
 /*
+ * ffc_id_noalloc - ffc_id without any device allocation. The paper has no
+ * counterpart: this is an interface variant for callers that cannot call
+ * cudaMalloc (or cudaMallocAsync) at call time, for example code running
+ * inside a framework whose caching allocator already owns the device memory
+ * (a raw allocation can fail or fragment its pool), latency-critical loops
+ * that cannot afford an allocation's implicit synchronisation, and
+ * deployments that fix their device memory budget up front.
+ *
+ * Arguments, outputs, statuses and results are those of ffc_id (FFC_FP64).
+ * Instead of allocating, the call keeps its QR scratch (column norms, pivot
+ * and reflector data, group slots, R11) in one fixed array of about 0.8 MB
+ * that every GPU loading the library holds until the process exits. Limits:
+ * n <= FFC_NOALLOC_MAX_COLS, min(r_max, s, n) <= FFC_NOALLOC_MAX_RANK,
+ * s <= 2048; larger problems return FFC_E_INVALID before anything is
+ * enqueued. The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture. All calls share the one array and the next call
+ * overwrites it: calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race. Synchronises `stream`.
+ */
+#define FFC_NOALLOC_MAX_COLS 16384
+#define FFC_NOALLOC_MAX_RANK 256
+ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precision,
+                          int64_t r_max, double tol,
+                          int32_t* skel_perm_dev, double* T_dev, int64_t ldt,
+                          int64_t* rank_host, double* r22_rel_host, void* stream);
+
+/*
  * ffc_id_error - relative Frobenius error of an ID on a full block
  * (§4.1.3, step 4): ||K - K(:, J) P||_F / ||K||_F with K_ij = K(Y[rows_i], X_j)
  * over m target rows (rows_dev NULL = rows 0..m-1 of Y). skel_perm_dev, T_dev,

@@ -35,6 +35,7 @@ EXPORTS = (
     "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
     "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
     "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
+    "ffc_id_noalloc",
 )
 PROFILE_PHASES = ("sample", "eval", "qr", "trsm", "bookkeeping")
 
@@ -104,6 +105,7 @@ def lib() -> ctypes.CDLL:
     L.ffc_sample_rows.argtypes = [vp, i32, i64, i32, vp, dbl, dbl, i64, i64, i64, u64, u64, vp, pi64, pi64, vp]
     L.ffc_eval_block.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i32, vp, i64, pdbl, vp]
     L.ffc_id.argtypes = [vp, i64, i64, i64, i32, i64, dbl, vp, vp, i64, pi64, pdbl, vp]
+    L.ffc_id_noalloc.argtypes = [vp, i64, i64, i64, i32, i64, dbl, vp, vp, i64, pi64, pdbl, vp]
     L.ffc_id_error.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, vp, i64, i64, pdbl, vp]
     L.ffc_tree_depth.argtypes = [i64, i64]
     L.ffc_tree_depth.restype = i32
