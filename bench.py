@@ -345,13 +345,74 @@ def reference_arm(args, rank, world):
     return 0
 
 
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal)
+
+
+def qr_roofline(prof, steps, precision_name, peaks, peak_src):
+    """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing."""
+    phase_ms = prof["ms"]
+    qr_ms = phase_ms["qr"] / max(steps, 1)
+    tflops = prof["qr_flops"] / steps / (qr_ms / 1e3) / 1e12 if qr_ms > 0 else 0.0
+    gbs = prof["qr_bytes"] / steps / (qr_ms / 1e3) / 1e9 if qr_ms > 0 else 0.0
+    if precision_name == "fp64":
+        peak, kern, src = FP64_PEAK_TFLOPS, "cpqr_kernel<double> (pivoted QR, FP64)", "nominal FP64 rate of GB300"
+    else:
+        peak, kern, src = FP32_PEAK_TFLOPS, "cpqr_kernel<float> (pivoted QR, FP32 updates, FP64 norms)", \
+            "nominal FP32 rate of GB300 (152 SMs x 128 lanes x 2.07 GHz)"
+    return {
+        "kernel": kern, "bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+        "traffic": None, "peak_source": src, "dominant_phase": max(phase_ms, key=phase_ms.get),
+        "phase_ms_per_step": {k: v / steps for k, v in phase_ms.items()},
+        "qr_flops_per_step": prof["qr_flops"] / steps, "qr_bytes_per_step": prof["qr_bytes"] / steps,
+        "qr_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_frac": gbs / peaks.get("hbm_gbs", 1.0),
+        "hbm_peak_source": peak_src,
+    }
+
+
+def accuracy_sample(torch, ffc, Pp, tree, results, n_sample=12, seed=7):
+    """Full-block ID error of a seeded sample of nodes for each precision (outside the timed region)."""
+    import numpy as np
+    W = WORKLOAD
+    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
+    host = {p: ffc.tree_result_to_host(r) for p, r in results.items()}
+    views = {p: ffc.tree_result_views(r) for p, r in results.items()}
+    any_p = next(iter(host))
+    nodes = host[any_p]["node"]
+    pick = sorted(np.random.default_rng(seed).choice(len(nodes), min(n_sample, len(nodes)), replace=False).tolist())
+    begin, count = tree.begin.cpu().numpy(), tree.count.cpu().numpy()
+    errs = {p: [] for p in results}
+    for i in pick:
+        node = int(nodes[i])
+        b, n = int(begin[node]), int(count[node])
+        far = ffc.ffc_far_field(Pp, x_c=tree.centroid[node].contiguous(), radius=float(tree.radius[node]), xi=W["xi"],
+                                ex_begin=b, ex_end=b + n)
+        for p in results:
+            h, v = host[p], views[p]
+            r = int(h["rank"][i])
+            skel = v["skel"][int(h["skel_off"][i]): int(h["skel_off"][i]) + n]
+            off = int(h["T_off"][i])
+            T = v["T"][off: off + r * (n - r)].view(n - r, r).t() if r else torch.zeros((0, n), device=Pp.device,
+                                                                                          dtype=torch.float64)
+            errs[p].append(ffc.ffc_id_error(k, Pp, Pp[b:b + n], skel, T, r, rows=far))
+    out = {"nodes_checked": [int(nodes[i]) for i in pick]}
+    for p in errs:
+        out[f"max_error_{p}"] = float(max(errs[p]))
+    if "mixed" in errs and "fp64" in errs:
+        out["max_abs_diff_mixed_vs_fp64"] = float(max(abs(a - b) for a, b in zip(errs["mixed"], errs["fp64"])))
+        out["within_1e-6"] = out["max_abs_diff_mixed_vs_fp64"] <= 1e-6
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="the timed form (value); the plain FP64 path is timed beside it unless --no-fp64-compare")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -378,42 +439,28 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prec = precision_code(ffc, args.precision)
-
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    res = None
-    # first call allocates; it is part of warm-up
-    clocks.start()
-    res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, prec, args.steps, args.warmup, flush, stream)
-    clk = clocks.stop()
-    torch.cuda.synchronize()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
-    views = ffc.tree_result_views(res)
-    n_nodes = int(views["n_out"])
-    value = n_nodes * args.steps * world / (total_ms / 1e3)
-
-    # roofline of the dominant phase, from the library's live CUDA-event timing
     peaks, peak_src = load_peaks()
-    phase_ms = prof["ms"]
-    dominant = max(phase_ms, key=phase_ms.get)
-    qr_ms = phase_ms["qr"] / max(args.steps, 1)
-    qr_tflops = prof["qr_flops"] / args.steps / (qr_ms / 1e3) / 1e12 if qr_ms > 0 else 0.0
-    roofline = {
-        "kernel": "cpqr_fp64_kernel (pivoted QR)", "bound": "alu", "achieved": qr_tflops,
-        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": qr_tflops / FP64_PEAK_TFLOPS,
-        "traffic": None, "peak_source": "nominal FP64 rate of GB300 (derived, see DESIGN.md)",
-        "dominant_phase": dominant, "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "qr_bytes_per_step": prof["qr_bytes"] / args.steps,
-        "qr_hbm_gbs": prof["qr_bytes"] / args.steps / (qr_ms / 1e3) / 1e9 if qr_ms > 0 else 0.0,
-        "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_src,
-    }
+
+    def timed(prec_code, steps, warmup):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, prec_code, steps, warmup, flush, stream)
+        torch.cuda.synchronize()
+        total = sum(times)
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+            torch.distributed.barrier()
+        return res, total, prof
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    res, total_ms, prof = timed(prec, args.steps, args.warmup)
+    clk = clocks.stop()
+    n_nodes = int(ffc.tree_result_views(res)["n_out"])
+    value = n_nodes * args.steps * world / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -422,8 +469,19 @@ def main():
                    "levels": "2..8", "kernel": "gaussian h=2", "tol": WORKLOAD["tol"], "s": "128 doubling to 2048",
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "clocks": clk, "gpu_launches": int(prof["launches"]),
-        "roofline": roofline,
+        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src),
     }
+    results = {args.precision: res}
+    if not args.no_fp64_compare and args.precision != "fp64":
+        fsteps = max(3, args.steps // 3)
+        res64, ms64, prof64 = timed(ffc.FP64, fsteps, 1)
+        v64 = n_nodes * fsteps * world / (ms64 / 1e3)
+        line["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / fsteps, "steps": fsteps,
+                              "roofline": qr_roofline(prof64, fsteps, "fp64", peaks, peak_src)}
+        line["speedup_vs_fp64"] = value / v64
+        results["fp64"] = res64
+    if not args.no_accuracy and rank == 0:
+        line["accuracy"] = accuracy_sample(torch, ffc, Pp, tree, results)
     if not args.no_e2e:
         line["e2e"] = run_e2e(torch, ffc, Pp, tree, prec, max(3, args.steps // 2), 2, stream)
     if oracle is not None:

@@ -168,7 +168,7 @@ ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype, c
   FFC_REQUIRE(s >= 0 && n >= 0 && d >= 1, "ffc_eval_block: need s, n >= 0 and d >= 1");
   FFC_REQUIRE(ldk >= std::max<int64_t>(s, 1), "ffc_eval_block: ldk must be >= s");
   FFC_REQUIRE(dtype == FFC_F64 || dtype == FFC_F32, "ffc_eval_block: bad dtype");
-  FFC_REQUIRE(precision == FFC_FP64, "ffc_eval_block: only FFC_FP64 is available in this build");
+  FFC_REQUIRE(precision == FFC_FP64 || precision == FFC_MIXED, "ffc_eval_block: bad precision");
   if (!kernel_ok(kernel, d)) return FFC_E_INVALID;
   FFC_REQUIRE(s == 0 || n == 0 || (Y_dev && rows_dev && X_dev && K_dev), "ffc_eval_block: null pointer");
   (void)center_dev;
@@ -209,7 +209,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   FFC_REQUIRE(r_max >= 0, "ffc_id: r_max must be >= 0");
   FFC_REQUIRE(std::min<int64_t>(r_max, std::min(s, n)) <= MAX_RANK, "ffc_id: rank cap above %d", MAX_RANK);
   FFC_REQUIRE(ldt >= std::max<int64_t>(r_max, 1), "ffc_id: ldt must be >= max(r_max, 1)");
-  FFC_REQUIRE(precision == FFC_FP64, "ffc_id: only FFC_FP64 is available in this build");
+  FFC_REQUIRE(precision == FFC_FP64 || precision == FFC_MIXED, "ffc_id: bad precision");
   FFC_REQUIRE(rank_host && r22_rel_host, "ffc_id: null output pointer");
   FFC_REQUIRE(n == 0 || (K_dev && skel_perm_dev && T_dev), "ffc_id: null pointer");
   cudaStream_t st = as_stream(stream);
@@ -218,7 +218,8 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   const int sm = std::max<int64_t>(s, 1) > 0 ? (int)std::max<int64_t>(s, 1) : 1;
   const int cap = cpqr_max_ctas(precision, sm);
   FFC_REQUIRE(cap > 0, "ffc_id: the QR kernel cannot be resident on this device");
-  const int g = std::min(cap, group_size(s, n, 16384));
+  FFC_REQUIRE(cpqr_min_group(n) <= cap, "ffc_id: n = %lld columns exceed what the QR can hold", (long long)n);
+  const int g = std::min(cap, std::max(cpqr_min_group(n), group_size(s, n, 4096)));
   const int rc_cap = std::max(kcap, 1);
   Arena ar;
   size_t bytes = 16 * 256 + round_up(sizeof(CpqrItem)) + round_up(sizeof(TrsmItem)) +
@@ -254,11 +255,12 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   FFC_CUDA(cudaMemcpyAsync(d_titem, &ti, sizeof(ti), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_assign, asg.data(), sizeof(CtaAssign) * g, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(barrier, 0, sizeof(unsigned), st));
+  FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * g, st));   // the QR's group accumulators start at zero
   FFC_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   FFC_CUDA(cudaMemsetAsync(rank, 0, sizeof(int32_t), st));
   ffc_status rc = launch_cpqr(precision, d_item, d_assign, g, (int)std::max<int64_t>(s, 1), st);
   if (rc != FFC_OK) return rc;
-  rc = launch_trsm_batched(precision, d_titem, 1, (n + 7) / 8, rc_cap, st);
+  rc = launch_trsm_batched(precision, d_titem, 1, trsm_tiles(n), rc_cap, st);
   if (rc != FFC_OK) return rc;
   int32_t hr = 0, hs = 0;
   double hr22 = 0.0;

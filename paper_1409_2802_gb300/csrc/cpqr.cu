@@ -1,4 +1,4 @@
-// Column-pivoted Householder QR and T = R11^-1 R12 (FP64 path).
+// Column-pivoted Householder QR and T = R11^-1 R12.
 //
 // Method: the ID of the sampled block comes from a rank-revealing QR
 // K' Pi = Q [R11 R12; 0 R22] (§2.1.3, ID theorem; Appendix A.1): the
@@ -6,23 +6,32 @@
 //
 // GPU design. A launch holds many independent blocks (work items). Each item
 // gets a group of g CTAs; CTA c of the group owns the contiguous column range
-// [n c / g, n (c+1) / g) for the whole factorisation. Columns never move: a
-// pivot is marked selected and its rows >= k are never read again, so R is
-// formed in place in the original column positions. One step k:
-//   1. every CTA reduces the g published (best norm, column, sum of squared
-//      norms) slots of the previous step -> the same pivot p and ||R22||_F on
-//      every CTA (deterministic reduction order);
-//   2. every CTA loads column p (rows k..s-1) from L2 and forms the LAPACK
-//      dlarfg reflector redundantly in shared memory;
-//   3. each warp applies the reflector to one owned column at a time, held
-//      in registers (R values per lane, s <= 32 R): one read and one write
-//      of the column per step; the residual norm is downdated as in LAPACK
-//      xLAQP2 and recomputed from the registers when cancellation makes the
-//      downdate unsafe;
-//   4. the CTA publishes its new local (best, column, sum) slot and joins a
-//      group barrier (global atomic counter, bounded spin).
-// Groups are co-resident (cooperative launch), so the barriers cannot
+// [n c / g, n (c+1) / g) (at most QR_NCOL_MAX columns) for the whole
+// factorisation, with their residual norms in shared memory. Columns never
+// move: a pivot is marked selected and its rows >= k are never read again,
+// so R is formed in place in the original column positions. One step k:
+//   1. every CTA folds its best (squared norm, column) key into the group's
+//      step accumulator with a 64-bit atomicMax and its sum of squared norms
+//      with an FP64 atomicAdd (both at L2), then joins the group barrier and
+//      reads back the winner and ||R22||^2;
+//   2. every CTA loads the pivot column (rows k..s-1) from L2 and forms the
+//      LAPACK dlarfg reflector redundantly in shared memory;
+//   3. each warp applies the reflector to its owned columns, two at a time:
+//      one pass over rows k..s-1 for v^T a, one for a -= tau (v^T a) v;
+//   4. one thread per column downdates the squared norm in FP64 (LAPACK
+//      xLAQP2, written with squares) and flags unsafe downdates, which a
+//      warp per flagged column recomputes.
+// GB300's FP64 pipe is ~70x narrower than FP32, so FP64 instructions stay
+// out of every full-warp path except the arithmetic that needs them (the
+// FP64 element type's own updates): keys compare as integers, the downdate
+// runs once per column, FP32 blocks use compensated FP32 sums of exact
+// squares for their column norms.
+// One cooperative launch per batch: CTA b walks its list of (item, rank in
+// the item's group) entries in increasing item order, so the lowest
+// unfinished item always has all of its CTAs and the group barriers cannot
 // deadlock; a wait that runs out sets FFC_E_TIMEOUT and ends the item.
+// Element type T: double (FFC_FP64) or float (FFC_MIXED: FP32 block,
+// reflectors and updates; FP64 norm downdating and triangular solve).
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -35,10 +44,27 @@ namespace {
 
 constexpr int QR_THREADS = 256;
 constexpr int QR_WARPS = QR_THREADS / 32;
+// Columns one CTA may own: their norms and flags live in shared memory.
+constexpr int QR_NCOL_MAX = 1024;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   return v;
 }
 
@@ -48,30 +74,13 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// better (value, column): larger value, then lower column
-__device__ __forceinline__ bool better(double v, int c, double bv, int bc) {
-  return v > bv || (v == bv && c < bc);
-}
-
-// Block-wide deterministic reduction of per-thread (best, col, sum).
-__device__ void block_reduce_slot(double& best, int& col, double& sum, double* sb, int* sc, double* ss) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    int oc = __shfl_xor_sync(0xffffffffu, col, o);
-    double os = __shfl_xor_sync(0xffffffffu, sum, o);
-    if (better(ob, oc, best, col)) { best = ob; col = oc; }
-    sum += os;
-  }
-  if (lane == 0) { sb[warp] = best; sc[warp] = col; ss[warp] = sum; }
-  __syncthreads();
-  best = sb[0]; col = sc[0]; sum = ss[0];
-  for (int w = 1; w < QR_WARPS; ++w) {
-    if (better(sb[w], sc[w], best, col)) { best = sb[w]; col = sc[w]; }
-    sum += ss[w];
-  }
-  __syncthreads();
+// Pivot key: the top 44 bits of the (non-negative) squared norm, then
+// 0xFFFFF - column, so the integer maximum picks the largest norm and, among
+// norms equal to 2^-32 relative, the lowest column. 0 = nothing selectable.
+__device__ __forceinline__ unsigned long long pivot_key(double nrm2, int col) {
+  if (!(nrm2 > 0.0)) return 0ull;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(nrm2);
+  return (b & ~0xFFFFFull) | (unsigned long long)(0xFFFFF - col);
 }
 
 // Thread 0 only: arrive and wait until `target` arrivals. false on timeout.
@@ -87,184 +96,428 @@ __device__ bool group_barrier(unsigned* ctr, unsigned target) {
   return true;
 }
 
-template <int R>
-__global__ void __launch_bounds__(QR_THREADS)
-cpqr_fp64_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ assign) {
-  extern __shared__ double vsh[];   // Householder vector, s entries
-  __shared__ double sb[QR_WARPS], ss[QR_WARPS];
-  __shared__ int sc[QR_WARPS];
-  __shared__ double sh_tau, sh_beta;
-  __shared__ int sh_fail;
+// Per-item, per-rank step slots, two in rotation (step k uses slots[k & 1]; a
+// CTA can only overwrite them two steps later, after every CTA has read them):
+// the CTA's pivot key and its sum of squared norms.
+struct StepSlot {
+  unsigned long long key;
+  double sum;
+};
 
-  const CtaAssign a = assign[blockIdx.x];
-  const CpqrItem it = items[a.item];
+// Exact, order-independent sum of non-negative doubles in integer arithmetic:
+// each value m 2^(e-1075) is aligned to the largest exponent emax as a 128-bit
+// fixed-point number (64 integer bits, 64 fraction bits) and added with carry.
+// Deterministic for any summation order, and free of FP64 instructions.
+struct Fix128 {
+  unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ int dbl_exponent(double x) {
+  const int e = (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
+  return e ? e : 1;
+}
+
+__device__ __forceinline__ void fix_add(Fix128& a, double x, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(b >> 52) & 0x7FF;
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (e) m |= 1ull << 52;
+  const int sh = emax - (e ? e : 1);
+  if (m == 0ull || sh >= 117) return;
+  const unsigned long long ih = sh < 64 ? (m >> sh) : 0ull;
+  const unsigned long long il = sh == 0 ? 0ull : (sh < 64 ? (m << (64 - sh)) : (m >> (sh - 64)));
+  a.lo += il;
+  a.hi += ih + (a.lo < il ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ void fix_add(Fix128& a, const Fix128& b) {
+  a.lo += b.lo;
+  a.hi += b.hi + (a.lo < b.lo ? 1ull : 0ull);
+}
+
+// value of a Fix128 aligned to emax (one thread; FP64 arithmetic)
+__device__ __forceinline__ double fix_value(const Fix128& a, int emax) {
+  return scalbn((double)a.hi, emax - 1075) + scalbn((double)a.lo, emax - 1075 - 64);
+}
+
+struct QrShared {
+  unsigned long long kw[QR_WARPS];
+  double psum[QR_THREADS];
+  float fw[QR_WARPS];
+  double dw[QR_WARPS];
+  unsigned long long key;
+  double sum, fro2, tau, beta;
+  int stop, status, n_rc;
+};
+
+// Exact square x*x = p + e (FMA), accumulated with a compensated sum (FP32 only).
+__device__ __forceinline__ void comp_add_square(float x, float& s, float& c) {
+  const float p = x * x;
+  const float e = fmaf(x, x, -p);
+  const float y = p - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+  c -= e;
+}
+
+// Squared norm of rows [i0, s) of a column, one warp; FP64 sums for FP64
+// data, compensated FP32 sums of exact squares for FP32 data.
+__device__ __forceinline__ double col_sumsq(const double* __restrict__ cj, int i0, int s, int lane) {
+  double a0 = 0.0, a1 = 0.0;
+  int i = i0 + lane;
+  for (; i + 32 < s; i += 64) {
+    const double x0 = cj[i], x1 = cj[i + 32];
+    a0 = fma(x0, x0, a0);
+    a1 = fma(x1, x1, a1);
+  }
+  if (i < s) { const double x0 = cj[i]; a0 = fma(x0, x0, a0); }
+  return warp_sum(a0 + a1);   // valid in every lane
+}
+
+// lane 0 of the warp returns the FP64 value of a compensated FP32 pair sum
+__device__ __forceinline__ double col_sumsq_f32(const float* __restrict__ cj, int i0, int s, int lane) {
+  float sm = 0.f, cm = 0.f;
+  for (int i = i0 + lane; i < s; i += 32) comp_add_square(cj[i], sm, cm);
+  float hi = sm, lo = -cm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float t = hi + h2;
+    const float bb = t - hi;
+    const float err = (hi - (t - bb)) + (h2 - bb);
+    hi = t;
+    lo = lo + l2 + err;
+  }
+  double r = 0.0;
+  if (lane == 0) r = (double)hi + (double)lo;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ double column_norm2(const T* __restrict__ cj, int i0, int s, int lane);
+
+template <>
+__device__ __forceinline__ double column_norm2<double>(const double* __restrict__ cj, int i0, int s, int lane) {
+  return col_sumsq(cj, i0, s, lane);
+}
+
+template <>
+__device__ __forceinline__ double column_norm2<float>(const float* __restrict__ cj, int i0, int s, int lane) {
+  return col_sumsq_f32(cj, i0, s, lane);   // meaningful in lane 0
+}
+
+// Applies H = I - tau v v^T (v in shared memory, rows k..s-1) to one column;
+// returns the updated entry in row k (in every lane).
+template <typename T>
+__device__ __forceinline__ T apply_reflector(T* __restrict__ cj, const T* __restrict__ vsh, T ttau, int k, int s,
+                                             int lane) {
+  T d0 = (T)0, d1 = (T)0, d2 = (T)0, d3 = (T)0;
+  int i = k + lane;
+  for (; i + 96 < s; i += 128) {
+    const T x0 = cj[i], x1 = cj[i + 32], x2 = cj[i + 64], x3 = cj[i + 96];
+    d0 = fma(vsh[i], x0, d0);
+    d1 = fma(vsh[i + 32], x1, d1);
+    d2 = fma(vsh[i + 64], x2, d2);
+    d3 = fma(vsh[i + 96], x3, d3);
+  }
+  for (; i < s; i += 32) d0 = fma(vsh[i], cj[i], d0);
+  const T tw = ttau * warp_sum((d0 + d1) + (d2 + d3));
+  T ak = (T)0;
+  for (int r = k + lane; r < s; r += 32) {
+    const T x = fma(-tw, vsh[r], cj[r]);
+    cj[r] = x;
+    if (r == k) ak = x;
+  }
+  return __shfl_sync(0xffffffffu, ak, 0);
+}
+
+// The same for two columns at once, so that their loads are in flight together.
+template <typename T>
+__device__ __forceinline__ void apply_reflector2(T* __restrict__ ca, T* __restrict__ cb, const T* __restrict__ vsh,
+                                                 T ttau, int k, int s, int lane, T& aka, T& akb) {
+  T a0 = (T)0, a1 = (T)0, b0 = (T)0, b1 = (T)0;
+  int i = k + lane;
+  for (; i + 32 < s; i += 64) {
+    const T xa0 = ca[i], xa1 = ca[i + 32], xb0 = cb[i], xb1 = cb[i + 32];
+    const T v0 = vsh[i], v1 = vsh[i + 32];
+    a0 = fma(v0, xa0, a0);
+    a1 = fma(v1, xa1, a1);
+    b0 = fma(v0, xb0, b0);
+    b1 = fma(v1, xb1, b1);
+  }
+  if (i < s) {
+    const T v0 = vsh[i];
+    a0 = fma(v0, ca[i], a0);
+    b0 = fma(v0, cb[i], b0);
+  }
+  const T twa = ttau * warp_sum(a0 + a1), twb = ttau * warp_sum(b0 + b1);
+  T ka = (T)0, kb = (T)0;
+  for (int r = k + lane; r < s; r += 32) {
+    const T v = vsh[r];
+    const T xa = fma(-twa, v, ca[r]), xb = fma(-twb, v, cb[r]);
+    ca[r] = xa;
+    cb[r] = xb;
+    if (r == k) { ka = xa; kb = xb; }
+  }
+  aka = __shfl_sync(0xffffffffu, ka, 0);
+  akb = __shfl_sync(0xffffffffu, kb, 0);
+}
+
+// CTA-wide: (max key over threads, FP64 sum of per-thread partials) into sh.key, sh.sum.
+__device__ void cta_reduce(unsigned long long key, double part, QrShared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  key = warp_max_u64(key);
+  if (lane == 0) sh.kw[warp] = key;
+  sh.psum[threadIdx.x] = part;
+  __syncthreads();
+  if (warp == 0) {
+    double v = 0.0;
+    for (int t = lane; t < QR_THREADS; t += 32) v += sh.psum[t];
+    v = warp_sum(v);
+    unsigned long long kk = lane < QR_WARPS ? sh.kw[lane] : 0ull;
+    kk = warp_max_u64(kk);
+    if (lane == 0) { sh.key = kk; sh.sum = v; }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
+                            double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
+                            int16_t* __restrict__ rcl, QrShared& sh) {
   const int s = it.s, n = it.n;
-  double* __restrict__ A = reinterpret_cast<double*>(it.A);
+  T* __restrict__ A = reinterpret_cast<T*>(it.A);
   const int64_t lda = it.lda;
   const int c0 = (int)((int64_t)n * a.rank / a.g), c1 = (int)((int64_t)n * (a.rank + 1) / a.g);
-  Slot* slots = reinterpret_cast<Slot*>(it.slots);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncols = c1 - c0;
+  StepSlot* slots = reinterpret_cast<StepSlot*>(it.slots);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
   const int kmax = min(it.r_max, min(s, n));
-  const double TOL3Z = 1.0536712127723509e-08;   // sqrt(2^-53)
-  if (threadIdx.x == 0) sh_fail = 0;
+  // LAPACK's recompute threshold sqrt(eps) for the precision the columns are
+  // stored in: the downdate subtracts a_kj^2, and a_kj is only as accurate as
+  // the stored data, so FP32 columns need sqrt(2^-24), not sqrt(2^-53)
+  const double TOL3Z = sizeof(T) == 4 ? 2.44140625e-04 : 1.0536712127723509e-08;
 
-  // initial residual norms of the owned columns
-  double best = -1.0, sum = 0.0;
-  int col = INT_MAX;
-  for (int j = c0 + warp; j < c1; j += QR_WARPS) {
-    const double* cj = A + (int64_t)j * lda;
-    double acc = 0.0;
-    for (int i = lane; i < s; i += 32) { double x = cj[i]; acc = fma(x, x, acc); }
-    acc = warp_sum(acc);
-    const double nr = sqrt(acc);
-    if (lane == 0) { it.vn1[j] = nr; it.vn2[j] = nr; it.selected[j] = 0; }
-    if (better(nr, j, best, col)) { best = nr; col = j; }
-    sum += acc;
+  // initial squared column norms, kept in shared memory for the whole factorisation
+  for (int j = warp; j < ncols; j += QR_WARPS) {
+    const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, 0, s, lane);
+    if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; sels[j] = 0; }
   }
-  if (lane != 0) sum = 0.0;   // one copy per warp
-  block_reduce_slot(best, col, sum, sb, sc, ss);
+  __syncthreads();
+  {
+    unsigned long long key = 0ull;
+    double part = 0.0;
+    for (int j = tid; j < ncols; j += QR_THREADS) {
+      const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+      key = kj > key ? kj : key;
+      part += vn1s[j];
+    }
+    cta_reduce(key, part, sh);
+  }
 
-  double fro2 = 0.0;
   int k = 0;
-  int status = FFC_OK;
   for (;; ++k) {
-    // publish this CTA's slot for step k and synchronise the group
-    if (a.g > 1) {
-      if (threadIdx.x == 0) {
-        Slot* sl = slots + (k & 1) * a.g + a.rank;
-        sl->best = best; sl->sum = sum; sl->col = col;
-        if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1))) sh_fail = 1;
+    // group winner and ||R22||^2 for step k: publish, barrier, reduce the
+    // group's slots (integer max of the keys, exact integer sum of the sums)
+    if (tid == 0) {
+      sh.stop = 0;
+      if (a.g > 1) {
+        StepSlot* sl = slots + (k & 1) * a.g + a.rank;
+        sl->key = sh.key;
+        sl->sum = sh.sum;
+        if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1))) {
+          sh.stop = 1;
+          sh.status = FFC_E_TIMEOUT;
+        }
       }
-      __syncthreads();
-      if (sh_fail) { status = FFC_E_TIMEOUT; break; }
-      // reduce the group's slots (same order on every CTA)
-      best = -1.0; col = INT_MAX; sum = 0.0;
-      for (int t = threadIdx.x; t < a.g; t += QR_THREADS) {
-        const Slot* sl = slots + (k & 1) * a.g + t;
-        double b = __ldcg(&sl->best), su = __ldcg(&sl->sum);
-        int c = __ldcg(&sl->col);
-        if (better(b, c, best, col)) { best = b; col = c; }
-        sum += su;
+    }
+    __syncthreads();
+    if (a.g > 1 && !sh.stop && warp == 0) {
+      const StepSlot* base = slots + (k & 1) * a.g;
+      unsigned long long kk = 0ull;
+      int emax = 1;
+      for (int t = lane; t < a.g; t += 32) {
+        const unsigned long long kt = __ldcg(&base[t].key);
+        kk = kt > kk ? kt : kk;
+        emax = max(emax, dbl_exponent(__ldcg(&base[t].sum)));
       }
-      block_reduce_slot(best, col, sum, sb, sc, ss);
+      kk = warp_max_u64(kk);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      Fix128 f = {0ull, 0ull};
+      for (int t = lane; t < a.g; t += 32) fix_add(f, __ldcg(&base[t].sum), emax);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        Fix128 g2;
+        g2.hi = __shfl_xor_sync(0xffffffffu, f.hi, o);
+        g2.lo = __shfl_xor_sync(0xffffffffu, f.lo, o);
+        fix_add(f, g2);
+      }
+      if (lane == 0) { sh.key = kk; sh.sum = fix_value(f, emax); }
     }
-    if (k == 0) fro2 = sum;
-    const double r22sq = sum;
-    if (it.tol > 0.0 && sqrt(r22sq) <= it.tol * sqrt(fro2)) break;
-    if (k >= kmax || col == INT_MAX || !(best > 0.0)) {
-      if (it.tol > 0.0) status = FFC_E_TOL_NOT_REACHED;
-      break;
+    __syncthreads();
+    if (tid == 0) {
+      if (!sh.stop) {
+        if (k == 0) sh.fro2 = sh.sum;
+        if (it.tol > 0.0 && sqrt(sh.sum) <= it.tol * sqrt(sh.fro2)) {
+          sh.stop = 1;
+          sh.status = FFC_OK;
+        } else if (k >= kmax || (sh.key >> 20) == 0ull) {
+          sh.stop = 1;
+          sh.status = it.tol > 0.0 ? FFC_E_TOL_NOT_REACHED : FFC_OK;
+        }
+      }
     }
-    const int p = col;
+    __syncthreads();
+    if (sh.stop) break;
+    const int p = 0xFFFFF - (int)(sh.key & 0xFFFFFull);
 
     // reflector from column p, rows k..s-1 (written by its owner before the barrier)
-    const double* cp = A + (int64_t)p * lda;
-    double part = 0.0;
-    for (int i = k + threadIdx.x; i < s; i += QR_THREADS) {
-      double x = __ldcg(cp + i);
+    const T* cp = A + (int64_t)p * lda;
+    T part = (T)0;
+    for (int i = k + tid; i < s; i += QR_THREADS) {
+      const T x = __ldcg(cp + i);
       vsh[i] = x;
       if (i > k) part = fma(x, x, part);
     }
     part = warp_sum(part);
-    if (lane == 0) sb[warp] = part;
+    if (lane == 0) {
+      if (sizeof(T) == 8) sh.dw[warp] = (double)part; else sh.fw[warp] = (float)part;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double xn2 = 0.0;
-      for (int w = 0; w < QR_WARPS; ++w) xn2 += sb[w];
-      const double alpha = vsh[k];
-      if (xn2 == 0.0) {
-        sh_tau = 0.0; sh_beta = alpha;
+    if (tid == 0) {
+      T xn2 = (T)0;
+      for (int w = 0; w < QR_WARPS; ++w) xn2 += sizeof(T) == 8 ? (T)sh.dw[w] : (T)sh.fw[w];
+      const T alpha = vsh[k];
+      if (xn2 == (T)0) {
+        sh.tau = 0.0;
+        sh.beta = (double)alpha;
       } else {
-        const double nrm = hypot(alpha, sqrt(xn2));
-        const double beta = alpha >= 0.0 ? -nrm : nrm;
-        sh_tau = (beta - alpha) / beta;
-        sh_beta = beta;
+        const T nrm = sqrt(fma(alpha, alpha, xn2));
+        const T beta = alpha >= (T)0 ? -nrm : nrm;
+        const T scale = (T)1 / (alpha - beta);
+        sh.tau = (double)((beta - alpha) / beta);
+        sh.beta = (double)beta;
+        vsh[k] = scale;   // read below, then replaced by 1
       }
+      if (a.rank == 0) { it.piv[k] = p; it.beta[k] = sh.beta; }
+      if (p >= c0 && p < c1) sels[p - c0] = 1;
     }
     __syncthreads();
-    const double tau = sh_tau, beta = sh_beta;
+    const double tau = sh.tau;
     if (tau != 0.0) {
-      const double den = vsh[k] - beta;
-      for (int i = k + 1 + threadIdx.x; i < s; i += QR_THREADS) vsh[i] = vsh[i] / den;
+      const T scale = vsh[k];
+      for (int i = k + 1 + tid; i < s; i += QR_THREADS) vsh[i] = vsh[i] * scale;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      vsh[k] = 1.0;
-      if (a.rank == 0) { it.piv[k] = p; it.beta[k] = beta; }
-      if (p >= c0 && p < c1) it.selected[p] = 1;
+    if (tid == 0) vsh[k] = (T)1;
+    if (tid == 0) sh.n_rc = 0;
+    __syncthreads();
+
+    // apply H_k to the owned free columns (two per warp at a time); row-k entries to aks
+    const T ttau = (T)tau;
+    for (int j0 = warp; j0 < ncols; j0 += 2 * QR_WARPS) {
+      const int jb = j0 + QR_WARPS;
+      const bool va = !sels[j0], vb = jb < ncols && !sels[jb];
+      T ka = (T)0, kb = (T)0;
+      if (tau != 0.0) {
+        if (va && vb) {
+          apply_reflector2(A + (int64_t)(c0 + j0) * lda, A + (int64_t)(c0 + jb) * lda, vsh, ttau, k, s, lane, ka, kb);
+        } else {
+          if (va) ka = apply_reflector(A + (int64_t)(c0 + j0) * lda, vsh, ttau, k, s, lane);
+          if (vb) kb = apply_reflector(A + (int64_t)(c0 + jb) * lda, vsh, ttau, k, s, lane);
+        }
+      } else {
+        if (va) ka = A[(int64_t)(c0 + j0) * lda + k];
+        if (vb) kb = A[(int64_t)(c0 + jb) * lda + k];
+      }
+      if (lane == 0) {
+        if (va) aks[j0] = ka;
+        if (vb) aks[jb] = kb;
+      }
     }
     __syncthreads();
 
-    // apply H_k to the owned free columns and downdate their norms
-    best = -1.0; col = INT_MAX; sum = 0.0;
-    for (int j = c0 + warp; j < c1; j += QR_WARPS) {
-      if (j == p || it.selected[j]) continue;
-      double* cj = A + (int64_t)j * lda;
-      double x[R];
-      double dot = 0.0;
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const int i = k + lane + 32 * c;
-        x[c] = (i < s) ? cj[i] : 0.0;
-        if (i < s) dot = fma(vsh[i], x[c], dot);
+    // FP64 downdate, one thread per column; unsafe ones go to the recompute list
+    for (int j = tid; j < ncols; j += QR_THREADS) {
+      if (sels[j]) continue;
+      const double akj = (double)aks[j];
+      const double rest = fma(-akj, akj, vn1s[j]);
+      if (rest <= TOL3Z * vn2s[j]) {
+        rcl[atomicAdd(&sh.n_rc, 1)] = (int16_t)j;
+      } else {
+        vn1s[j] = rest;
       }
-      if (tau != 0.0) {
-        dot = warp_sum(dot);
-        const double tw = tau * dot;
-#pragma unroll
-        for (int c = 0; c < R; ++c) {
-          const int i = k + lane + 32 * c;
-          if (i < s) { x[c] = fma(-tw, vsh[i], x[c]); cj[i] = x[c]; }
-        }
-      }
-      const double akj = __shfl_sync(0xffffffffu, x[0], 0);
-      double nr1 = it.vn1[j], nr2 = it.vn2[j];
-      if (nr1 != 0.0) {
-        double t = fabs(akj) / nr1;
-        t = fmax(0.0, (1.0 + t) * (1.0 - t));
-        const double q = nr1 / nr2;
-        const double t2 = t * q * q;
-        if (t2 <= TOL3Z) {
-          double acc = 0.0;
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            const int i = k + lane + 32 * c;
-            if (i > k && i < s) acc = fma(x[c], x[c], acc);
-          }
-          acc = warp_sum(acc);
-          nr1 = sqrt(acc);
-          nr2 = nr1;
-        } else {
-          nr1 = nr1 * sqrt(t);
-        }
-      }
-      if (lane == 0) { it.vn1[j] = nr1; it.vn2[j] = nr2; }
-      if (better(nr1, j, best, col)) { best = nr1; col = j; }
-      if (lane == 0) sum += nr1 * nr1;
     }
-    block_reduce_slot(best, col, sum, sb, sc, ss);
+    __syncthreads();
+    for (int q = warp; q < sh.n_rc; q += QR_WARPS) {
+      const int j = rcl[q];
+      const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, k + 1, s, lane);
+      if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
+    }
+    __syncthreads();
+    unsigned long long key = 0ull;
+    double psum = 0.0;
+    for (int j = tid; j < ncols; j += QR_THREADS) {
+      if (sels[j]) continue;
+      const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+      key = kj > key ? kj : key;
+      psum += vn1s[j];
+    }
+    cta_reduce(key, psum, sh);
   }
 
-  // status_out starts at FFC_OK; a timeout anywhere in the group wins
-  if (threadIdx.x == 0) {
-    if (status == FFC_E_TIMEOUT) atomicExch(it.status_out, (int)FFC_E_TIMEOUT);
+  // outputs; status_out starts at FFC_OK and a timeout anywhere in the group wins
+  if (tid == 0) {
+    if (sh.status == FFC_E_TIMEOUT) atomicExch(it.status_out, (int)FFC_E_TIMEOUT);
     if (a.rank == 0) {
       *it.rank_out = k;
-      *it.r22_out = fro2 > 0.0 ? sqrt(sum) / sqrt(fro2) : 0.0;
-      if (status != FFC_E_TIMEOUT) atomicCAS(it.status_out, (int)FFC_OK, status);
+      *it.r22_out = sh.fro2 > 0.0 ? sqrt(sh.sum) / sqrt(sh.fro2) : 0.0;
+      if (sh.status != FFC_E_TIMEOUT) atomicCAS(it.status_out, (int)FFC_OK, sh.status);
     }
+  }
+  // selected flags of the owned columns for the finalize step
+  for (int j = tid; j < ncols; j += QR_THREADS) it.selected[c0 + j] = sels[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS)
+cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
+            const int32_t* __restrict__ cta_off) {
+  // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries
+  // (QR_NCOL_MAX T), recompute list (QR_NCOL_MAX int16), selected flags
+  // (QR_NCOL_MAX bytes), Householder vector (s_max T)
+  extern __shared__ __align__(16) unsigned char qsm[];
+  double* vn1s = reinterpret_cast<double*>(qsm);
+  double* vn2s = vn1s + QR_NCOL_MAX;
+  T* aks = reinterpret_cast<T*>(vn2s + QR_NCOL_MAX);
+  int16_t* rcl = reinterpret_cast<int16_t*>(aks + QR_NCOL_MAX);
+  uint8_t* sels = reinterpret_cast<uint8_t*>(rcl + QR_NCOL_MAX);
+  T* vsh = reinterpret_cast<T*>(sels + QR_NCOL_MAX);
+  __shared__ QrShared sh;
+  const int e0 = cta_off ? cta_off[blockIdx.x] : (int)blockIdx.x;
+  const int e1 = cta_off ? cta_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+  for (int e = e0; e < e1; ++e) {
+    const CtaAssign a = entries[e];
+    const CpqrItem it = items[a.item];
+    if (threadIdx.x == 0) sh.status = FFC_OK;
+    __syncthreads();
+    factor_item<T>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh);
+    __syncthreads();
   }
 }
 
 // -------- finalize: skeleton order and dense R11 -----------------------------
 
+template <typename T>
 __global__ void __launch_bounds__(256)
 finalize_kernel(const TrsmItem* __restrict__ items) {
   __shared__ int wc[8];
   __shared__ int base;
   const TrsmItem it = items[blockIdx.x];
   const int r = *it.rank, n = it.n;
-  const double* A = reinterpret_cast<const double*>(it.A);
+  const T* A = reinterpret_cast<const T*>(it.A);
   for (int i = threadIdx.x; i < r; i += blockDim.x) it.skel_perm[i] = it.piv[i];
   if (threadIdx.x == 0) base = r;
   __syncthreads();
@@ -282,17 +535,18 @@ finalize_kernel(const TrsmItem* __restrict__ items) {
     if (threadIdx.x == 0) base += tot;
     __syncthreads();
   }
-  // R11 (r x r, row-major, ld r): R11[i][k] = A[i, piv[k]] above the diagonal, beta[k] on it
+  // R11 (r x r, row-major, ld r): R11[i][k] = A[i, piv[k]] above the diagonal, beta[k] on it;
+  // walked column by column so that the reads of A are contiguous
   for (int64_t e = threadIdx.x; e < (int64_t)r * r; e += blockDim.x) {
-    const int i = (int)(e / r), kk = (int)(e % r);
+    const int kk = (int)(e / r), i = (int)(e % r);
     double v = 0.0;
-    if (i < kk) v = A[i + (int64_t)it.piv[kk] * it.lda];
+    if (i < kk) v = (double)A[i + (int64_t)it.piv[kk] * it.lda];
     else if (i == kk) v = it.beta[kk];
-    it.R11[e] = v;
+    it.R11[(int64_t)i * r + kk] = v;
   }
 }
 
-// -------- T = R11^-1 R12: one warp per non-skeleton column --------------------
+// -------- T = R11^-1 R12 (FP64) -----------------------------------------------
 
 __device__ __forceinline__ int find_trsm_item(const TrsmItem* items, int n_items, int64_t g) {
   int lo = 0, hi = n_items - 1;
@@ -303,52 +557,75 @@ __device__ __forceinline__ int find_trsm_item(const TrsmItem* items, int n_items
   return lo;
 }
 
-template <int RT>
+// T = R11^-1 R12 for a tile of TS_COLS non-skeleton columns per CTA, FP64.
+// The tile (r x TS_COLS) lives in shared memory. Going up in diagonal blocks
+// of TS_NB rows: each warp solves the block for its columns by substitution
+// (lane = row, the solved entry broadcast by shuffle), then the CTA subtracts
+// R11[0:i0, block] * T[block, :] from the rows above (an FP64 GEMM slab with
+// R11 rows read contiguously).
+constexpr int TS_COLS = 16, TS_NB = 32;
+
+template <typename T>
 __global__ void __launch_bounds__(256)
 trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
+  extern __shared__ double Ts[];   // [r][TS_COLS]
   const int q = find_trsm_item(items, n_items, blockIdx.x);
   const TrsmItem it = items[q];
   const int r = *it.rank, n = it.n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = (int)(blockIdx.x - it.tile_begin) * 8 + warp;   // index among the n - r free columns
-  if (c >= n - r || r == 0) return;
-  const int j = it.skel_perm[r + c];
-  const double* A = reinterpret_cast<const double*>(it.A);
-  const double* b = A + (int64_t)j * it.lda;
+  const int c0 = (int)(blockIdx.x - it.tile_begin) * TS_COLS;
+  const int nc = min(TS_COLS, n - r - c0);
+  if (nc <= 0 || r == 0) return;
+  const T* A = reinterpret_cast<const T*>(it.A);
   const double* R11 = it.R11;
-  double t[RT];
-#pragma unroll
-  for (int u = 0; u < RT; ++u) {
-    const int i = lane + 32 * u;
-    t[u] = (i < r) ? b[i] : 0.0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < r * nc; e += blockDim.x) {
+    const int c = e / r, i = e % r;
+    Ts[i * TS_COLS + c] = (double)A[i + (int64_t)it.skel_perm[r + c0 + c] * it.lda];
   }
-  for (int i = r - 1; i >= 0; --i) {
-    const double* row = R11 + (int64_t)i * r;
-    double part = 0.0;
-#pragma unroll
-    for (int u = 0; u < RT; ++u) {
-      const int kk = lane + 32 * u;
-      if (kk > i && kk < r) part = fma(row[kk], t[u], part);
+  __syncthreads();
+  for (int i1 = r; i1 > 0;) {
+    const int i0 = max(0, i1 - TS_NB), nb = i1 - i0;
+    for (int c = warp; c < nc; c += 8) {
+      double t = lane < nb ? Ts[(i0 + lane) * TS_COLS + c] : 0.0;
+      for (int ii = nb - 1; ii >= 0; --ii) {
+        if (lane == ii) t = t / R11[(int64_t)(i0 + ii) * r + i0 + ii];
+        const double ti = __shfl_sync(0xffffffffu, t, ii);
+        if (lane < ii) t = fma(-R11[(int64_t)(i0 + lane) * r + i0 + ii], ti, t);
+      }
+      if (lane < nb) Ts[(i0 + lane) * TS_COLS + c] = t;
     }
-    part = warp_sum(part);
-    const int owner_u = i >> 5;
-#pragma unroll
-    for (int u = 0; u < RT; ++u)
-      if (u == owner_u && lane == (i & 31)) t[u] = (t[u] - part) / row[i];
+    __syncthreads();
+    for (int e = tid; e < i0 * nc; e += blockDim.x) {
+      const int j = e / nc, c = e % nc;
+      const double* row = R11 + (int64_t)j * r + i0;
+      double acc = Ts[j * TS_COLS + c];
+      for (int ii = 0; ii < nb; ++ii) acc = fma(-row[ii], Ts[(i0 + ii) * TS_COLS + c], acc);
+      Ts[j * TS_COLS + c] = acc;
+    }
+    __syncthreads();
+    i1 = i0;
   }
   const int64_t ldt = it.ldt > 0 ? it.ldt : r;
-  double* T = it.T + (int64_t)c * ldt;
-#pragma unroll
-  for (int u = 0; u < RT; ++u) {
-    const int i = lane + 32 * u;
-    if (i < r) T[i] = t[u];
+  for (int e = tid; e < r * nc; e += blockDim.x) {
+    const int c = e / r, i = e % r;
+    it.T[(int64_t)(c0 + c) * ldt + i] = Ts[i * TS_COLS + c];
   }
 }
 
-template <int R>
-ffc_status launch_cpqr_r(const CpqrItem* items, const CtaAssign* assign, int grid, int s_max, cudaStream_t st) {
-  const size_t smem = (size_t)s_max * sizeof(double);
-  auto kfn = cpqr_fp64_kernel<R>;
+template <typename T>
+size_t cpqr_smem_bytes(int s_max) {
+  return QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) + (size_t)std::max(s_max, 1) * sizeof(T);
+}
+
+template <typename T>
+ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const int32_t* cta_off, int grid,
+                         int s_max, cudaStream_t st) {
+  if (s_max > 2048) {
+    set_error("cpqr: s = %d exceeds the supported 2048 rows", s_max);
+    return FFC_E_INVALID;
+  }
+  const size_t smem = cpqr_smem_bytes<T>(s_max);
+  auto kfn = cpqr_kernel<T>;
   FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -360,79 +637,58 @@ ffc_status launch_cpqr_r(const CpqrItem* items, const CtaAssign* assign, int gri
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign));
+  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off));
   return FFC_OK;
 }
 
-template <int R>
-int max_ctas_r(int s_max) {
+template <typename T>
+int max_ctas_t(int s_max) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_fp64_kernel<R>, QR_THREADS,
-                                                (size_t)s_max * sizeof(double));
+  const size_t smem = cpqr_smem_bytes<T>(s_max);
+  cudaFuncSetAttribute(cpqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<T>, QR_THREADS, smem);
   return per_sm * sm_count();
 }
 
-template <int RT>
-ffc_status launch_trsm_rt(const TrsmItem* items, int n_items, int64_t total_tiles, cudaStream_t st) {
+template <typename T>
+ffc_status launch_trsm_t(const TrsmItem* items_dev, int n_items, int64_t total_tiles, int r_cap_max,
+                         cudaStream_t st) {
+  if (r_cap_max > 1024) {
+    set_error("trsm: rank cap %d exceeds 1024", r_cap_max);
+    return FFC_E_INVALID;
+  }
+  finalize_kernel<T><<<n_items, 256, 0, st>>>(items_dev);
+  FFC_CUDA(cudaGetLastError());
   if (total_tiles <= 0) return FFC_OK;
-  trsm_kernel<RT><<<(unsigned)total_tiles, 256, 0, st>>>(items, n_items);
+  const size_t smem = (size_t)std::max(r_cap_max, 1) * TS_COLS * sizeof(double);
+  FFC_CUDA(cudaFuncSetAttribute(trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  trsm_kernel<T><<<(unsigned)total_tiles, 256, smem, st>>>(items_dev, n_items);
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
 }
 
 }  // namespace
 
-int cpqr_rows_per_lane(int s_max) {
-  int R = 1;
-  while (32 * R < s_max) R *= 2;
-  return R;
-}
+int64_t trsm_tiles(int64_t n) { return (n + TS_COLS - 1) / TS_COLS; }
+
+int cpqr_min_group(int64_t n) { return (int)std::max<int64_t>(1, (n + QR_NCOL_MAX - 1) / QR_NCOL_MAX); }
 
 int cpqr_max_ctas(int precision, int s_max) {
-  (void)precision;
-  switch (cpqr_rows_per_lane(s_max)) {
-    case 1: return max_ctas_r<1>(s_max);
-    case 2: return max_ctas_r<2>(s_max);
-    case 4: return max_ctas_r<4>(s_max);
-    case 8: return max_ctas_r<8>(s_max);
-    case 16: return max_ctas_r<16>(s_max);
-    case 32: return max_ctas_r<32>(s_max);
-    default: return max_ctas_r<64>(s_max);
-  }
+  return precision == FFC_MIXED ? max_ctas_t<float>(s_max) : max_ctas_t<double>(s_max);
 }
 
-ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
-                       int s_max, cudaStream_t st) {
-  (void)precision;
+ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid, int s_max,
+                       cudaStream_t st, const int32_t* cta_off) {
   if (grid <= 0) return FFC_OK;
-  switch (cpqr_rows_per_lane(s_max)) {
-    case 1: return launch_cpqr_r<1>(items_dev, assign_dev, grid, s_max, st);
-    case 2: return launch_cpqr_r<2>(items_dev, assign_dev, grid, s_max, st);
-    case 4: return launch_cpqr_r<4>(items_dev, assign_dev, grid, s_max, st);
-    case 8: return launch_cpqr_r<8>(items_dev, assign_dev, grid, s_max, st);
-    case 16: return launch_cpqr_r<16>(items_dev, assign_dev, grid, s_max, st);
-    case 32: return launch_cpqr_r<32>(items_dev, assign_dev, grid, s_max, st);
-    case 64: return launch_cpqr_r<64>(items_dev, assign_dev, grid, s_max, st);
-    default:
-      set_error("cpqr: s = %d exceeds the supported 2048 rows", s_max);
-      return FFC_E_INVALID;
-  }
+  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st);
+  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st);
 }
 
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,
                                int r_cap_max, cudaStream_t st) {
-  (void)precision;
   if (n_items <= 0) return FFC_OK;
-  finalize_kernel<<<n_items, 256, 0, st>>>(items_dev);
-  FFC_CUDA(cudaGetLastError());
-  if (r_cap_max <= 32) return launch_trsm_rt<1>(items_dev, n_items, total_tiles, st);
-  if (r_cap_max <= 64) return launch_trsm_rt<2>(items_dev, n_items, total_tiles, st);
-  if (r_cap_max <= 128) return launch_trsm_rt<4>(items_dev, n_items, total_tiles, st);
-  if (r_cap_max <= 256) return launch_trsm_rt<8>(items_dev, n_items, total_tiles, st);
-  if (r_cap_max <= 512) return launch_trsm_rt<16>(items_dev, n_items, total_tiles, st);
-  if (r_cap_max <= 1024) return launch_trsm_rt<32>(items_dev, n_items, total_tiles, st);
-  set_error("trsm: rank cap %d exceeds 1024", r_cap_max);
-  return FFC_E_INVALID;
+  if (precision == FFC_MIXED) return launch_trsm_t<float>(items_dev, n_items, total_tiles, r_cap_max, st);
+  return launch_trsm_t<double>(items_dev, n_items, total_tiles, r_cap_max, st);
 }
 
 }  // namespace ffc

@@ -1,4 +1,4 @@
-// Kernel-block evaluation K'_ij = K(Y[rows_i], X_j), FP64 path.
+// Kernel-block evaluation K'_ij = K(Y[rows_i], X_j), SIMT path (FP64 and mixed).
 //
 // Kernels: Gaussian (§4.2, eq. gaussian_kernel), Laplace ||x-y||^(2-d)
 // (§4.3), polynomial (x.y/h + c)^p (§4.4). The block is the s x n matrix of
@@ -31,16 +31,20 @@ __device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// MODE 0: Gaussian, 1: Laplace (map), 2: polynomial, 3: Laplace min-distance pass
-template <typename TP, int MODE>
+// MODE 0: Gaussian, 1: Laplace (map), 2: polynomial, 3: Laplace min-distance pass.
+// CT: type of the staged coordinates and the distance / inner-product sums;
+// OT: type of the stored block. With CT = float and a centre given, the
+// coordinates are centred at it in FP64 before rounding to FP32, so the
+// differences keep the precision of the node's scale rather than of |x|.
+template <typename TP, int MODE, typename CT, typename OT>
 __global__ void __launch_bounds__(EVAL_THREADS)
-eval_fp64_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kernel kp,
-                 const EvalItem* __restrict__ items, int n_items, int64_t total_tiles, double* min_d2,
-                 int32_t* status) {
-  __shared__ double ys[TI][DC + 1];
-  __shared__ double xs[TJ][DC + 1];
+eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kernel kp,
+            const EvalItem* __restrict__ items, int n_items, int64_t total_tiles, double* min_d2) {
+  __shared__ CT ys[TI][DC + 1];
+  __shared__ CT xs[TJ][DC + 1];
   const int tid = threadIdx.x;
   const int r = tid % TI, cg = tid / TI;   // row in tile, column group (0..3)
+  constexpr bool centre = (sizeof(CT) == 4) && (MODE != 2);
   for (int64_t g = blockIdx.x; g < total_tiles; g += gridDim.x) {
     const int q = find_item(items, n_items, g);
     const EvalItem it = items[q];
@@ -49,33 +53,40 @@ eval_fp64_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_
     const int64_t local = g - it.tile_begin;
     const int64_t i0 = (local % rt) * TI, j0 = (local / rt) * TJ;
     if (i0 >= s || j0 >= n) continue;   // tile beyond the rows actually sampled
-    double acc[TJ / 4];
+    const double* ctr = (centre && it.center) ? it.center : nullptr;
+    CT acc[TJ / 4];
 #pragma unroll
-    for (int u = 0; u < TJ / 4; ++u) acc[u] = 0.0;
+    for (int u = 0; u < TJ / 4; ++u) acc[u] = (CT)0;
     for (int k0 = 0; k0 < d; k0 += DC) {
       const int kc = min(DC, d - k0);
       for (int e = tid; e < TI * DC; e += EVAL_THREADS) {
         int rr = e / DC, kk = e % DC;
         double v = 0.0;
-        if (i0 + rr < s && kk < kc) v = ld_point(Y + it.rows[i0 + rr] * (int64_t)d + k0 + kk);
-        ys[rr][kk] = v;
+        if (i0 + rr < s && kk < kc) {
+          v = ld_point(Y + it.rows[i0 + rr] * (int64_t)d + k0 + kk);
+          if (ctr) v -= ctr[k0 + kk];
+        }
+        ys[rr][kk] = (CT)v;
       }
       for (int e = tid; e < TJ * DC; e += EVAL_THREADS) {
         int cc = e / DC, kk = e % DC;
         double v = 0.0;
-        if (j0 + cc < n && kk < kc) v = ld_point(X + (it.x_begin + j0 + cc) * (int64_t)d + k0 + kk);
-        xs[cc][kk] = v;
+        if (j0 + cc < n && kk < kc) {
+          v = ld_point(X + (it.x_begin + j0 + cc) * (int64_t)d + k0 + kk);
+          if (ctr) v -= ctr[k0 + kk];
+        }
+        xs[cc][kk] = (CT)v;
       }
       __syncthreads();
       for (int kk = 0; kk < kc; ++kk) {
-        const double y = ys[r][kk];
+        const CT y = ys[r][kk];
 #pragma unroll
         for (int u = 0; u < TJ / 4; ++u) {
-          const double x = xs[cg + 4 * u][kk];
+          const CT x = xs[cg + 4 * u][kk];
           if (MODE == 2) {
             acc[u] = fma(y, x, acc[u]);
           } else {
-            const double df = y - x;
+            const CT df = y - x;
             acc[u] = fma(df, df, acc[u]);
           }
         }
@@ -87,31 +98,38 @@ eval_fp64_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_
       double mn = INFINITY;
 #pragma unroll
       for (int u = 0; u < TJ / 4; ++u)
-        if (i < s && j0 + cg + 4 * u < n) mn = fmin(mn, acc[u]);
+        if (i < s && j0 + cg + 4 * u < n) mn = fmin(mn, (double)acc[u]);
       for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
       if ((tid & 31) == 0 && mn < INFINITY) atomic_min_pos(&min_d2[q], mn);
       continue;
     }
     if (i >= s) continue;
-    double* K = reinterpret_cast<double*>(it.K);
-    const double two_h2 = 2.0 * kp.h * kp.h;
+    OT* K = reinterpret_cast<OT*>(it.K);
     const double ln_rmin = (MODE == 1) ? 0.5 * log(min_d2[q]) : 0.0;
 #pragma unroll
     for (int u = 0; u < TJ / 4; ++u) {
       const int64_t j = j0 + cg + 4 * u;
       if (j >= n) continue;
-      double v;
-      if (MODE == 0) {
-        v = exp(-acc[u] / two_h2);
-      } else if (MODE == 1) {
-        v = exp(-(double)(d - 2) * (0.5 * log(acc[u]) - ln_rmin));
+      OT v;
+      if (sizeof(CT) == 8) {
+        const double a = (double)acc[u];
+        if (MODE == 0) v = (OT)exp(-a / (2.0 * kp.h * kp.h));
+        else if (MODE == 1) v = (OT)exp(-(double)(d - 2) * (0.5 * log(a) - ln_rmin));
+        else v = (OT)pow(a / kp.h + kp.c, (double)kp.p);
       } else {
-        v = pow(acc[u] / kp.h + kp.c, (double)kp.p);
+        const float a = (float)acc[u];
+        if (MODE == 0) {
+          v = (OT)expf(-a * (float)(0.5 / (kp.h * kp.h)));
+        } else {
+          const float base = a * (float)(1.0 / kp.h) + (float)kp.c;
+          float pw = base;
+          for (int e = 1; e < kp.p; ++e) pw *= base;
+          v = (OT)pw;
+        }
       }
       K[i + j * it.ldk] = v;
     }
   }
-  (void)status;
 }
 
 __global__ void laplace_scale_kernel(const double* min_d2, int n_items, int d, double* log_scale,
@@ -132,23 +150,23 @@ __global__ void fill_kernel(double* p, int n, double v) {
   if (i < n) p[i] = v;
 }
 
-template <typename TP>
+template <typename TP, typename CT, typename OT>
 ffc_status launch_eval_t(ffc_kernel k, const TP* Y, const TP* X, int d, const EvalItem* items, int n_items,
-                         int64_t total_tiles, double* min_d2, double* log_scale, int32_t* status,
-                         cudaStream_t st) {
+                         int64_t total_tiles, double* min_d2, double* log_scale, int32_t* status, cudaStream_t st) {
   int grid = (int)std::min<int64_t>(total_tiles, (int64_t)sm_count() * 16);
   if (grid <= 0) return FFC_OK;
   if (k.kind == FFC_GAUSSIAN) {
-    eval_fp64_kernel<TP, 0><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2, status);
+    eval_kernel<TP, 0, CT, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
     if (log_scale) FFC_CUDA(cudaMemsetAsync(log_scale, 0, sizeof(double) * n_items, st));
   } else if (k.kind == FFC_POLYNOMIAL) {
-    eval_fp64_kernel<TP, 2><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2, status);
+    eval_kernel<TP, 2, CT, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
     if (log_scale) FFC_CUDA(cudaMemsetAsync(log_scale, 0, sizeof(double) * n_items, st));
   } else {
+    // Laplace: FP64 distances (the map amplifies their relative error (d-2)/2 times)
     fill_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(min_d2, n_items, INFINITY);
-    eval_fp64_kernel<TP, 3><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2, status);
+    eval_kernel<TP, 3, double, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
     laplace_scale_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(min_d2, n_items, d, log_scale, status);
-    eval_fp64_kernel<TP, 1><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2, status);
+    eval_kernel<TP, 1, double, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
   }
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
@@ -162,12 +180,18 @@ int64_t eval_row_tiles(int64_t s) { return (s + TI - 1) / TI; }
 ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
                        const EvalItem* items_dev, int n_items, int64_t total_tiles, double* min_d2,
                        double* log_scale, int32_t* status, cudaStream_t st) {
-  (void)precision;
+  if (precision == FFC_MIXED) {
+    if (dtype == FFC_F64)
+      return launch_eval_t<double, float, float>(k, (const double*)Y, (const double*)X, d, items_dev, n_items,
+                                                 total_tiles, min_d2, log_scale, status, st);
+    return launch_eval_t<float, float, float>(k, (const float*)Y, (const float*)X, d, items_dev, n_items,
+                                              total_tiles, min_d2, log_scale, status, st);
+  }
   if (dtype == FFC_F64)
-    return launch_eval_t<double>(k, (const double*)Y, (const double*)X, d, items_dev, n_items, total_tiles,
-                                 min_d2, log_scale, status, st);
-  return launch_eval_t<float>(k, (const float*)Y, (const float*)X, d, items_dev, n_items, total_tiles, min_d2,
-                              log_scale, status, st);
+    return launch_eval_t<double, double, double>(k, (const double*)Y, (const double*)X, d, items_dev, n_items,
+                                                 total_tiles, min_d2, log_scale, status, st);
+  return launch_eval_t<float, double, double>(k, (const float*)Y, (const float*)X, d, items_dev, n_items,
+                                              total_tiles, min_d2, log_scale, status, st);
 }
 
 }  // namespace ffc

@@ -149,9 +149,13 @@ ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, in
                        const EvalItem* items_dev, int n_items, int64_t total_tiles,
                        double* min_d2 /* n_items, Laplace */, double* log_scale /* n_items */,
                        int32_t* status /* n_items */, cudaStream_t st);
+// entries: per-CTA work lists (CTA b runs entries[cta_off[b] .. cta_off[b+1]) in order), or with
+// cta_off == NULL one entry per CTA.
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
-                       int s_max, cudaStream_t st);
+                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr);
 int cpqr_max_ctas(int precision, int s_max);
+int cpqr_min_group(int64_t n);   // fewest CTAs a group of n columns may have (per-CTA column cap)
+int64_t trsm_tiles(int64_t n);   // CTAs of the triangular solve for n columns
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,
                                int r_cap_max, cudaStream_t st);
 ffc_status launch_id_error(ffc_kernel k, const void* Y, int dtype, const int64_t* rows, int64_t m,

@@ -55,6 +55,8 @@ struct Scalars {
 __global__ void noalloc_setup_kernel(CpqrItem item, TrsmItem titem, int g, Scalars* sc, CpqrItem* d_item,
                                      TrsmItem* d_titem, CtaAssign* d_assign) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // the QR's group accumulators (start of the slot area) start at zero
+  if (t < 16) reinterpret_cast<unsigned long long*>(item.slots)[t] = 0ull;
   if (t == 0) {
     *d_item = item;
     *d_titem = titem;
@@ -114,7 +116,7 @@ extern "C" ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t 
   const int s_launch = (int)std::max<int64_t>(s, 1);
   const int cap = cpqr_max_ctas(precision, s_launch);
   FFC_REQUIRE(cap > 0, "ffc_id_noalloc: the QR kernel cannot be resident on this device");
-  const int g = std::min<int>({cap, (int)NA_MAX_GROUP, group_size_noalloc(s, n)});
+  const int g = std::min<int>({cap, (int)NA_MAX_GROUP, std::max(cpqr_min_group(n), group_size_noalloc(s, n))});
   const int rc_cap = (int)std::max<int64_t>(kcap, 1);
 
   CpqrItem* d_item = reinterpret_cast<CpqrItem*>(base + OFF_ITEM);
@@ -139,7 +141,7 @@ extern "C" ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t 
   FFC_CUDA(cudaGetLastError());
   rc = launch_cpqr(precision, d_item, d_assign, g, s_launch, st);
   if (rc != FFC_OK) return rc;
-  rc = launch_trsm_batched(precision, d_titem, 1, (n + 7) / 8, rc_cap, st);
+  rc = launch_trsm_batched(precision, d_titem, 1, trsm_tiles(n), rc_cap, st);
   if (rc != FFC_OK) return rc;
   Scalars hs = {};
   FFC_CUDA(cudaMemcpyAsync(&hs, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));

@@ -180,6 +180,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   const int d = R->d;
   const int r_cap_glob = P.s_max / 2;
   const int rcap_round = (int)std::min<int64_t>(s_nom, r_cap_glob);
+  const size_t esz = P.precision == FFC_MIXED ? sizeof(float) : sizeof(double);   // K' element size
   // per-item sizes
   std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W);
   std::vector<int> g(W);
@@ -199,22 +200,53 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   }
   const int cap = cpqr_max_ctas(P.precision, (int)s_nom);
   if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
-  const int64_t per_cta = std::max<int64_t>(16384, (elems + cap - 1) / cap);
+  // Group sizes: about 16K elements per CTA when everything fits in one
+  // co-resident launch; otherwise shrink the groups in proportion so the
+  // whole round is still one launch, with CTAs shared round-robin between
+  // items (each CTA walks its items in increasing order).
   int64_t G = 0;
+  for (int q = 0; q < W; ++q)
+    G += std::max<int64_t>(cpqr_min_group(R->count_h[items[q]]), group_size_tree(s_nom, R->count_h[items[q]], 4096));
+  const bool shared_ctas = G > cap;
+  const int64_t per_cta = shared_ctas ? std::max<int64_t>(1, elems / cap) : 16384;
+  G = 0;
   for (int q = 0; q < W; ++q) {
-    g[q] = std::min(cap, group_size_tree(s_nom, R->count_h[items[q]], per_cta));
+    const int64_t n = R->count_h[items[q]];
+    int64_t gq = shared_ctas ? (s_nom * n) / per_cta : group_size_tree(s_nom, n, 4096);
+    gq = std::max<int64_t>(1, std::min<int64_t>({gq, (int64_t)cap, std::max<int64_t>(1, n / 4)}));
+    gq = std::max<int64_t>(gq, cpqr_min_group(n));   // per-CTA column cap (<= cap for N <= 1.5M)
+    g[q] = (int)gq;
     goff[q] = G;
     G += g[q];
   }
-  // trsm tiles (8 columns per CTA)
+  const int grid = shared_ctas ? cap : (int)G;
+  // per-CTA entry lists, items in increasing order within each list
+  std::vector<std::vector<CtaAssign>> lists(grid);
+  {
+    int64_t ptr = 0;
+    for (int q = 0; q < W; ++q) {
+      for (int c = 0; c < g[q]; ++c) lists[(ptr + c) % grid].push_back(CtaAssign{q, c, g[q], 0});
+      ptr = (ptr + g[q]) % grid;
+    }
+  }
+  std::vector<int32_t> hoff(grid + 1, 0);
+  std::vector<CtaAssign> ha;
+  ha.reserve(G);
+  for (int b = 0; b < grid; ++b) {
+    hoff[b] = (int32_t)ha.size();
+    ha.insert(ha.end(), lists[b].begin(), lists[b].end());
+  }
+  hoff[grid] = (int32_t)ha.size();
+  // triangular-solve tiles
   std::vector<int64_t> ttiles(W);
   int64_t ttot = 0;
-  for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += (R->count_h[items[q]] + 7) / 8; }
+  for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += trsm_tiles(R->count_h[items[q]]); }
 
   const int64_t scratch_ctas = std::min<int64_t>(W, 2048);
   Layout L;
   const size_t o_si = L.add<SampleItem>(W), o_ei = L.add<EvalItem>(W), o_qi = L.add<CpqrItem>(W),
-               o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(G), o_sout = L.add<int64_t>(W),
+               o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(G), o_coff = L.add<int32_t>(grid + 1),
+               o_sout = L.add<int64_t>(W),
                o_fc = L.add<int64_t>(W), o_sst = L.add<int32_t>(W), o_md = L.add<double>(W), o_ls = L.add<double>(W),
                o_est = L.add<int32_t>(W), o_K = L.add<double>((size_t)s_nom * SN),
                o_piv = L.add<int32_t>((size_t)W * rcap_round), o_beta = L.add<double>((size_t)W * rcap_round),
@@ -239,6 +271,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   CpqrItem* d_qi = (CpqrItem*)(b + o_qi);
   TrsmItem* d_ti = (TrsmItem*)(b + o_ti);
   CtaAssign* d_as = (CtaAssign*)(b + o_as);
+  int32_t* d_coff = (int32_t*)(b + o_coff);
   int64_t* s_out = (int64_t*)(b + o_sout);
   int64_t* fc = (int64_t*)(b + o_fc);
   int32_t* sst = (int32_t*)(b + o_sst);
@@ -265,7 +298,6 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   std::vector<EvalItem> he(W);
   std::vector<CpqrItem> hq(W);
   std::vector<TrsmItem> ht(W);
-  std::vector<CtaAssign> ha(G);
   std::vector<int32_t> ho(W);
   for (int q = 0; q < W; ++q) {
     const int o = items[q];
@@ -276,31 +308,33 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     si.x_c = tree->centroid_dev + node * d; si.thr2 = 0.0; si.radius = tree->radius_dev + node; si.xi = P.xi;
     si.s = s_nom; si.stream_id = (uint64_t)node; si.rows = R->rows + R->rows_off_h[o];
     EvalItem& ei = he[q];
-    ei.rows = si.rows; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = K + koff[q]; ei.ldk = s_nom;
-    ei.center = nullptr; ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom);
+    ei.rows = si.rows; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
+    ei.center = P.precision == FFC_MIXED ? tree->centroid_dev + node * d : nullptr;
+    ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom);
     CpqrItem& qi = hq[q];
     qi = CpqrItem{};
-    qi.A = K + koff[q]; qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;
+    qi.A = (void*)((char*)K + esz * koff[q]); qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;
     qi.piv = piv + (size_t)q * rcap_round; qi.beta = beta + (size_t)q * rcap_round;
     qi.vn1 = vn1 + noff[q]; qi.vn2 = vn2 + noff[q]; qi.selected = sel + noff[q];
     qi.slots = slots + 2 * goff[q]; qi.barrier = bar + q; qi.rank_out = qrank + q; qi.r22_out = qr22 + q;
     qi.status_out = qst + q;
     TrsmItem& ti = ht[q];
     ti = TrsmItem{};
-    ti.A = K + koff[q]; ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = qrank + q; ti.piv = qi.piv; ti.beta = qi.beta;
+    ti.A = (void*)((char*)K + esz * koff[q]); ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = qrank + q; ti.piv = qi.piv; ti.beta = qi.beta;
     ti.selected = qi.selected; ti.skel_perm = R->skel + R->skel_off_h[o]; ti.R11 = R11 + r11off[q];
     ti.T = R->T + R->T_off_h[o]; ti.ldt = 0; ti.r_cap = (int32_t)std::min<int64_t>(n, rcap_round);
     ti.tile_begin = ttiles[q];
-    for (int c = 0; c < g[q]; ++c) ha[goff[q] + c] = CtaAssign{q, c, g[q], 0};
   }
   FFC_CUDA(cudaMemcpyAsync(d_si, hs.data(), sizeof(SampleItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_ei, he.data(), sizeof(EvalItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_qi, hq.data(), sizeof(CpqrItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_ti, ht.data(), sizeof(TrsmItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_as, ha.data(), sizeof(CtaAssign) * G, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_coff, hoff.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(oidx, ho.data(), sizeof(int32_t) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(est, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * W, st));
+  FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * G, st));   // the QR's group accumulators start at zero
   FFC_CUDA(cudaMemsetAsync(qst, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, st));
@@ -314,17 +348,10 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
   if (rc != FFC_OK) return rc;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
-  // cooperative QR launches: consecutive items whose groups fit together
-  int q0 = 0, qr_launches = 0;
-  while (q0 < W) {
-    int q1 = q0;
-    int64_t ctas = 0;
-    while (q1 < W && ctas + g[q1] <= cap) { ctas += g[q1]; ++q1; }
-    rc = launch_cpqr(P.precision, d_qi, d_as + goff[q0], (int)ctas, (int)s_nom, st);
-    if (rc != FFC_OK) return rc;
-    ++qr_launches;
-    q0 = q1;
-  }
+  // one cooperative QR launch for the whole round
+  rc = launch_cpqr(P.precision, d_qi, d_as, grid, (int)s_nom, st, d_coff);
+  if (rc != FFC_OK) return rc;
+  const int qr_launches = 1;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[3], st));
   rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
   if (rc != FFC_OK) return rc;
@@ -363,7 +390,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
       for (int k = 0; k < hr[q]; ++k) fl += 4.0 * (s - k) * (n - k);
       pf.qr_flops += fl;
       pf.eval_flops += per_coord * s * n * d;
-      pf.qr_bytes += 2.0 * s * n * sizeof(double);
+      pf.qr_bytes += 2.0 * s * n * (double)esz;
     }
   }
   return FFC_OK;
@@ -381,7 +408,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   FFC_REQUIRE(points_perm_dev && tree->begin_dev && tree->count_dev && tree->centroid_dev && tree->radius_dev,
               "ffc_compress_tree: null pointer");
   const ffc_params& P = *params;
-  FFC_REQUIRE(P.precision == FFC_FP64, "ffc_compress_tree: only FFC_FP64 is available in this build");
+  FFC_REQUIRE(P.precision == FFC_FP64 || P.precision == FFC_MIXED, "ffc_compress_tree: bad precision");
   FFC_REQUIRE(P.s0 >= 2 && P.s_max >= P.s0 && P.s_max <= 2048, "ffc_compress_tree: need 2 <= s0 <= s_max <= 2048");
   FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
