@@ -363,6 +363,8 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src):
         "kernel": kern, "bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
         "traffic": None, "peak_source": src, "dominant_phase": max(phase_ms, key=phase_ms.get),
         "phase_ms_per_step": {k: v / steps for k, v in phase_ms.items()},
+        "qr_ms_per_step_by_round": [round(v / steps, 3) for v in prof.get("qr_ms_round", [])],
+        "nodes_per_step_by_round": [int(v // steps) for v in prof.get("items_round", [])],
         "qr_flops_per_step": prof["qr_flops"] / steps, "qr_bytes_per_step": prof["qr_bytes"] / steps,
         "qr_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_frac": gbs / peaks.get("hbm_gbs", 1.0),
         "hbm_peak_source": peak_src,

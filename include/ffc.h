@@ -306,6 +306,8 @@ typedef struct {
   double qr_flops;      /* accumulated */
   double eval_flops;    /* accumulated */
   double qr_bytes;      /* one read + one write of every QR block, accumulated */
+  double qr_ms_round[8];      /* QR time of sample-size round i (s = s0 2^i), accumulated */
+  int64_t items_round[8];     /* nodes that round i processed, accumulated */
 } ffc_tree_profile;
 
 ffc_status ffc_tree_profile_enable(ffc_tree_result* result, int32_t enabled);

@@ -124,6 +124,10 @@ __device__ __forceinline__ void fix_add(Fix128& a, double x, int emax) {
   if (e) m |= 1ull << 52;
   const int sh = emax - (e ? e : 1);
   if (m == 0ull || sh >= 117) return;
+  if (sh < 0) {   // above the window: saturate (the caller sizes emax so this does not happen)
+    a.hi = ~0ull;
+    return;
+  }
   const unsigned long long ih = sh < 64 ? (m >> sh) : 0ull;
   const unsigned long long il = sh == 0 ? 0ull : (sh < 64 ? (m << (64 - sh)) : (m >> (sh - 64)));
   a.lo += il;
@@ -147,7 +151,7 @@ struct QrShared {
   double dw[QR_WARPS];
   unsigned long long key;
   double sum, fro2, tau, beta;
-  int stop, status, n_rc;
+  int stop, status, n_rc, emax;
 };
 
 // Exact square x*x = p + e (FMA), accumulated with a compensated sum (FP32 only).
@@ -224,11 +228,19 @@ __device__ __forceinline__ T apply_reflector(T* __restrict__ cj, const T* __rest
   for (; i < s; i += 32) d0 = fma(vsh[i], cj[i], d0);
   const T tw = ttau * warp_sum((d0 + d1) + (d2 + d3));
   T ak = (T)0;
-  for (int r = k + lane; r < s; r += 32) {
-    const T x = fma(-tw, vsh[r], cj[r]);
-    cj[r] = x;
-    if (r == k) ak = x;
+  int r = k + lane;
+  if (r < s) {
+    ak = fma(-tw, vsh[r], cj[r]);
+    cj[r] = ak;
   }
+  for (r += 32; r + 96 < s; r += 128) {
+    const T x0 = cj[r], x1 = cj[r + 32], x2 = cj[r + 64], x3 = cj[r + 96];
+    cj[r] = fma(-tw, vsh[r], x0);
+    cj[r + 32] = fma(-tw, vsh[r + 32], x1);
+    cj[r + 64] = fma(-tw, vsh[r + 64], x2);
+    cj[r + 96] = fma(-tw, vsh[r + 96], x3);
+  }
+  for (; r < s; r += 32) cj[r] = fma(-tw, vsh[r], cj[r]);
   return __shfl_sync(0xffffffffu, ak, 0);
 }
 
@@ -236,29 +248,47 @@ __device__ __forceinline__ T apply_reflector(T* __restrict__ cj, const T* __rest
 template <typename T>
 __device__ __forceinline__ void apply_reflector2(T* __restrict__ ca, T* __restrict__ cb, const T* __restrict__ vsh,
                                                  T ttau, int k, int s, int lane, T& aka, T& akb) {
-  T a0 = (T)0, a1 = (T)0, b0 = (T)0, b1 = (T)0;
+  // pass 1: 8 independent loads per lane per iteration keep enough of the
+  // (L2-resident) columns in flight
+  T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0, b0 = (T)0, b1 = (T)0, b2 = (T)0, b3 = (T)0;
   int i = k + lane;
-  for (; i + 32 < s; i += 64) {
-    const T xa0 = ca[i], xa1 = ca[i + 32], xb0 = cb[i], xb1 = cb[i + 32];
-    const T v0 = vsh[i], v1 = vsh[i + 32];
-    a0 = fma(v0, xa0, a0);
-    a1 = fma(v1, xa1, a1);
-    b0 = fma(v0, xb0, b0);
-    b1 = fma(v1, xb1, b1);
+  for (; i + 96 < s; i += 128) {
+    const T xa0 = ca[i], xa1 = ca[i + 32], xa2 = ca[i + 64], xa3 = ca[i + 96];
+    const T xb0 = cb[i], xb1 = cb[i + 32], xb2 = cb[i + 64], xb3 = cb[i + 96];
+    const T v0 = vsh[i], v1 = vsh[i + 32], v2 = vsh[i + 64], v3 = vsh[i + 96];
+    a0 = fma(v0, xa0, a0); a1 = fma(v1, xa1, a1); a2 = fma(v2, xa2, a2); a3 = fma(v3, xa3, a3);
+    b0 = fma(v0, xb0, b0); b1 = fma(v1, xb1, b1); b2 = fma(v2, xb2, b2); b3 = fma(v3, xb3, b3);
   }
-  if (i < s) {
+  for (; i < s; i += 32) {
     const T v0 = vsh[i];
     a0 = fma(v0, ca[i], a0);
     b0 = fma(v0, cb[i], b0);
   }
-  const T twa = ttau * warp_sum(a0 + a1), twb = ttau * warp_sum(b0 + b1);
+  const T twa = ttau * warp_sum((a0 + a1) + (a2 + a3)), twb = ttau * warp_sum((b0 + b1) + (b2 + b3));
+  // pass 2: row k first (its entry feeds the norm downdate), then the rest
+  // four rows per lane per iteration
   T ka = (T)0, kb = (T)0;
-  for (int r = k + lane; r < s; r += 32) {
+  int r = k + lane;
+  if (r < s) {
     const T v = vsh[r];
-    const T xa = fma(-twa, v, ca[r]), xb = fma(-twb, v, cb[r]);
-    ca[r] = xa;
-    cb[r] = xb;
-    if (r == k) { ka = xa; kb = xb; }
+    ka = fma(-twa, v, ca[r]);
+    kb = fma(-twb, v, cb[r]);
+    ca[r] = ka;
+    cb[r] = kb;
+  }
+  for (r += 32; r + 96 < s; r += 128) {
+    const T xa0 = ca[r], xa1 = ca[r + 32], xa2 = ca[r + 64], xa3 = ca[r + 96];
+    const T xb0 = cb[r], xb1 = cb[r + 32], xb2 = cb[r + 64], xb3 = cb[r + 96];
+    const T v0 = vsh[r], v1 = vsh[r + 32], v2 = vsh[r + 64], v3 = vsh[r + 96];
+    ca[r] = fma(-twa, v0, xa0); ca[r + 32] = fma(-twa, v1, xa1);
+    ca[r + 64] = fma(-twa, v2, xa2); ca[r + 96] = fma(-twa, v3, xa3);
+    cb[r] = fma(-twb, v0, xb0); cb[r + 32] = fma(-twb, v1, xb1);
+    cb[r + 64] = fma(-twb, v2, xb2); cb[r + 96] = fma(-twb, v3, xb3);
+  }
+  for (; r < s; r += 32) {
+    const T v = vsh[r];
+    ca[r] = fma(-twa, v, ca[r]);
+    cb[r] = fma(-twb, v, cb[r]);
   }
   aka = __shfl_sync(0xffffffffu, ka, 0);
   akb = __shfl_sync(0xffffffffu, kb, 0);
@@ -280,6 +310,82 @@ __device__ void cta_reduce(unsigned long long key, double part, QrShared& sh) {
     if (lane == 0) { sh.key = kk; sh.sum = v; }
   }
   __syncthreads();
+}
+
+// One warp updates NC adjacent owned columns per pass (those not selected):
+// v^T a for all of them, then a -= tau (v^T a) v, with NC loads per lane per
+// row chunk in flight; lane 0 then downdates each column's squared norm in
+// FP64 (the warp recomputes it when the downdate is unsafe) and folds the
+// column into the thread's pivot key and norm sum.
+template <typename T, int NC>
+__device__ __forceinline__ void update_columns(T* __restrict__ A, int64_t lda, int c0, int ncols,
+                                               const uint8_t* __restrict__ sels, const T* __restrict__ vsh, T ttau,
+                                               bool apply, int k, int s, int warp, int lane, double tol3z,
+                                               double* __restrict__ vn1s, double* __restrict__ vn2s,
+                                               unsigned long long& key, double& psum) {
+  for (int j0 = warp * NC; j0 < ncols; j0 += QR_WARPS * NC) {
+    bool va[NC];
+    T* base = A + (int64_t)(c0 + j0) * lda;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) va[c] = (j0 + c < ncols) && !sels[j0 + c];
+    T ak[NC];
+    if (apply) {
+      T acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = (T)0;
+#pragma unroll 2
+      for (int i = k + lane; i < s; i += 32) {
+        const T v = vsh[i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (va[c]) acc[c] = fma(v, base[(int64_t)c * lda + i], acc[c]);
+      }
+      T tw[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) tw[c] = ttau * warp_sum(acc[c]);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ak[c] = (T)0;
+#pragma unroll 2
+      for (int r = k + lane; r < s; r += 32) {
+        const T v = vsh[r];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (va[c]) {
+            const T x = fma(-tw[c], v, base[(int64_t)c * lda + r]);
+            base[(int64_t)c * lda + r] = x;
+            if (r == k) ak[c] = x;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ak[c] = __shfl_sync(0xffffffffu, ak[c], 0);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ak[c] = va[c] ? base[(int64_t)c * lda + k] : (T)0;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (!va[c]) continue;
+      const int j = j0 + c;
+      int unsafe = 0;
+      if (lane == 0) {
+        const double akj = (double)ak[c];
+        const double rest = fma(-akj, akj, vn1s[j]);
+        if (rest <= tol3z * vn2s[j]) unsafe = 1;
+        else vn1s[j] = rest;
+      }
+      unsafe = __shfl_sync(0xffffffffu, unsafe, 0);
+      if (unsafe) {
+        const double nr = column_norm2<T>(base + (int64_t)c * lda, k + 1, s, lane);
+        if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
+      }
+      if (lane == 0) {
+        const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+        key = kj > key ? kj : key;
+        psum += vn1s[j];
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -336,17 +442,24 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (a.g > 1 && !sh.stop && warp == 0) {
       const StepSlot* base = slots + (k & 1) * a.g;
       unsigned long long kk = 0ull;
-      int emax = 1;
+      // every later step's sums are below step 0's total, so its exponent
+      // (plus one) bounds them; 128-bit fixed point keeps ~2^-116 of it
+      int emax = sh.emax;
+      if (k == 0) {
+        emax = 1;
+        for (int t = lane; t < a.g; t += 32) emax = max(emax, dbl_exponent(__ldcg(&base[t].sum)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        emax = min(emax + 11, 2046);   // room for the sum of up to 2^11 slots
+        if (lane == 0) sh.emax = emax;
+      }
+      Fix128 f = {0ull, 0ull};
       for (int t = lane; t < a.g; t += 32) {
         const unsigned long long kt = __ldcg(&base[t].key);
         kk = kt > kk ? kt : kk;
-        emax = max(emax, dbl_exponent(__ldcg(&base[t].sum)));
+        fix_add(f, __ldcg(&base[t].sum), emax);
       }
       kk = warp_max_u64(kk);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-      Fix128 f = {0ull, 0ull};
-      for (int t = lane; t < a.g; t += 32) fix_add(f, __ldcg(&base[t].sum), emax);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         Fix128 g2;
@@ -415,8 +528,18 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (tid == 0) sh.n_rc = 0;
     __syncthreads();
 
-    // apply H_k to the owned free columns (two per warp at a time); row-k entries to aks
+    // apply H_k to the owned free columns: short columns NC at a time per
+    // warp (many loads in flight), long ones two at a time
     const T ttau = (T)tau;
+    unsigned long long key = 0ull;
+    double psum = 0.0;
+    if (s - k <= 256) {
+      update_columns<T, 8>(A, lda, c0, ncols, sels, vsh, ttau, tau != 0.0, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
+                           psum);
+    } else if (s - k <= 1024) {
+      update_columns<T, 4>(A, lda, c0, ncols, sels, vsh, ttau, tau != 0.0, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
+                           psum);
+    } else {
     for (int j0 = warp; j0 < ncols; j0 += 2 * QR_WARPS) {
       const int jb = j0 + QR_WARPS;
       const bool va = !sels[j0], vb = jb < ncols && !sels[jb];
@@ -432,38 +555,33 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
         if (va) ka = A[(int64_t)(c0 + j0) * lda + k];
         if (vb) kb = A[(int64_t)(c0 + jb) * lda + k];
       }
-      if (lane == 0) {
-        if (va) aks[j0] = ka;
-        if (vb) aks[jb] = kb;
+      // FP64 norm downdate of the two columns by lane 0, right behind their
+      // update (its latency hides behind the other warps' column passes); the
+      // whole warp recomputes a norm when the downdate is unsafe
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const bool valid = h == 0 ? va : vb;
+        if (!valid) continue;
+        const int j = h == 0 ? j0 : jb;
+        int unsafe = 0;
+        if (lane == 0) {
+          const double akj = (double)(h == 0 ? ka : kb);
+          const double rest = fma(-akj, akj, vn1s[j]);
+          if (rest <= TOL3Z * vn2s[j]) unsafe = 1;
+          else vn1s[j] = rest;
+        }
+        unsafe = __shfl_sync(0xffffffffu, unsafe, 0);
+        if (unsafe) {
+          const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, k + 1, s, lane);
+          if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
+        }
+        if (lane == 0) {
+          const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+          key = kj > key ? kj : key;
+          psum += vn1s[j];
+        }
       }
     }
-    __syncthreads();
-
-    // FP64 downdate, one thread per column; unsafe ones go to the recompute list
-    for (int j = tid; j < ncols; j += QR_THREADS) {
-      if (sels[j]) continue;
-      const double akj = (double)aks[j];
-      const double rest = fma(-akj, akj, vn1s[j]);
-      if (rest <= TOL3Z * vn2s[j]) {
-        rcl[atomicAdd(&sh.n_rc, 1)] = (int16_t)j;
-      } else {
-        vn1s[j] = rest;
-      }
-    }
-    __syncthreads();
-    for (int q = warp; q < sh.n_rc; q += QR_WARPS) {
-      const int j = rcl[q];
-      const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, k + 1, s, lane);
-      if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
-    }
-    __syncthreads();
-    unsigned long long key = 0ull;
-    double psum = 0.0;
-    for (int j = tid; j < ncols; j += QR_THREADS) {
-      if (sels[j]) continue;
-      const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
-      key = kj > key ? kj : key;
-      psum += vn1s[j];
     }
     cta_reduce(key, psum, sh);
   }
@@ -517,6 +635,7 @@ finalize_kernel(const TrsmItem* __restrict__ items) {
   __shared__ int base;
   const TrsmItem it = items[blockIdx.x];
   const int r = *it.rank, n = it.n;
+  if (r < 0) return;   // attempt that will be redone with a larger sample
   const T* A = reinterpret_cast<const T*>(it.A);
   for (int i = threadIdx.x; i < r; i += blockDim.x) it.skel_perm[i] = it.piv[i];
   if (threadIdx.x == 0) base = r;
@@ -574,7 +693,7 @@ trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
   const int r = *it.rank, n = it.n;
   const int c0 = (int)(blockIdx.x - it.tile_begin) * TS_COLS;
   const int nc = min(TS_COLS, n - r - c0);
-  if (nc <= 0 || r == 0) return;
+  if (nc <= 0 || r <= 0) return;
   const T* A = reinterpret_cast<const T*>(it.A);
   const double* R11 = it.R11;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -78,6 +78,17 @@ __global__ void patch_kernel(int W, const int64_t* s_out, int64_t s_nom, int r_c
   qr[q].r_max = cap;
 }
 
+// Rank handed to the finalize / triangular solve: -1 (skip) for an attempt
+// that will be redone with a doubled sample, whose T would be discarded.
+__global__ void gate_kernel(int W, int64_t s_nom, int s_max, const int64_t* s_out, const int32_t* st_qr,
+                            const int32_t* qr_rank, int32_t* trsm_rank) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W) return;
+  const int64_t s_eff = s_out[q];
+  const bool again = st_qr[q] == FFC_E_TOL_NOT_REACHED && s_eff > 0 && !(s_eff < s_nom) && 2 * s_nom <= s_max;
+  trsm_rank[q] = again ? -1 : qr_rank[q];
+}
+
 __global__ void epilogue_kernel(int W, const int32_t* out_idx, int64_t s_nom, int s_max, const int64_t* s_out,
                                 const int64_t* fc, const double* lsc, const int32_t* st_eval,
                                 const int32_t* qr_rank, const double* qr_r22, const int32_t* st_qr,
@@ -254,7 +265,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
                o_slots = L.add<Slot>(2 * G), o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
                o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
-               o_oidx = L.add<int32_t>(W);
+               o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W);
   if (L.off > R->ws_bytes) {
     if (R->ws) {
       FFC_CUDA(cudaStreamSynchronize(st));
@@ -293,6 +304,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   int32_t* scratch = (int32_t*)(b + o_scr);
   int32_t* flags = (int32_t*)(b + o_flag);
   int32_t* oidx = (int32_t*)(b + o_oidx);
+  int32_t* trank = (int32_t*)(b + o_trank);
 
   std::vector<SampleItem> hs(W);
   std::vector<EvalItem> he(W);
@@ -320,7 +332,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     qi.status_out = qst + q;
     TrsmItem& ti = ht[q];
     ti = TrsmItem{};
-    ti.A = (void*)((char*)K + esz * koff[q]); ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = qrank + q; ti.piv = qi.piv; ti.beta = qi.beta;
+    ti.A = (void*)((char*)K + esz * koff[q]); ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = trank + q; ti.piv = qi.piv; ti.beta = qi.beta;
     ti.selected = qi.selected; ti.skel_perm = R->skel + R->skel_off_h[o]; ti.R11 = R11 + r11off[q];
     ti.T = R->T + R->T_off_h[o]; ti.ldt = 0; ti.r_cap = (int32_t)std::min<int64_t>(n, rcap_round);
     ti.tile_begin = ttiles[q];
@@ -353,6 +365,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   if (rc != FFC_OK) return rc;
   const int qr_launches = 1;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[3], st));
+  gate_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_nom, P.s_max, s_out, qst, qrank, trank);
   rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
   if (rc != FFC_OK) return rc;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[4], st));
@@ -378,9 +391,14 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
       float ms = 0.f;
       FFC_CUDA(cudaEventElapsedTime(&ms, R->ev[ph], R->ev[ph + 1]));
       pf.ms[ph] += ms;
+      if (ph == 2) {
+        const int rd = std::min(R->rounds, 7);
+        pf.qr_ms_round[rd] += ms;
+        pf.items_round[rd] += W;
+      }
     }
     const int eval_launches = P.kernel.kind == FFC_LAPLACE ? 4 : 1;
-    pf.launches += 1 + 1 + eval_launches + qr_launches + 2 + 1;
+    pf.launches += 1 + 1 + eval_launches + qr_launches + 1 + 2 + 1;
     pf.qr_launches += qr_launches;
     pf.rounds += 1;
     const double per_coord = P.kernel.kind == FFC_POLYNOMIAL ? 2.0 : 3.0;

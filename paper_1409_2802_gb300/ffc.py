@@ -72,7 +72,8 @@ class c_tree_profile(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int32), ("calls", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("launches", ctypes.c_int64), ("qr_launches", ctypes.c_int64),
                 ("ms", ctypes.c_double * 5), ("qr_flops", ctypes.c_double), ("eval_flops", ctypes.c_double),
-                ("qr_bytes", ctypes.c_double)]
+                ("qr_bytes", ctypes.c_double), ("qr_ms_round", ctypes.c_double * 8),
+                ("items_round", ctypes.c_int64 * 8)]
 
 
 @dataclass(frozen=True)
@@ -289,7 +290,7 @@ class TreeResult:
         _check(lib().ffc_tree_profile_get(self.handle, ctypes.byref(p)))
         return {"calls": p.calls, "rounds": p.rounds, "launches": p.launches, "qr_launches": p.qr_launches,
                 "ms": dict(zip(PROFILE_PHASES, list(p.ms))), "qr_flops": p.qr_flops, "eval_flops": p.eval_flops,
-                "qr_bytes": p.qr_bytes}
+                "qr_bytes": p.qr_bytes, "qr_ms_round": list(p.qr_ms_round), "items_round": list(p.items_round)}
 
     def close(self):
         if self.handle and self.handle.value:
