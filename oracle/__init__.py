@@ -22,6 +22,8 @@ checks it against the paper by eye: no blocking, no fusion, no reordering.
 * ``tree``      PCA median-split binary tree and per-node far-field geometry.
 * ``compress``  per-node sampled ID over all tree levels >= 2.
 * ``mlp``       FP64 forward/backward/Adam of the learned sampling proposal.
+* ``proposal``  its features, weighted sampling without replacement and the
+                leverage-score training targets (§3, §4.1.3).
 
 Parity pins live in ``tests/test_oracle_*.py``. Parts without an independent
 pin are marked "parity unpinned" in their module docstring.

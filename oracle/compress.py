@@ -15,6 +15,11 @@ whole far field (the sampler returned fewer than s rows) the QR may run to
 min(s, n) steps; the rank never exceeds
 r_cap = s_max / 2. A node that cannot meet the tolerance within those limits
 keeps its last ID with status TOL_NOT_REACHED.
+
+With a learned ``Proposal`` the s rows of each attempt come from
+``proposal.propose_from_mask`` (pool of c*s uniform rows, network weights,
+weighted draw without replacement) instead of the uniform sampler; the rows
+of a larger attempt are drawn afresh and need not extend the smaller one.
 """
 from __future__ import annotations
 
@@ -24,6 +29,7 @@ import numpy as np
 
 from .interp import interpolative_decomposition
 from .kernels import Kernel, kernel_block
+from .proposal import POOL_FACTOR, propose_from_mask
 from .sampling import far_field_mask, sample_uniform_from_mask
 
 STATUS_OK = 0
@@ -46,11 +52,19 @@ class NodeResult:
     attempts: list = field(default_factory=list)   # s values tried
 
 
+@dataclass
+class Proposal:
+    theta32: np.ndarray     # FP32 master parameters of the proposal network
+    proj: np.ndarray        # 8 x d random directions of the projection features
+    c: int = POOL_FACTOR    # pool size factor
+
+
 def rank_cap(s_eff: int, n: int, all_rows: bool, r_cap: int) -> int:
     return min(n, r_cap, s_eff if all_rows else s_eff // 2)
 
 
-def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048, xi=1.0):
+def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048, xi=1.0,
+                  proposal: Proposal | None = None):
     b, c = int(tree.begin[node]), int(tree.count[node])
     far = far_field_mask(Xp, tree.centroid[node], tree.radius[node], xi, b, b + c)
     far_count = int(far.sum())
@@ -60,7 +74,11 @@ def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048,
     tried = []
     while True:
         tried.append(s)
-        rows = sample_uniform_from_mask(far, s, seed, node)
+        if proposal is None:
+            rows = sample_uniform_from_mask(far, s, seed, node)
+        else:
+            rows = propose_from_mask(far, Xp, s, seed, node, tree.centroid[node], tree.radius[node],
+                                     kernel, proposal.proj, proposal.theta32, proposal.c)
         if rows.size == 0:
             return NodeResult(node, 0, rows, 0, np.arange(c), np.zeros((0, c)), 0.0, 0.0,
                               far_count, STATUS_FARFIELD_EMPTY, tried)
@@ -80,8 +98,9 @@ def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048,
 
 
 def compress_tree(Xp, tree, kernel: Kernel, tol, seed=0, min_level=2, s0=128, s_max=2048,
-                  nodes=None):
+                  nodes=None, proposal: Proposal | None = None):
     """Compress every node at level >= min_level (or just ``nodes``)."""
     if nodes is None:
         nodes = [i for i in range(tree.n_nodes) if tree.level[i] >= min_level]
-    return [compress_node(Xp, tree, i, kernel, tol, seed, s0, s_max) for i in nodes]
+    return [compress_node(Xp, tree, i, kernel, tol, seed, s0, s_max, proposal=proposal)
+            for i in nodes]

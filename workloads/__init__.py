@@ -20,6 +20,13 @@ Workloads (sizes of the paper's experiments, §4.1, and of the benchmark suite):
                         dimensions by a random orthonormal map plus small
                         Gaussian noise (§4.1.1 "Low intrinsic dimension").
 * ``standard_normal``   the §4.1.1 "Normal" data set.
+
+Random inputs of the learned proposal (drawn here so both sides share them):
+
+* ``mlp_init``          initial FP32 parameters of the 12-128-128-1 network
+                        (flat vector; layout in ``MLP_LAYOUT``).
+* ``projections``       the 8 random directions g_k ~ N(0, I/d) of the
+                        projection features.
 """
 from __future__ import annotations
 
@@ -32,6 +39,10 @@ __all__ = [
     "low_intrinsic",
     "standard_normal",
     "random_matrix",
+    "mlp_init",
+    "projections",
+    "MLP_LAYOUT",
+    "MLP_N_PARAMS",
 ]
 
 
@@ -105,3 +116,39 @@ def random_matrix(m: int, n: int, seed: int = 0, decay: float | None = None) -> 
     V, _ = np.linalg.qr(g.standard_normal((n, k)))
     sv = decay ** np.arange(k, dtype=np.float64)
     return (U * sv) @ V.T
+
+
+# Flat parameter vector of the proposal network (FP32 master copy): name ->
+# (offset, shape). Matrices are row-major with W[j, k] = weight from input k
+# to unit j. This is an interface shared by value, not code: each side of the
+# project spells it out itself.
+MLP_LAYOUT = {
+    "W1": (0, (128, 12)),
+    "b1": (1536, (128,)),
+    "W2": (1664, (128, 128)),
+    "b2": (18048, (128,)),
+    "w3": (18176, (128,)),
+    "b3": (18304, (1,)),
+}
+MLP_N_PARAMS = 18305
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """He-normal initial weights (std sqrt(2 / fan_in)), zero biases, as float32.
+
+    The output layer uses std sqrt(1 / fan_in) / 4 so that the initial logits
+    are small and the initial proposal is close to uniform.
+    """
+    g = _rng(seed)
+    theta = np.zeros(MLP_N_PARAMS, dtype=np.float64)
+    for name, fan_in, std in (("W1", 12, np.sqrt(2.0 / 12)), ("W2", 128, np.sqrt(2.0 / 128)),
+                              ("w3", 128, 0.25 * np.sqrt(1.0 / 128))):
+        off, shape = MLP_LAYOUT[name]
+        size = int(np.prod(shape))
+        theta[off:off + size] = std * g.standard_normal(size)
+    return theta.astype(np.float32)
+
+
+def projections(d: int, seed: int = 0, k: int = 8) -> np.ndarray:
+    """k x d matrix of independent N(0, 1/d) entries (float64)."""
+    return np.ascontiguousarray(_rng(seed).standard_normal((k, d)) / np.sqrt(d))
