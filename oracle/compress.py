@@ -17,9 +17,9 @@ r_cap = s_max / 2. A node that cannot meet the tolerance within those limits
 keeps its last ID with status TOL_NOT_REACHED.
 
 With a learned ``Proposal`` the s rows of each attempt come from
-``proposal.propose_from_mask`` (pool of c*s uniform rows, network weights,
-weighted draw without replacement) instead of the uniform sampler; the rows
-of a larger attempt are drawn afresh and need not extend the smaller one.
+``proposal.propose_from_mask`` (network weights over the candidate pool,
+weighted draw without replacement) instead of the uniform sampler; its keys
+do not depend on s, so a larger attempt extends the smaller one as well.
 """
 from __future__ import annotations
 
@@ -29,7 +29,7 @@ import numpy as np
 
 from .interp import interpolative_decomposition
 from .kernels import Kernel, kernel_block
-from .proposal import POOL_FACTOR, propose_from_mask
+from .proposal import propose_from_mask
 from .sampling import far_field_mask, sample_uniform_from_mask
 
 STATUS_OK = 0
@@ -56,7 +56,7 @@ class NodeResult:
 class Proposal:
     theta32: np.ndarray     # FP32 master parameters of the proposal network
     proj: np.ndarray        # 8 x d random directions of the projection features
-    c: int = POOL_FACTOR    # pool size factor
+    pool_rows: int = 0      # 0: the whole far field; else a uniform pool of this size
 
 
 def rank_cap(s_eff: int, n: int, all_rows: bool, r_cap: int) -> int:
@@ -78,7 +78,7 @@ def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048,
             rows = sample_uniform_from_mask(far, s, seed, node)
         else:
             rows = propose_from_mask(far, Xp, s, seed, node, tree.centroid[node], tree.radius[node],
-                                     kernel, proposal.proj, proposal.theta32, proposal.c)
+                                     kernel, proposal.proj, proposal.theta32, proposal.pool_rows)
         if rows.size == 0:
             return NodeResult(node, 0, rows, 0, np.arange(c), np.zeros((0, c)), 0.0, 0.0,
                               far_count, STATUS_FARFIELD_EMPTY, tried)

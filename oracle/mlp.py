@@ -12,10 +12,12 @@ Network: x (12) -> z1 = W1 x + b1 -> h1 = GELU(z1) (128)
                 -> z2 = W2 h1 + b2 -> h2 = GELU(z2) (128) -> o = w3 . h2 + b3.
 GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 (Hendrycks & Gimpel, erf form).
 
-Loss of a batch of B nodes (rows of node b in [off[b], off[b+1])), targets t
-with sum_i t_i = 1 per node (the leverage scores divided by the rank):
-    L = (1/B) sum_b  -sum_{i in b} t_i log softmax_b(o)_i,
+Loss of a batch of B nodes (rows of node b in [off[b], off[b+1])), targets
+t >= 0 normalised per node to the distribution q_i = t_i / sum_{j in b} t_j
+(for leverage scores, q = l / r):
+    L = (1/B) sum_b  -sum_{i in b} q_i log softmax_b(o)_i,
 the cross-entropy between the target distribution and the network's proposal.
+A node whose targets sum to zero contributes nothing.
 
 Adam: Kingma & Ba (ICLR 2015), Algorithm 1, with bias-corrected moments.
 
@@ -109,7 +111,7 @@ def backward(theta, cache, g_o):
 
 
 def softmax_cross_entropy(o, t, node_off):
-    """Mean over nodes of -sum t_i log softmax(o)_i, and dL/do."""
+    """Mean over nodes of -sum q_i log softmax(o)_i (q = t / sum t per node), and dL/do."""
     o = np.asarray(o, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
     B = len(node_off) - 1
@@ -123,9 +125,12 @@ def softmax_cross_entropy(o, t, node_off):
         mx = np.max(ob)
         lse = mx + np.log(np.sum(np.exp(ob - mx)))
         pb = np.exp(ob - lse)
-        tb = t[a:e]
-        loss += -np.sum(tb * (ob - lse))
-        g_o[a:e] = pb * np.sum(tb) - tb
+        tsum = np.sum(t[a:e])
+        if tsum <= 0.0:
+            continue
+        qb = t[a:e] / tsum
+        loss += -np.sum(qb * (ob - lse))
+        g_o[a:e] = pb - qb
     return loss / B, g_o / B
 
 

@@ -20,18 +20,20 @@ Readings used here (the paper has no learned part):
     f3 = rho / h  (h = 1 for the Laplace kernel, which has no length scale)
     f4..f11 = <g_k, delta> / rho for the 8 given random directions g_k.
   A node with rho = 0 uses rho = 1.
-* Proposal for a sample of s rows: a candidate pool of c*s far-field rows is
-  drawn with the uniform sampler (the same stream, so the pool is the
-  uniform sample of size c*s; c = 8). The network gives a logit o_i per pool
-  row; weights w_i = exp(o_i - max o); mixed weights
-  w'_i = 0.9 w_i / mean(w) + 0.1, so every row keeps at least a tenth of its
-  uniform weight. s rows are drawn without replacement with probabilities
-  proportional to w' by Efraimidis & Spirakis' keys (Inf. Proc. Letters 97,
-  2006): key_i = ln(u_i) / w'_i, u_i the unit double of draw i (i = pool
-  position) of stream (seed, stream_id, DOMAIN_WEIGHTED_KEYS); the s largest
-  keys win, ties to the lower pool position, rows in decreasing key order.
-  When the pool holds at most s rows (the far field is that small) all of it
-  is the sample.
+* Candidate pool: the whole far field in ascending index order (the
+  leverage distribution of §3 is over every row of the block, and the rows
+  that carry it are few: a uniform pool of a few times s rows misses them).
+  Optionally a uniform pool of a fixed number P of rows (the uniform sampler
+  with s = P, same stream) bounds the cost. The pool does not depend on s.
+* The network gives a logit o_i per pool row; weights w_i = exp(o_i - max o);
+  mixed weights w'_i = 0.9 w_i / mean(w) + 0.1, so every row keeps at least
+  a tenth of its uniform weight. s rows are drawn without replacement with
+  probabilities proportional to w' by Efraimidis & Spirakis' keys (Inf. Proc.
+  Letters 97, 2006): key_i = ln(u_i) / w'_i, u_i the unit double of draw i
+  (i = pool position) of stream (seed, stream_id, DOMAIN_WEIGHTED_KEYS); the
+  s largest keys win, ties to the lower pool position, rows in decreasing key
+  order (the whole pool when it has at most s rows). The keys do not depend
+  on s, so a size-s sample is a prefix of the size-2s sample.
 * Training targets: the leverage scores of the node's full far-field block K
   (m x n) with respect to its epsilon-rank r (§4.1.3 step 1), divided by r
   so they sum to one over the node's rows (sum_i l_i = r, §3).
@@ -47,7 +49,6 @@ from .sampling import far_field_mask, sample_uniform_from_mask
 from .spectral import eps_rank, row_leverage_scores
 
 N_FEATURES = 12
-POOL_FACTOR = 8
 UNIFORM_MIX = 0.1
 
 
@@ -108,11 +109,18 @@ def weighted_select(pool_rows, o, s, seed, stream_id):
     return pool_rows[order[:min(int(s), P)]], keys
 
 
+def candidate_pool(far, seed, stream_id, pool_rows: int = 0):
+    """The whole far field (pool_rows = 0) or a uniform pool of pool_rows rows."""
+    if pool_rows <= 0:
+        return np.flatnonzero(far)
+    return sample_uniform_from_mask(far, int(pool_rows), seed, stream_id)
+
+
 def propose_from_mask(far, Y, s, seed, stream_id, x_c, rho, kernel: Kernel, proj, theta32,
-                      c: int = POOL_FACTOR):
+                      pool_rows: int = 0):
     """Learned proposal of s far-field rows (far = boolean far-field mask)."""
-    pool = sample_uniform_from_mask(far, c * int(s), seed, stream_id)
-    if pool.size <= s:
+    pool = candidate_pool(far, seed, stream_id, pool_rows)
+    if pool.size == 0:
         return pool
     F = features(Y, pool, x_c, rho, kernel, proj)
     o, _ = forward(half_weights(theta32), F)
@@ -121,11 +129,11 @@ def propose_from_mask(far, Y, s, seed, stream_id, x_c, rho, kernel: Kernel, proj
 
 
 def propose_rows(Y, s, seed, stream_id, x_c, radius, kernel: Kernel, proj, theta32, xi=1.0,
-                 ex_begin=0, ex_end=0, c: int = POOL_FACTOR):
+                 ex_begin=0, ex_end=0, pool_rows: int = 0):
     """Returns (rows, far_count) for the far field of (x_c, radius, xi) minus [ex_begin, ex_end)."""
     far = far_field_mask(Y, x_c, radius, xi, ex_begin, ex_end)
-    return propose_from_mask(far, Y, s, seed, stream_id, x_c, radius, kernel, proj, theta32, c), \
-        int(far.sum())
+    return propose_from_mask(far, Y, s, seed, stream_id, x_c, radius, kernel, proj, theta32,
+                             pool_rows), int(far.sum())
 
 
 def leverage_targets(K, eps):

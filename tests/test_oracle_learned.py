@@ -162,23 +162,24 @@ def _node_setup(seed=0):
     return Y, x_c, rho
 
 
-def test_proposal_draws_from_the_uniform_pool():
+def test_proposal_draws_from_the_pool_and_is_prefix_consistent():
     Y, x_c, rho = _node_setup()
     proj = workloads.projections(8, seed=1)
     theta = workloads.mlp_init(seed=2)
+    kern = Kernel(GAUSSIAN, h=2.0)
     far = far_field_mask(Y, x_c, rho, 1.0, 0, 64)
-    for s in (16, 128):
-        rows = proposal.propose_from_mask(far, Y, s, 3, 17, x_c, rho, Kernel(GAUSSIAN, h=2.0),
-                                          proj, theta)
-        pool = sample_uniform_from_mask(far, 8 * s, 3, 17)
-        assert far.sum() > 8 * s
-        assert rows.size == s and np.unique(rows).size == s
-        assert set(rows) <= set(pool)
-        assert np.all(far[rows])
+    for pool_rows in (0, 600):
+        pool = proposal.candidate_pool(far, 3, 17, pool_rows)
+        assert pool.size == (far.sum() if pool_rows == 0 else 600)
+        big = proposal.propose_from_mask(far, Y, 256, 3, 17, x_c, rho, kern, proj, theta, pool_rows)
+        for s in (16, 128):
+            rows = proposal.propose_from_mask(far, Y, s, 3, 17, x_c, rho, kern, proj, theta, pool_rows)
+            assert rows.size == s and np.unique(rows).size == s
+            assert set(rows) <= set(pool) and np.all(far[rows])
+            assert list(rows) == list(big[:s])          # keys do not depend on s
     # a far field no larger than s is taken whole
     small = np.zeros_like(far); small[np.flatnonzero(far)[:20]] = True
-    rows = proposal.propose_from_mask(small, Y, 32, 3, 17, x_c, rho, Kernel(GAUSSIAN, h=2.0),
-                                      proj, theta)
+    rows = proposal.propose_from_mask(small, Y, 32, 3, 17, x_c, rho, kern, proj, theta)
     assert sorted(rows) == list(np.flatnonzero(small))
 
 
