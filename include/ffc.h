@@ -236,17 +236,28 @@ typedef struct {
   double tol;          /* relative tolerance on ||R22||_F / ||K'||_F (1e-6) */
   double xi;           /* far-field separation (1.0) */
   uint64_t seed;       /* sampling seed; the stream id of a node is its heap id */
+  int32_t sampler;     /* ffc_sampler: FFC_SAMPLE_UNIFORM (0) or FFC_SAMPLE_LEARNED (1) */
+  int32_t pool_rows;   /* learned: 0 = the whole far field is the candidate pool, else a
+                          uniform pool of pool_rows >= s_max rows */
+  const double* proj_dev;   /* learned: 8 x d random directions of the projection features */
+  const float* mlp_dev;     /* learned: FFC_MLP_PARAMS network parameters (FP32 master copy) */
 } ffc_params;
+
+/* Row sampler of a tree compression: uniform (§2.2) or the learned proposal
+ * (ffc_propose_rows, same seed and stream id). */
+typedef enum { FFC_SAMPLE_UNIFORM = 0, FFC_SAMPLE_LEARNED = 1 } ffc_sampler;
 
 /*
  * Compression of every node at level >= min_level. For a node with
  * centroid x_c, radius rho and positions [b, b + n): far field = positions
  * outside [b, b + n) at distance >= xi rho from x_c; s = s0; sample s rows
- * (ffc_sample_rows with stream_id = node id), evaluate K' (s x n), run the
- * pivoted QR in tolerance mode for at most s/2 steps (min(s, n) when the
- * sample already holds the whole far field); if the tolerance is not met,
- * double s (the sample is prefix consistent) while s <= s_max; else keep the
- * last ID with status FFC_E_TOL_NOT_REACHED.
+ * (ffc_sample_rows with stream_id = node id, or ffc_propose_rows with the
+ * learned sampler), evaluate K' (s x n), run the pivoted QR in tolerance mode
+ * for at most s/2 steps (min(s, n) when the sample already holds the whole
+ * far field); if the tolerance is not met, double s (both samplers are
+ * prefix consistent: the learned draw's keys do not depend on s, so its
+ * s_max best rows are drawn once) while s <= s_max; else keep the last ID
+ * with status FFC_E_TOL_NOT_REACHED.
  */
 typedef struct ffc_tree_result ffc_tree_result;   /* opaque; owns device memory */
 
@@ -313,6 +324,116 @@ typedef struct {
 ffc_status ffc_tree_profile_enable(ffc_tree_result* result, int32_t enabled);
 ffc_status ffc_tree_profile_reset(ffc_tree_result* result);
 ffc_status ffc_tree_profile_get(const ffc_tree_result* result, ffc_tree_profile* out);
+
+
+/* ------------------------------------------------------------------------
+ * Learned row proposal and its training (the leverage-score distribution of
+ * §3, Def. "Statistical Leverage", and §4.1.3 "Leverage sampling", predicted
+ * by a small network from per-row features).
+ *
+ * Network: 12 features -> 128 (GELU) -> 128 (GELU) -> 1 logit, GELU(z) =
+ * z Phi(z) (erf form). Parameters: an FP32 master vector of FFC_MLP_PARAMS
+ * floats, matrices row-major with W[j][k] = weight from input k to unit j:
+ *   W1 128x12 at 0 | b1 128 at 1536 | W2 128x128 at 1664 | b2 128 at 18048 |
+ *   w3 128 at 18176 | b3 at 18304.
+ * Every pass uses the parameters rounded to FP16 (nearest even) and
+ * accumulates in FP32.
+ */
+#define FFC_MLP_PARAMS 18305
+#define FFC_N_FEATURES 12
+#define FFC_MAX_DRAW 8192    /* largest number of rows of one weighted draw */
+
+/*
+ * ffc_features - the 12 features of targets Y[rows[i]] for a node with
+ * centroid x_c and radius rho (rho <= 0 is taken as 1), with
+ * delta = y - x_c, r = ||delta||:
+ *   f0 = r / rho
+ *   f1 = K(y, x_c) normalised: Gaussian exp(-r^2/(2h^2)); Laplace
+ *        (rho/r)^(d-2); polynomial (y.x_c/h + c)^p / (||y|| ||x_c||/h + c)^p
+ *   f2 = ||y|| / rho;  f3 = rho / h (h = 1 for Laplace)
+ *   f4..f11 = <g_k, delta> / rho for the rows g_k of proj_dev (8 x d FP64).
+ * The O(d) sums run in FP32 on coordinates rounded to FP32, the per-row
+ * transforms in FP64; stored as FP32 row-major R x 12 in feats_dev.
+ * rows_dev: R indices in [0, M). x_c_dev: d doubles. Asynchronous.
+ */
+ffc_status ffc_features(ffc_kernel k, const void* Y_dev, int32_t dtype, int64_t M, int32_t d,
+                        const int64_t* rows_dev, int64_t R, const double* x_c_dev, double radius,
+                        const double* proj_dev, float* feats_dev, void* stream);
+
+/* ffc_mlp_forward - logits_dev[i] (R floats) of the feature rows feats_dev
+ * (R x 12 FP32). Asynchronous. */
+ffc_status ffc_mlp_forward(const float* params_dev, const float* feats_dev, int64_t R, float* logits_dev,
+                           void* stream);
+
+/*
+ * ffc_sample_weighted - s of the P pool rows without replacement, row i with
+ * weight w'_i = 0.9 w_i / mean(w) + 0.1, w_i = exp(o_i - max o), by the keys
+ * of Efraimidis & Spirakis (2006): key_i = ln(u_i) / w'_i with u_i the unit
+ * double (top 53 bits + 1/2) * 2^-53 of draw i of stream (seed, stream_id,
+ * domain 2) (Philox layout as in ffc_sample_rows). The min(s, P) largest keys
+ * win (ties: lower pool position) and are written in decreasing key order,
+ * so a size-s draw is a prefix of the size-2s draw. Keys are formed in FP64
+ * from the FP32 logits. min(s, P) <= FFC_MAX_DRAW; any P.
+ * rows_dev: capacity min(s, P). Asynchronous.
+ */
+ffc_status ffc_sample_weighted(const int64_t* pool_dev, const float* logits_dev, int64_t P, int64_t s,
+                               uint64_t seed, uint64_t stream_id, int64_t* rows_dev, void* stream);
+
+/*
+ * ffc_propose_rows - the learned proposal of s far-field rows: the candidate
+ * pool is the whole far field in ascending order (pool_rows = 0; the
+ * leverage distribution the network predicts is over every row) or a
+ * uniform pool of pool_rows rows (ffc_sample_rows with s = pool_rows, same
+ * seed and stream); then the features and logits of every pool row and
+ * ffc_sample_weighted over the pool. s <= FFC_MAX_DRAW. rows_dev: capacity
+ * s. Outputs and statuses as in ffc_sample_rows (FFC_E_FARFIELD_TOO_SMALL
+ * when fewer than s rows exist). Synchronises.
+ */
+ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int64_t M, int32_t d,
+                            const double* x_c_dev, double radius, double xi, int64_t ex_begin, int64_t ex_end,
+                            const double* proj_dev, const float* params_dev, int64_t pool_rows, int64_t s,
+                            uint64_t seed, uint64_t stream_id, int64_t* rows_dev, int64_t* s_out_host,
+                            int64_t* far_count_host, void* stream);
+
+/*
+ * ffc_mlp_loss_grad - loss and gradient of the proposal on a batch of nodes:
+ * rows [node_off[b], node_off[b+1]) of feats_dev / targets_dev belong to
+ * node b (node_off_dev: n_nodes + 1 int64 on the device, non-decreasing,
+ * node_off[0] = 0, node_off[n_nodes] = R). Targets t >= 0 (FP64, e.g. the
+ * leverage scores of ffc_leverage) are normalised per node, q = t / sum_b t,
+ * and the loss is the mean cross-entropy between q and the proposal:
+ *   L = (1/B) sum_b -sum_{i in b} q_i log softmax_b(o)_i
+ * (a node whose targets sum to zero contributes nothing).
+ * grad_dev: FFC_MLP_PARAMS floats (dL/dparameter, taken at the FP16 values).
+ * loss_host: L (FP64 sums). Deterministic for a fixed device. Synchronises.
+ */
+ffc_status ffc_mlp_loss_grad(const float* params_dev, const float* feats_dev, const double* targets_dev,
+                             const int64_t* node_off_dev, int32_t n_nodes, int64_t R, double* loss_host,
+                             float* grad_dev, void* stream);
+
+/*
+ * ffc_adam_step - one Adam update (Kingma & Ba 2015, Algorithm 1; step >= 1)
+ * of n FP32 parameters with FP32 moments m, v, computed in FP64:
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Asynchronous.
+ */
+ffc_status ffc_adam_step(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int64_t n,
+                         int64_t step, double lr, double beta1, double beta2, double eps, void* stream);
+
+/*
+ * ffc_leverage - statistical leverage scores of the rows of K (m x n FP64,
+ * column-major, ld ldk) with respect to rank r (§3, Def. "Statistical
+ * Leverage"): l_i = ||U_r(i, :)||^2 for K = U Sigma V^T. r = r_fixed when
+ * r_fixed > 0, else the eps-rank (number of sigma_k >= eps sigma_1, §4.1.3).
+ * Route: G = K^T K, Jacobi eigen-decomposition of G, l_i = ||K(i,:) V_r
+ * Sigma_r^-1||^2, all FP64; singular values below about 1e-7 sigma_1 are not
+ * resolved. lev_dev: m doubles (sum = r). sigma_dev: n doubles, decreasing.
+ * n <= 1024. FFC_E_TOL_NOT_REACHED (soft) if Jacobi did not converge.
+ * Synchronises.
+ */
+ffc_status ffc_leverage(const double* K_dev, int64_t m, int64_t n, int64_t ldk, double eps, int64_t r_fixed,
+                        double* lev_dev, double* sigma_dev, int64_t* rank_host, void* stream);
 
 #ifdef __cplusplus
 }

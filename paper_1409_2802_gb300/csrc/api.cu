@@ -59,7 +59,7 @@ struct Arena {
 
 static size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-static bool kernel_ok(const ffc_kernel& k, int d) {
+bool kernel_ok(const ffc_kernel& k, int d) {
   if (k.kind == FFC_GAUSSIAN) {
     if (!(k.h > 0.0)) { set_error("Gaussian bandwidth h must be > 0"); return false; }
   } else if (k.kind == FFC_LAPLACE) {

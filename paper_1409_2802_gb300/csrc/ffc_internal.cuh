@@ -136,6 +136,38 @@ struct TrsmItem {
   int64_t tile_begin;   // prefix of 8-column tiles over items
 };
 
+struct FeatItem {
+  const int64_t* rows;   // candidate indices into Y
+  const int64_t* count;  // device count of valid rows, or NULL: all cap rows are valid
+  int64_t cap;           // output rows reserved for the item
+  int64_t out_begin;     // first output row (flat over items)
+  const double* x_c;     // node centroid (d)
+  const double* radius;  // device radius or NULL
+  double radius_host;    // used when radius == NULL
+};
+
+struct FarItem {
+  int64_t M;             // candidates [0, M)
+  int64_t ex_begin, ex_end;
+  const double* x_c;     // d doubles
+  const double* radius;  // device radius or NULL
+  double radius_host;
+  double xi;
+  int64_t* list;         // capacity M: far candidates, ascending
+  int64_t* count;        // device: |list|
+};
+
+struct SelectItem {
+  const int64_t* pool;   // candidate rows
+  const int64_t* count;  // device pool size, or NULL: P
+  int64_t P;
+  const float* logits;   // network output per pool row
+  int64_t s;             // rows wanted
+  uint64_t stream_id;
+  int64_t* rows_out;     // capacity s
+  int64_t* s_out;        // device: rows written (may be NULL)
+};
+
 // ----------------------------------------------------------------------------
 // launchers (implemented in the .cu files; all enqueue on `st`)
 
@@ -166,8 +198,27 @@ ffc_status launch_build_tree(const void* points, int dtype, int64_t N, int d, in
                              const int64_t* begin_host, const int64_t* count_host, const int64_t* begin_dev,
                              const int64_t* count_dev, double* centroid, double* radius, cudaStream_t st);
 
+ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const FeatItem* items_dev, int n_items,
+                           int64_t total, const double* proj, float* out, cudaStream_t st);
+ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st);
+// keep_max: largest min(s, P) over the items (<= 8192); any pool size P
+ffc_status launch_select(const SelectItem* items_dev, int n_items, int64_t keep_max, uint64_t seed, cudaStream_t st);
+// far-field lists of n_items nodes; tile_cnt: n_items x far_list_tiles(M_max) int64 workspace
+ffc_status launch_far_lists(const void* Y, int dtype, int d, const FarItem* items_dev, int n_items, int64_t M_max,
+                            int64_t* tile_cnt, cudaStream_t st);
+int64_t far_list_tiles(int64_t M);
+ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const double* targets,
+                                const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,
+                                double* loss_part, float* part, int n_part, float* grad, cudaStream_t st);
+int mlp_backward_grid(int64_t R);
+ffc_status launch_adam(float* theta, const float* g, float* m, float* v, int64_t n, int64_t step, double lr,
+                       double b1, double b2, double eps, cudaStream_t st);
+ffc_status launch_leverage(const double* K, int64_t m, int64_t n, int64_t ldk, double eps, int64_t r_fixed,
+                           double* lev, double* sigma, int64_t* rank_host, int32_t* sweeps_host, cudaStream_t st);
+
 // host helpers
 int sm_count();
+bool kernel_ok(const ffc_kernel& k, int d);   // sets the error message when false
 void node_layout(int64_t N, int depth, int64_t* begin, int64_t* count, int32_t* level);
 
 }  // namespace ffc

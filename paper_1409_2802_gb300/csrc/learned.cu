@@ -1,0 +1,755 @@
+// Learned row proposal: per-row features, the 12-128-128-1 GELU network
+// (forward, backward, per-node softmax cross-entropy, Adam) and the weighted
+// draw without replacement from a candidate pool.
+//
+// The network replaces the leverage-score row distribution of §3 (Def.
+// "Statistical Leverage"; §4.1.3 "Leverage sampling"), which needs a basis of
+// the full far-field block, by a prediction from 12 cheap features. Weights
+// are kept as an FP32 master copy and used rounded to FP16 (round to nearest
+// even); every product accumulates in FP32.
+//
+// Layout of the parameter vector (FFC_MLP_PARAMS floats, matrices row-major,
+// W[j][k] = weight from input k to unit j):
+//   W1 128x12 @0 | b1 128 @1536 | W2 128x128 @1664 | b2 128 @18048 | w3 128 @18176 | b3 @18304
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ffc_internal.cuh"
+
+namespace ffc {
+
+constexpr int NF = FFC_N_FEATURES;   // 12
+constexpr int NH = 128;
+constexpr int OFF_W1 = 0, OFF_B1 = 1536, OFF_W2 = 1664, OFF_B2 = 18048, OFF_W3 = 18176, OFF_B3 = 18304;
+static_assert(OFF_B3 + 1 == FFC_MLP_PARAMS, "parameter layout");
+static_assert(NF == 12, "feature count");
+
+constexpr int FT = 64;          // rows per network tile
+constexpr int NET_THREADS = 256;
+
+__device__ __forceinline__ float half_round(float w) { return __half2float(__float2half_rn(w)); }
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+// d/dz z Phi(z) = Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_prime_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// ----------------------------------------------------------------------------
+// features (one warp per row)
+
+template <typename TP>
+__global__ void __launch_bounds__(256) features_kernel(const TP* __restrict__ Y, int d, const FeatItem* items,
+                                                       int n_items, int64_t total, ffc_kernel k,
+                                                       const double* __restrict__ proj, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp_global; f < total; f += nwarps) {
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {              // last item with out_begin <= f
+      int mid = (lo + hi + 1) >> 1;
+      if (items[mid].out_begin <= f) lo = mid; else hi = mid - 1;
+    }
+    const FeatItem& it = items[lo];
+    const int64_t i = f - it.out_begin;
+    const int64_t cnt = it.count ? *it.count : it.cap;
+    float* o = out + f * NF;
+    if (i >= cnt) {
+      if (lane < NF) o[lane] = 0.0f;
+      continue;
+    }
+    const TP* y = Y + it.rows[i] * (int64_t)d;
+    const double* xc = it.x_c;
+    // O(d) sums in FP32 (coordinates rounded to FP32 first); the per-row
+    // transforms below are FP64
+    float sdd = 0.0f, syy = 0.0f, syx = 0.0f, sxx = 0.0f;
+    float sp[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sp[q] = 0.0f;
+    for (int c = lane; c < d; c += 32) {
+      const float yv = (float)__ldg(y + c), xv = (float)xc[c];
+      const float dl = yv - xv;
+      sdd = fmaf(dl, dl, sdd); syy = fmaf(yv, yv, syy); syx = fmaf(yv, xv, syx); sxx = fmaf(xv, xv, sxx);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sp[q] = fmaf((float)proj[(int64_t)q * d + c], dl, sp[q]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sdd += __shfl_xor_sync(0xffffffffu, sdd, off);
+      syy += __shfl_xor_sync(0xffffffffu, syy, off);
+      syx += __shfl_xor_sync(0xffffffffu, syx, off);
+      sxx += __shfl_xor_sync(0xffffffffu, sxx, off);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sp[q] += __shfl_xor_sync(0xffffffffu, sp[q], off);
+    }
+    double rho = it.radius ? *it.radius : it.radius_host;
+    if (!(rho > 0.0)) rho = 1.0;
+    const double dd = sdd, r = sqrt(dd);
+    double v = 0.0;
+    if (lane == 0) {
+      v = r / rho;
+    } else if (lane == 1) {
+      if (k.kind == FFC_GAUSSIAN) v = exp(-dd / (2.0 * k.h * k.h));
+      else if (k.kind == FFC_LAPLACE) v = pow(rho / r, (double)(d - 2));
+      else v = pow((double)syx / k.h + k.c, (double)k.p) /
+               pow(sqrt((double)syy) * sqrt((double)sxx) / k.h + k.c, (double)k.p);
+    } else if (lane == 2) {
+      v = sqrt((double)syy) / rho;
+    } else if (lane == 3) {
+      v = rho / (k.kind == FFC_LAPLACE ? 1.0 : k.h);
+    } else if (lane < NF) {
+      float pv = sp[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) if (lane - 4 == q) pv = sp[q];
+      v = (double)pv / rho;
+    }
+    if (lane < NF) o[lane] = (float)v;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// network: shared tiles and the two dense layers of one 64-row tile
+//
+// Thread (ty = warp, tx = lane) computes rows 8 ty .. 8 ty + 7 and units
+// 4 tx .. 4 tx + 3 of a 64 x 128 layer output.
+
+struct NetWeights {
+  alignas(16) __half W2T[NH * NH];     // W2T[k * NH + j] = W2[j][k]
+  alignas(16) float W1T[NF * NH];      // W1T[k * NH + j] = W1[j][k]
+  alignas(16) float b1[NH];
+  alignas(16) float b2[NH];
+  alignas(16) float w3[NH];
+  float b3;
+};
+
+__device__ void load_weights(const float* __restrict__ P, NetWeights& w) {
+  for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) {
+    const int j = e / NH, kk = e % NH;
+    w.W2T[kk * NH + j] = __float2half_rn(P[OFF_W2 + e]);
+  }
+  for (int e = threadIdx.x; e < NH * NF; e += blockDim.x) {
+    const int j = e / NF, kk = e % NF;
+    w.W1T[kk * NH + j] = half_round(P[OFF_W1 + e]);
+  }
+  for (int j = threadIdx.x; j < NH; j += blockDim.x) {
+    w.b1[j] = half_round(P[OFF_B1 + j]);
+    w.b2[j] = half_round(P[OFF_B2 + j]);
+    w.w3[j] = half_round(P[OFF_W3 + j]);
+  }
+  if (threadIdx.x == 0) w.b3 = half_round(P[OFF_B3]);
+}
+
+// z1 = W1 x + b1 for the thread's 8 x 4 block; X is FT x NF row-major.
+__device__ __forceinline__ void layer1(const NetWeights& w, const float* X, int ty, int tx, float z[8][4]) {
+  const float4 b = *reinterpret_cast<const float4*>(&w.b1[4 * tx]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { z[i][0] = b.x; z[i][1] = b.y; z[i][2] = b.z; z[i][3] = b.w; }
+#pragma unroll
+  for (int kk = 0; kk < NF; ++kk) {
+    const float4 wv = *reinterpret_cast<const float4*>(&w.W1T[kk * NH + 4 * tx]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float x = X[(8 * ty + i) * NF + kk];
+      z[i][0] = fmaf(wv.x, x, z[i][0]); z[i][1] = fmaf(wv.y, x, z[i][1]);
+      z[i][2] = fmaf(wv.z, x, z[i][2]); z[i][3] = fmaf(wv.w, x, z[i][3]);
+    }
+  }
+}
+
+// z2 = W2 h1 + b2; H1 is FT x NH row-major (k contiguous).
+__device__ __forceinline__ void layer2(const NetWeights& w, const float* H1, int ty, int tx, float z[8][4]) {
+  const float4 b = *reinterpret_cast<const float4*>(&w.b2[4 * tx]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { z[i][0] = b.x; z[i][1] = b.y; z[i][2] = b.z; z[i][3] = b.w; }
+#pragma unroll 2
+  for (int k0 = 0; k0 < NH; k0 += 4) {
+    float4 hv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hv[i] = *reinterpret_cast<const float4*>(&H1[(8 * ty + i) * NH + k0]);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const __half2* wp = reinterpret_cast<const __half2*>(&w.W2T[(k0 + kk) * NH + 4 * tx]);
+      const float2 w01 = __half22float2(wp[0]), w23 = __half22float2(wp[1]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float h = kk == 0 ? hv[i].x : (kk == 1 ? hv[i].y : (kk == 2 ? hv[i].z : hv[i].w));
+        z[i][0] = fmaf(w01.x, h, z[i][0]); z[i][1] = fmaf(w01.y, h, z[i][1]);
+        z[i][2] = fmaf(w23.x, h, z[i][2]); z[i][3] = fmaf(w23.y, h, z[i][3]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void load_x_tile(const float* __restrict__ F, int64_t row0, int64_t R, float* X) {
+  for (int e = threadIdx.x; e < FT * NF; e += blockDim.x) {
+    const int64_t r = row0 + e / NF;
+    X[e] = r < R ? F[row0 * NF + e] : 0.0f;
+  }
+}
+
+struct FwdSmem {
+  NetWeights w;
+  alignas(16) float X[FT * NF];
+  alignas(16) float H1[FT * NH];
+};
+
+// logits o[r] for R feature rows
+__global__ void __launch_bounds__(NET_THREADS) mlp_forward_kernel(const float* __restrict__ P,
+                                                                  const float* __restrict__ F, int64_t R,
+                                                                  float* __restrict__ logits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  load_weights(P, S.w);
+  const int64_t tiles = (R + FT - 1) / FT;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t row0 = t * FT;
+    __syncthreads();
+    load_x_tile(F, row0, R, S.X);
+    __syncthreads();
+    float z[8][4];
+    layer1(S.w, S.X, ty, tx, z);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float4 h = make_float4(gelu_f(z[i][0]), gelu_f(z[i][1]), gelu_f(z[i][2]), gelu_f(z[i][3]));
+      *reinterpret_cast<float4*>(&S.H1[(8 * ty + i) * NH + 4 * tx]) = h;
+    }
+    __syncthreads();
+    layer2(S.w, S.H1, ty, tx, z);
+    float po[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      po[i] = 0.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) po[i] = fmaf(S.w.w3[4 * tx + u], gelu_f(z[i][u]), po[i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) po[i] += __shfl_xor_sync(0xffffffffu, po[i], off);
+    if (tx < 8) {
+      float v = po[0];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) if (tx == i) v = po[i];
+      const int64_t r = row0 + 8 * ty + tx;
+      if (r < R) logits[r] = v + S.w.b3;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// training: per-node softmax cross-entropy and the backward pass
+
+template <typename T>
+__device__ T block_sum(T v, T* red) {   // blockDim.x == 256, deterministic order
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T s = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+__device__ float block_max(float v, float* red) {
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = red[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s = fmaxf(s, red[i]);
+  return s;
+}
+
+// One CTA per node b, targets normalised to q_i = t_i / sum_b t: lse_b,
+// loss_b = -sum q (o - lse) = lse - (sum t o) / (sum t), g_o = (softmax - q) / B.
+__global__ void __launch_bounds__(256) node_ce_kernel(const float* __restrict__ logits,
+                                                      const double* __restrict__ targets,
+                                                      const int64_t* __restrict__ node_off, int n_nodes,
+                                                      float* __restrict__ g_o, double* __restrict__ loss_part) {
+  __shared__ double redd[8];
+  __shared__ float redf[8];
+  const int b = blockIdx.x;
+  const int64_t a = node_off[b], e = node_off[b + 1];
+  float mx = -INFINITY;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) mx = fmaxf(mx, logits[i]);
+  mx = block_max(mx, redf);
+  double se = 0.0, st = 0.0, sto = 0.0;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    const double o = logits[i], t = targets[i];
+    se += exp(o - (double)mx); st += t; sto += t * o;
+  }
+  se = block_sum(se, redd);
+  st = block_sum(st, redd);
+  sto = block_sum(sto, redd);
+  const double lse = (double)mx + log(se);
+  const double inv_t = st > 0.0 ? 1.0 / st : 0.0;
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x)
+    g_o[i] = (float)((exp((double)logits[i] - lse) - targets[i] * inv_t) / (double)n_nodes);
+  if (threadIdx.x == 0) loss_part[b] = (e > a && st > 0.0) ? (lse - sto * inv_t) : 0.0;
+}
+
+struct BwdSmem {
+  NetWeights w;
+  alignas(16) __half W2[NH * NH];      // row-major W2[j][k]
+  alignas(16) float X[FT * NF];
+  alignas(16) float go[FT];
+  alignas(16) float Z1[FT * NH];
+  alignas(16) float H1[FT * NH];       // h1, later g_z1
+  alignas(16) float GZ2[FT * NH];
+  alignas(16) float red[8 * NH];
+};
+
+// Gradient partials of one CTA over its row tiles; part: gridDim.x x FFC_MLP_PARAMS.
+__global__ void __launch_bounds__(NET_THREADS, 1) mlp_backward_kernel(const float* __restrict__ P,
+                                                                      const float* __restrict__ F,
+                                                                      const float* __restrict__ g_o, int64_t R,
+                                                                      float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  load_weights(P, S.w);
+  for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) S.W2[e] = __float2half_rn(P[OFF_W2 + e]);
+
+  float dW2[4][16];            // units 4 tx + u, inputs 16 ty + c
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) dW2[u][c] = 0.0f;
+  float dW1[6];                // unit threadIdx.x / 2, inputs 6 (threadIdx.x & 1) + c
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dW1[c] = 0.0f;
+  float dw3[4] = {0, 0, 0, 0}, db2[4] = {0, 0, 0, 0}, db1[4] = {0, 0, 0, 0};
+  float db3 = 0.0f;
+  const int j1 = threadIdx.x >> 1, c1 = 6 * (threadIdx.x & 1);
+
+  const int64_t tiles = (R + FT - 1) / FT;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t row0 = t * FT;
+    __syncthreads();
+    load_x_tile(F, row0, R, S.X);
+    for (int e = threadIdx.x; e < FT; e += blockDim.x) S.go[e] = row0 + e < R ? g_o[row0 + e] : 0.0f;
+    __syncthreads();
+    float z[8][4];
+    layer1(S.w, S.X, ty, tx, z);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      *reinterpret_cast<float4*>(&S.Z1[(8 * ty + i) * NH + 4 * tx]) = make_float4(z[i][0], z[i][1], z[i][2], z[i][3]);
+      *reinterpret_cast<float4*>(&S.H1[(8 * ty + i) * NH + 4 * tx]) =
+          make_float4(gelu_f(z[i][0]), gelu_f(z[i][1]), gelu_f(z[i][2]), gelu_f(z[i][3]));
+    }
+    if (threadIdx.x == 0) {
+      float s = 0.0f;
+      for (int r = 0; r < FT; ++r) s += S.go[r];
+      db3 += s;
+    }
+    __syncthreads();
+    layer2(S.w, S.H1, ty, tx, z);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float go = S.go[8 * ty + i];
+      float g4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dw3[u] = fmaf(go, gelu_f(z[i][u]), dw3[u]);
+        g4[u] = go * S.w.w3[4 * tx + u] * gelu_prime_f(z[i][u]);
+        db2[u] += g4[u];
+      }
+      *reinterpret_cast<float4*>(&S.GZ2[(8 * ty + i) * NH + 4 * tx]) = make_float4(g4[0], g4[1], g4[2], g4[3]);
+    }
+    __syncthreads();
+    // dW2[j][k] += sum_r gz2[r][j] h1[r][k]
+    for (int r = 0; r < FT; ++r) {
+      const float4 g = *reinterpret_cast<const float4*>(&S.GZ2[r * NH + 4 * tx]);
+      const float gg[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const float4 h = *reinterpret_cast<const float4*>(&S.H1[r * NH + 16 * ty + 4 * c4]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dW2[u][4 * c4 + 0] = fmaf(gg[u], h.x, dW2[u][4 * c4 + 0]);
+          dW2[u][4 * c4 + 1] = fmaf(gg[u], h.y, dW2[u][4 * c4 + 1]);
+          dW2[u][4 * c4 + 2] = fmaf(gg[u], h.z, dW2[u][4 * c4 + 2]);
+          dW2[u][4 * c4 + 3] = fmaf(gg[u], h.w, dW2[u][4 * c4 + 3]);
+        }
+      }
+    }
+    // g_h1[r][k] = sum_j W2[j][k] gz2[r][j] for rows 8 ty + i, inputs 4 tx + u
+    float gh[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) gh[i][u] = 0.0f;
+#pragma unroll 2
+    for (int j0 = 0; j0 < NH; j0 += 4) {
+      float4 gv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) gv[i] = *reinterpret_cast<const float4*>(&S.GZ2[(8 * ty + i) * NH + j0]);
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const __half2* wp = reinterpret_cast<const __half2*>(&S.W2[(j0 + jj) * NH + 4 * tx]);
+        const float2 w01 = __half22float2(wp[0]), w23 = __half22float2(wp[1]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float g = jj == 0 ? gv[i].x : (jj == 1 ? gv[i].y : (jj == 2 ? gv[i].z : gv[i].w));
+          gh[i][0] = fmaf(w01.x, g, gh[i][0]); gh[i][1] = fmaf(w01.y, g, gh[i][1]);
+          gh[i][2] = fmaf(w23.x, g, gh[i][2]); gh[i][3] = fmaf(w23.y, g, gh[i][3]);
+        }
+      }
+    }
+    __syncthreads();   // every thread is done reading H1 (dW2) before it becomes g_z1
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 z1 = *reinterpret_cast<const float4*>(&S.Z1[(8 * ty + i) * NH + 4 * tx]);
+      const float g0 = gh[i][0] * gelu_prime_f(z1.x), g1 = gh[i][1] * gelu_prime_f(z1.y);
+      const float g2 = gh[i][2] * gelu_prime_f(z1.z), g3 = gh[i][3] * gelu_prime_f(z1.w);
+      db1[0] += g0; db1[1] += g1; db1[2] += g2; db1[3] += g3;
+      *reinterpret_cast<float4*>(&S.H1[(8 * ty + i) * NH + 4 * tx]) = make_float4(g0, g1, g2, g3);
+    }
+    __syncthreads();
+    // dW1[j][k] += sum_r gz1[r][j] x[r][k]
+    for (int r = 0; r < FT; ++r) {
+      const float g = S.H1[r * NH + j1];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) dW1[c] = fmaf(g, S.X[r * NF + c1 + c], dW1[c]);
+    }
+  }
+
+  // write this CTA's partial gradient
+  float* out = part + (int64_t)blockIdx.x * FFC_MLP_PARAMS;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) out[OFF_W2 + (4 * tx + u) * NH + 16 * ty + c] = dW2[u][c];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[OFF_W1 + j1 * NF + c1 + c] = dW1[c];
+  // per-unit sums over the 8 row groups (warps), in warp order
+  auto emit = [&](const float (&src)[4], int off) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) S.red[ty * NH + 4 * tx + u] = src[u];
+    __syncthreads();
+    if (threadIdx.x < NH) {
+      float s = 0.0f;
+      for (int w = 0; w < 8; ++w) s += S.red[w * NH + threadIdx.x];
+      out[off + threadIdx.x] = s;
+    }
+  };
+  emit(dw3, OFF_W3);
+  emit(db2, OFF_B2);
+  emit(db1, OFF_B1);
+  if (threadIdx.x == 0) out[OFF_B3] = db3;
+}
+
+__global__ void grad_reduce_kernel(const float* __restrict__ part, int n_part, float* __restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= FFC_MLP_PARAMS) return;
+  float s = 0.0f;
+  for (int c = 0; c < n_part; ++c) s += part[(int64_t)c * FFC_MLP_PARAMS + p];
+  grad[p] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, double lr, double b1, double b2, double eps,
+                            double bc1, double bc2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double gg = g[p];
+  const double mm = b1 * (double)m[p] + (1.0 - b1) * gg;
+  const double vv = b2 * (double)v[p] + (1.0 - b2) * gg * gg;
+  const double mh = mm / bc1, vh = vv / bc2;
+  theta[p] = (float)((double)theta[p] - lr * mh / (sqrt(vh) + eps));
+  m[p] = (float)mm;
+  v[p] = (float)vv;
+}
+
+// ----------------------------------------------------------------------------
+// weighted draw without replacement (Efraimidis-Spirakis keys), one CTA per pool
+
+constexpr int SEL_THREADS = 1024;
+constexpr int SEL_CAP = 16384;      // entries sorted at once in shared memory
+constexpr int SEL_MAX_KEEP = 8192;  // largest min(s, P) of one draw
+
+__device__ __forceinline__ bool sel_less(uint64_t ka, uint32_t pa, uint64_t kb, uint32_t pb) {
+  return ka < kb || (ka == kb && pa < pb);
+}
+
+// Ascending bitonic sort of (key, pos) pairs [0, n) in shared memory, n a power of two.
+__device__ void bitonic_sort(uint64_t* key, uint32_t* pos, int n) {
+  for (int kk = 2; kk <= n; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & kk) == 0;
+          const bool gt = sel_less(key[l], pos[l], key[i], pos[i]);
+          if (gt == up) {
+            const uint64_t tk = key[i]; key[i] = key[l]; key[l] = tk;
+            const uint32_t tp = pos[i]; pos[i] = pos[l]; pos[l] = tp;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sort key of pool position i: -ln(u_i) / w'_i > 0, whose bit pattern sorts
+// ascending exactly as the key ln(u_i) / w'_i sorts descending.
+__device__ __forceinline__ uint64_t es_sort_key(float logit, double mx, double mean, uint64_t seed,
+                                                uint64_t stream_id, int64_t i) {
+  const double w = exp((double)logit - mx);
+  const double wp = 0.9 * w / mean + 0.1;
+  const uint64_t draw = philox_draw(seed, stream_id, DOMAIN_WEIGHTED_KEYS, (uint64_t)i);
+  const double u = ((double)(draw >> 11) + 0.5) * 0x1.0p-53;
+  return (uint64_t)__double_as_longlong(-log(u) / wp);
+}
+
+// One CTA per pool: the min(s, P) pool rows with the largest keys, in key
+// order. Pools above SEL_CAP entries are streamed in chunks behind the
+// running best rows.
+__global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* items, uint64_t seed) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SelectItem& it = items[blockIdx.x];
+  const int64_t P = it.count ? *it.count : it.P;
+  const int64_t n_keep = P < it.s ? P : it.s;
+  if (threadIdx.x == 0 && it.s_out) *it.s_out = n_keep;
+  if (n_keep <= 0) return;
+  uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
+  uint32_t* pos = reinterpret_cast<uint32_t*>(key + SEL_CAP);
+  __shared__ double redd[32];
+  __shared__ float redf[32];
+  float mx = -INFINITY;
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) mx = fmaxf(mx, it.logits[i]);
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = redf[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, redf[i]);
+  double sw = 0.0;
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sw += exp((double)it.logits[i] - (double)mx);
+  for (int off = 16; off > 0; off >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, off);
+  if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = sw;
+  __syncthreads();
+  sw = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sw += redd[i];
+  const double mean = sw / (double)P;
+  const double dmx = (double)mx;
+  auto fill = [&](int lo, int hi, int64_t base) {   // entries [lo, hi) <- positions base, base + 1, ...
+    for (int e = lo + (int)threadIdx.x; e < hi; e += blockDim.x) {
+      const int64_t i = base + (e - lo);
+      if (i < P) {
+        key[e] = es_sort_key(it.logits[i], dmx, mean, seed, it.stream_id, i);
+        pos[e] = (uint32_t)i;
+      } else {
+        key[e] = ~0ull;
+        pos[e] = 0xFFFFFFFFu;
+      }
+    }
+  };
+  if (P > SEL_CAP && n_keep > SEL_MAX_KEEP) return;   // rejected on the host; no endless chunk loop
+  if (P <= SEL_CAP) {
+    int Pp = 1;
+    while (Pp < P) Pp <<= 1;
+    fill(0, Pp, 0);
+    __syncthreads();
+    bitonic_sort(key, pos, Pp);
+  } else {
+    int keep2 = 1;
+    while (keep2 < n_keep) keep2 <<= 1;
+    fill(0, SEL_CAP, 0);
+    __syncthreads();
+    bitonic_sort(key, pos, SEL_CAP);
+    for (int64_t base = SEL_CAP; base < P; base += SEL_CAP - keep2) {
+      fill(keep2, SEL_CAP, base);   // the best keep2 so far stay in [0, keep2)
+      __syncthreads();
+      bitonic_sort(key, pos, SEL_CAP);
+    }
+  }
+  for (int64_t i = threadIdx.x; i < n_keep; i += blockDim.x) it.rows_out[i] = it.pool[pos[i]];
+}
+
+// ----------------------------------------------------------------------------
+// far-field lists of many nodes at once (ascending candidate order), with the
+// same FP64 distance test as the uniform sampler
+
+constexpr int FL_TILE = 256;
+
+template <typename TP>
+__device__ __forceinline__ bool far_member(const TP* __restrict__ Y, int d, int64_t j, const FarItem& it,
+                                           double thr2) {
+  if (j >= it.M || (j >= it.ex_begin && j < it.ex_end)) return false;
+  const TP* y = Y + j * (int64_t)d;
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double df = ld_point(y + k) - __ldg(it.x_c + k);
+    acc = fma(df, df, acc);
+  }
+  return acc >= thr2;
+}
+
+__device__ __forceinline__ double far_thr2(const FarItem& it) {
+  const double thr = it.xi * (it.radius ? *it.radius : it.radius_host);
+  return thr * thr;
+}
+
+// blockIdx.y = item, blockIdx.x = tile of FL_TILE candidates
+template <typename TP>
+__global__ void __launch_bounds__(FL_TILE) far_count_kernel(const TP* __restrict__ Y, int d, const FarItem* items,
+                                                            int64_t tiles, int64_t* tile_cnt) {
+  __shared__ int wc[FL_TILE / 32];
+  const FarItem& it = items[blockIdx.y];
+  const int64_t j = (int64_t)blockIdx.x * FL_TILE + threadIdx.x;
+  const bool f = far_member(Y, d, j, it, far_thr2(it));
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < FL_TILE / 32; ++w) t += wc[w];
+    tile_cnt[(int64_t)blockIdx.y * tiles + blockIdx.x] = t;
+  }
+}
+
+// one CTA per item: exclusive scan of its tile counts, total to *count
+__global__ void far_scan_kernel(const FarItem* items, int64_t tiles, int64_t* tile_cnt) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t carry;
+  int64_t* tc = tile_cnt + (int64_t)blockIdx.x * tiles;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < tiles; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < tiles ? tc[i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+      const int64_t add = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < tiles) tc[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *items[blockIdx.x].count = carry;
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(FL_TILE) far_scatter_kernel(const TP* __restrict__ Y, int d, const FarItem* items,
+                                                              int64_t tiles, const int64_t* tile_off) {
+  __shared__ int wc[FL_TILE / 32];
+  const FarItem& it = items[blockIdx.y];
+  const int64_t j = (int64_t)blockIdx.x * FL_TILE + threadIdx.x;
+  const bool f = far_member(Y, d, j, it, far_thr2(it));
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wc[w] = __popc(b);
+  __syncthreads();
+  int off = 0;
+  for (int q = 0; q < w; ++q) off += wc[q];
+  if (f) it.list[tile_off[(int64_t)blockIdx.y * tiles + blockIdx.x] + off + __popc(b & ((1u << lane) - 1u))] = j;
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+
+static int net_grid(int64_t R, int per_sm) {
+  const int64_t tiles = (R + FT - 1) / FT;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * per_sm));
+}
+
+ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const FeatItem* items_dev, int n_items,
+                           int64_t total, const double* proj, float* out, cudaStream_t st) {
+  if (total <= 0 || n_items <= 0) return FFC_OK;
+  const int64_t warps = total;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sm_count() * 16));
+  if (dtype == FFC_F64)
+    features_kernel<double><<<grid, 256, 0, st>>>((const double*)Y, d, items_dev, n_items, total, k, proj, out);
+  else
+    features_kernel<float><<<grid, 256, 0, st>>>((const float*)Y, d, items_dev, n_items, total, k, proj, out);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st) {
+  if (R <= 0) return FFC_OK;
+  const size_t smem = sizeof(FwdSmem);
+  FFC_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  mlp_forward_kernel<<<net_grid(R, 2), NET_THREADS, smem, st>>>(params, feats, R, logits);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+ffc_status launch_select(const SelectItem* items_dev, int n_items, int64_t keep_max, uint64_t seed, cudaStream_t st) {
+  if (n_items <= 0) return FFC_OK;
+  if (keep_max > SEL_MAX_KEEP) {
+    set_error("weighted draw of %lld rows exceeds %d", (long long)keep_max, SEL_MAX_KEEP);
+    return FFC_E_INVALID;
+  }
+  const size_t smem = (size_t)SEL_CAP * (sizeof(uint64_t) + sizeof(uint32_t));
+  FFC_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  select_kernel<<<n_items, SEL_THREADS, smem, st>>>(items_dev, seed);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+ffc_status launch_far_lists(const void* Y, int dtype, int d, const FarItem* items_dev, int n_items, int64_t M_max,
+                            int64_t* tile_cnt, cudaStream_t st) {
+  if (n_items <= 0 || M_max <= 0) return FFC_OK;
+  const int64_t tiles = (M_max + FL_TILE - 1) / FL_TILE;
+  FFC_REQUIRE(n_items <= 65535, "far lists: at most 65535 items per launch");
+  const dim3 grid((unsigned)tiles, (unsigned)n_items);
+  if (dtype == FFC_F64) {
+    far_count_kernel<double><<<grid, FL_TILE, 0, st>>>((const double*)Y, d, items_dev, tiles, tile_cnt);
+    far_scan_kernel<<<n_items, 1024, 0, st>>>(items_dev, tiles, tile_cnt);
+    far_scatter_kernel<double><<<grid, FL_TILE, 0, st>>>((const double*)Y, d, items_dev, tiles, tile_cnt);
+  } else {
+    far_count_kernel<float><<<grid, FL_TILE, 0, st>>>((const float*)Y, d, items_dev, tiles, tile_cnt);
+    far_scan_kernel<<<n_items, 1024, 0, st>>>(items_dev, tiles, tile_cnt);
+    far_scatter_kernel<float><<<grid, FL_TILE, 0, st>>>((const float*)Y, d, items_dev, tiles, tile_cnt);
+  }
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+int64_t far_list_tiles(int64_t M) { return (M + FL_TILE - 1) / FL_TILE; }
+
+ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const double* targets,
+                                const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,
+                                double* loss_part, float* part, int n_part, float* grad, cudaStream_t st) {
+  FFC_REQUIRE(n_part >= 1, "gradient partial count must be >= 1");
+  ffc_status rc = launch_mlp_forward(params, feats, R, logits, st);
+  if (rc != FFC_OK) return rc;
+  node_ce_kernel<<<n_nodes, 256, 0, st>>>(logits, targets, node_off_dev, n_nodes, g_o, loss_part);
+  FFC_CUDA(cudaGetLastError());
+  const size_t smem = sizeof(BwdSmem);
+  FFC_CUDA(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  mlp_backward_kernel<<<n_part, NET_THREADS, smem, st>>>(params, feats, g_o, R, part);
+  FFC_CUDA(cudaGetLastError());
+  grad_reduce_kernel<<<(FFC_MLP_PARAMS + 255) / 256, 256, 0, st>>>(part, n_part, grad);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+int mlp_backward_grid(int64_t R) { return net_grid(R, 1); }
+
+ffc_status launch_adam(float* theta, const float* g, float* m, float* v, int64_t n, int64_t step, double lr,
+                       double b1, double b2, double eps, cudaStream_t st) {
+  if (n <= 0) return FFC_OK;
+  const double bc1 = 1.0 - std::pow(b1, (double)step), bc2 = 1.0 - std::pow(b2, (double)step);
+  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+}  // namespace ffc

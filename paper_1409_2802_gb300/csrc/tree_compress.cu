@@ -1,7 +1,9 @@
 // ffc_compress_tree: sampled-row ID of every tree node at level >= min_level.
 //
 // For each node (far field of the node's centroid and radius, §4.1 steps
-// 2-3): uniform sample of s far-field rows (§2.2), K' = K(rows, node sources),
+// 2-3): uniform sample of s far-field rows (§2.2) or the learned proposal
+// (features and network logits of the candidate pool, weighted draw without
+// replacement; drawn once per call for s_max rows), K' = K(rows, node sources),
 // pivoted QR in tolerance mode for at most s/2 steps, T = R11^-1 R12
 // (§2.1.3, App. A.1). Nodes whose tolerance is not met within s/2 steps are
 // re-run with s doubled (the sample is prefix consistent) while s <= s_max.
@@ -48,6 +50,11 @@ struct ffc_tree_result {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int rounds = 0;
+  // learned sampler: per output node, rows drawn (<= s_max, best first) and far-field size;
+  // proposal workspace (grow-only)
+  int64_t *lcount = nullptr, *lfar = nullptr;
+  char* pws = nullptr;
+  size_t pws_bytes = 0;
   // tracing
   ffc_tree_profile prof{};
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -177,6 +184,139 @@ ffc_status alloc_outputs(ffc_tree_result* R) {
   return FFC_OK;
 }
 
+__global__ void learned_round_kernel(int W, const int32_t* out_idx, int64_t s_nom, const int64_t* lcount,
+                                     const int64_t* lfar, int64_t* s_out, int64_t* fc) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W) return;
+  const int o = out_idx[q];
+  const int64_t c = lcount[o];
+  s_out[q] = c < s_nom ? c : s_nom;
+  fc[q] = lfar[o];
+}
+
+__global__ void copy_counts_kernel(int n, const int64_t* src, int64_t* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+ffc_status grow(char** buf, size_t* have, size_t want, cudaStream_t st) {
+  if (want <= *have) return FFC_OK;
+  if (*buf) {
+    FFC_CUDA(cudaStreamSynchronize(st));
+    FFC_CUDA(cudaFree(*buf));
+    *buf = nullptr;
+  }
+  const size_t bytes = want + want / 4;
+  FFC_CUDA(cudaMalloc((void**)buf, bytes));
+  *have = bytes;
+  return FFC_OK;
+}
+
+// Learned sampler: for every output node, the candidate pool (whole far field
+// or a uniform pool), features, network logits and the weighted draw of its
+// min(s_max, P) best rows, in key order. The keys do not depend on s, so
+// every sample-size round takes a prefix of these rows. Nodes are processed
+// in groups of at most PROPOSE_ROWS candidate rows.
+constexpr int64_t PROPOSE_ROWS = 48ll << 20;
+
+ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree, cudaStream_t st) {
+  const ffc_params& P = R->p;
+  const int d = R->d;
+  const int64_t n_out = R->n_out;
+  const bool whole = P.pool_rows == 0;
+  if (!R->lcount) {
+    FFC_CUDA(cudaMalloc((void**)&R->lcount, sizeof(int64_t) * 2 * n_out));
+    R->lfar = R->lcount + n_out;
+  }
+  int64_t o0 = 0;
+  while (o0 < n_out) {
+    // group [o0, o1)
+    int64_t o1 = o0, rows = 0;
+    while (o1 < n_out && (o1 == o0 || rows + (whole ? R->N - R->count_h[o1] : P.pool_rows) <= PROPOSE_ROWS) &&
+           o1 - o0 < 2048) {
+      rows += whole ? R->N - R->count_h[o1] : P.pool_rows;
+      ++o1;
+    }
+    const int g = (int)(o1 - o0);
+    std::vector<int64_t> cap(g), base(g);
+    int64_t tot = 0;
+    for (int i = 0; i < g; ++i) {
+      cap[i] = whole ? std::max<int64_t>(R->N - R->count_h[o0 + i], 1) : P.pool_rows;
+      base[i] = tot;
+      tot += cap[i];
+    }
+    const int64_t tiles = far_list_tiles(R->N);
+    Layout L;
+    const size_t o_far = L.add<FarItem>(g), o_smp = L.add<SampleItem>(g), o_fi = L.add<FeatItem>(g),
+                 o_si = L.add<SelectItem>(g), o_pool = L.add<int64_t>(tot),
+                 o_feat = L.add<float>((size_t)tot * FFC_N_FEATURES), o_lg = L.add<float>(tot),
+                 o_cnt = L.add<int64_t>(g), o_fc = L.add<int64_t>(g), o_st = L.add<int32_t>(g),
+                 o_tc = L.add<int64_t>(whole ? (size_t)g * tiles : 0),
+                 o_scr = L.add<int32_t>(whole ? 0 : (size_t)std::min(g, 2048) * R->N);
+    ffc_status rc = grow(&R->pws, &R->pws_bytes, L.off, st);
+    if (rc != FFC_OK) return rc;
+    char* b = R->pws;
+    FarItem* d_far = (FarItem*)(b + o_far);
+    SampleItem* d_smp = (SampleItem*)(b + o_smp);
+    FeatItem* d_fi = (FeatItem*)(b + o_fi);
+    SelectItem* d_si = (SelectItem*)(b + o_si);
+    int64_t* pool = (int64_t*)(b + o_pool);
+    float* feats = (float*)(b + o_feat);
+    float* logits = (float*)(b + o_lg);
+    int64_t* cnt = (int64_t*)(b + o_cnt);
+    int64_t* fc = (int64_t*)(b + o_fc);
+    int32_t* sst = (int32_t*)(b + o_st);
+    int64_t* tcnt = (int64_t*)(b + o_tc);
+    int32_t* scratch = (int32_t*)(b + o_scr);
+    std::vector<FarItem> hfar(whole ? g : 0);
+    std::vector<SampleItem> hsmp(whole ? 0 : g);
+    std::vector<FeatItem> hfi(g);
+    std::vector<SelectItem> hsi(g);
+    for (int i = 0; i < g; ++i) {
+      const int64_t o = o0 + i, node = R->node_h[o], bgn = R->begin_h[o], n = R->count_h[o];
+      const double* xc = tree->centroid_dev + node * d;
+      const double* rad = tree->radius_dev + node;
+      if (whole) {
+        FarItem& f = hfar[i];
+        f.M = R->N; f.ex_begin = bgn; f.ex_end = bgn + n; f.x_c = xc; f.radius = rad; f.radius_host = 0.0;
+        f.xi = P.xi; f.list = pool + base[i]; f.count = cnt + i;
+      } else {
+        SampleItem& si = hsmp[i];
+        si.M = R->N; si.ex_begin = bgn; si.ex_end = bgn + n; si.x_c = xc; si.thr2 = 0.0; si.radius = rad;
+        si.xi = P.xi; si.s = cap[i]; si.stream_id = (uint64_t)node; si.rows = pool + base[i];
+      }
+      FeatItem& fi = hfi[i];
+      fi.rows = pool + base[i]; fi.count = cnt + i; fi.cap = cap[i]; fi.out_begin = base[i];
+      fi.x_c = xc; fi.radius = rad; fi.radius_host = 0.0;
+      SelectItem& se = hsi[i];
+      se.pool = pool + base[i]; se.count = cnt + i; se.P = cap[i]; se.logits = logits + base[i]; se.s = P.s_max;
+      se.stream_id = (uint64_t)node; se.rows_out = R->rows + R->rows_off_h[o]; se.s_out = R->lcount + o;
+    }
+    if (whole) FFC_CUDA(cudaMemcpyAsync(d_far, hfar.data(), sizeof(FarItem) * g, cudaMemcpyHostToDevice, st));
+    else FFC_CUDA(cudaMemcpyAsync(d_smp, hsmp.data(), sizeof(SampleItem) * g, cudaMemcpyHostToDevice, st));
+    FFC_CUDA(cudaMemcpyAsync(d_fi, hfi.data(), sizeof(FeatItem) * g, cudaMemcpyHostToDevice, st));
+    FFC_CUDA(cudaMemcpyAsync(d_si, hsi.data(), sizeof(SelectItem) * g, cudaMemcpyHostToDevice, st));
+    if (whole) {
+      rc = launch_far_lists(X, R->dtype, d, d_far, g, R->N, tcnt, st);
+      if (rc == FFC_OK) {
+        copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, cnt, fc);
+        FFC_CUDA(cudaGetLastError());
+      }
+    } else {
+      rc = launch_sample(X, R->dtype, d, d_smp, g, R->N, P.pool_rows, P.seed, cnt, fc, sst, scratch, st);
+    }
+    if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, tot, P.proj_dev, feats, st);
+    if (rc == FFC_OK) rc = launch_mlp_forward(P.mlp_dev, feats, tot, logits, st);
+    if (rc == FFC_OK) rc = launch_select(d_si, g, P.s_max, P.seed, st);
+    if (rc != FFC_OK) return rc;
+    copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, fc, R->lfar + o0);
+    FFC_CUDA(cudaGetLastError());
+    if (R->prof.enabled) R->prof.launches += (whole ? 4 : 1) + 4;
+    o0 = o1;
+  }
+  return FFC_OK;
+}
+
 int group_size_tree(int64_t s, int64_t n, int64_t elems) {
   int64_t g = (s * n + elems - 1) / std::max<int64_t>(elems, 1);
   g = std::min<int64_t>(g, std::max<int64_t>(1, n / 4));
@@ -254,6 +394,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += trsm_tiles(R->count_h[items[q]]); }
 
   const int64_t scratch_ctas = std::min<int64_t>(W, 2048);
+  const bool learned = P.sampler == FFC_SAMPLE_LEARNED;
   Layout L;
   const size_t o_si = L.add<SampleItem>(W), o_ei = L.add<EvalItem>(W), o_qi = L.add<CpqrItem>(W),
                o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(G), o_coff = L.add<int32_t>(grid + 1),
@@ -320,7 +461,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     si.x_c = tree->centroid_dev + node * d; si.thr2 = 0.0; si.radius = tree->radius_dev + node; si.xi = P.xi;
     si.s = s_nom; si.stream_id = (uint64_t)node; si.rows = R->rows + R->rows_off_h[o];
     EvalItem& ei = he[q];
-    ei.rows = si.rows; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
+    ei.rows = R->rows + R->rows_off_h[o]; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
     ei.center = P.precision == FFC_MIXED ? tree->centroid_dev + node * d : nullptr;
     ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom);
     CpqrItem& qi = hq[q];
@@ -353,8 +494,14 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
 
   const bool prof = R->prof.enabled != 0;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[0], st));
-  ffc_status rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, st);
-  if (rc != FFC_OK) return rc;
+  ffc_status rc = FFC_OK;
+  if (learned) {   // the node's best s_max rows were drawn once per call: take the first s_nom
+    learned_round_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, oidx, s_nom, R->lcount, R->lfar, s_out, fc);
+    FFC_CUDA(cudaGetLastError());
+  } else {
+    rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, st);
+    if (rc != FFC_OK) return rc;
+  }
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[1], st));
   patch_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
   rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
@@ -432,11 +579,13 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");
   FFC_REQUIRE(P.min_level >= 0 && P.min_level <= tree->depth, "ffc_compress_tree: min_level out of range");
-  ffc_kernel kk = P.kernel;
-  if (kk.kind == FFC_GAUSSIAN) FFC_REQUIRE(kk.h > 0.0, "Gaussian bandwidth must be > 0");
-  else if (kk.kind == FFC_LAPLACE) FFC_REQUIRE(d != 2, "d = 2 Laplace kernel unsupported");
-  else if (kk.kind == FFC_POLYNOMIAL) FFC_REQUIRE(kk.h != 0.0 && kk.p >= 1, "bad polynomial kernel");
-  else FFC_REQUIRE(false, "unknown kernel kind");
+  if (!kernel_ok(P.kernel, d)) return FFC_E_INVALID;
+  FFC_REQUIRE(P.sampler == FFC_SAMPLE_UNIFORM || P.sampler == FFC_SAMPLE_LEARNED, "ffc_compress_tree: bad sampler");
+  if (P.sampler == FFC_SAMPLE_LEARNED) {
+    FFC_REQUIRE(P.pool_rows == 0 || P.pool_rows >= P.s_max,
+                "ffc_compress_tree: pool_rows must be 0 (whole far field) or >= s_max");
+    FFC_REQUIRE(P.proj_dev && P.mlp_dev, "ffc_compress_tree: the learned sampler needs proj_dev and mlp_dev");
+  }
   cudaStream_t st = as_stream(stream);
 
   ffc_tree_result* R = *result;
@@ -474,6 +623,19 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   int64_t s_nom = P.s0;
   R->rounds = 0;
   if (R->prof.enabled) R->prof.calls += 1;
+  if (P.sampler == FFC_SAMPLE_LEARNED) {
+    const bool prof = R->prof.enabled != 0;
+    if (prof) FFC_CUDA(cudaEventRecord(R->ev[0], st));
+    ffc_status rc = propose_tree(R, points_perm_dev, tree, st);
+    if (rc != FFC_OK) return rc;
+    if (prof) {
+      FFC_CUDA(cudaEventRecord(R->ev[1], st));
+      FFC_CUDA(cudaEventSynchronize(R->ev[1]));
+      float ms = 0.f;
+      FFC_CUDA(cudaEventElapsedTime(&ms, R->ev[0], R->ev[1]));
+      R->prof.ms[0] += ms;
+    }
+  }
   while (!active.empty()) {
     ffc_status rc = run_round(R, points_perm_dev, tree, active, s_nom, again, st);
     if (rc != FFC_OK) return rc;
@@ -502,6 +664,8 @@ void ffc_tree_result_free(ffc_tree_result* R) {
   if (!R) return;
   if (R->out_mem) cudaFree(R->out_mem);
   if (R->ws) cudaFree(R->ws);
+  if (R->pws) cudaFree(R->pws);
+  if (R->lcount) cudaFree(R->lcount);
   for (auto& e : R->ev)
     if (e) cudaEventDestroy(e);
   delete R;

@@ -35,8 +35,12 @@ EXPORTS = (
     "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
     "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
     "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
-    "ffc_id_noalloc",
+    "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
+    "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage",
 )
+MLP_PARAMS = 18305
+N_FEATURES = 12
+MAX_DRAW = 8192
 PROFILE_PHASES = ("sample", "eval", "qr", "trsm", "bookkeeping")
 
 
@@ -58,7 +62,8 @@ class c_tree(ctypes.Structure):
 class c_params(ctypes.Structure):
     _fields_ = [("kernel", c_kernel), ("precision", ctypes.c_int32), ("min_level", ctypes.c_int32),
                 ("s0", ctypes.c_int32), ("s_max", ctypes.c_int32), ("tol", ctypes.c_double),
-                ("xi", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
+                ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -119,6 +124,14 @@ def lib() -> ctypes.CDLL:
     L.ffc_tree_profile_enable.argtypes = [vp, i32]
     L.ffc_tree_profile_reset.argtypes = [vp]
     L.ffc_tree_profile_get.argtypes = [vp, ctypes.POINTER(c_tree_profile)]
+    L.ffc_features.argtypes = [c_kernel, vp, i32, i64, i32, vp, i64, vp, dbl, vp, vp, vp]
+    L.ffc_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.ffc_sample_weighted.argtypes = [vp, vp, i64, i64, u64, u64, vp, vp]
+    L.ffc_propose_rows.argtypes = [c_kernel, vp, i32, i64, i32, vp, dbl, dbl, i64, i64, vp, vp, i64, i64, u64, u64,
+                                   vp, pi64, pi64, vp]
+    L.ffc_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, i64, pdbl, vp, vp]
+    L.ffc_adam_step.argtypes = [vp, vp, vp, vp, i64, i64, dbl, dbl, dbl, dbl, vp]
+    L.ffc_leverage.argtypes = [vp, i64, i64, i64, dbl, i64, vp, vp, pi64, vp]
     for name in EXPORTS:
         if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
             getattr(L, name).restype = ctypes.c_int
@@ -305,12 +318,19 @@ class TreeResult:
 
 
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
-                      s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None) -> TreeResult:
+                      s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
+                      proposal: tuple | None = None, pool_rows=0) -> TreeResult:
+    """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
+    sampler, proj_p, mlp_p = 0, None, None
+    if proposal is not None:
+        mlp, proj = proposal
+        _dev(mlp, "proposal params"), _dev(proj, "proposal proj")
+        sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
-                 ctypes.c_uint64(int(seed)))
+                 ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p)
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
@@ -352,3 +372,90 @@ def tree_result_to_host(res: TreeResult) -> dict:
     """numpy copies of a TreeResult's per-node outputs."""
     views = tree_result_views(res)
     return {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in views.items()}
+
+
+# ---------------------------------------------------------------------------
+# learned row proposal and its training
+
+
+def ffc_features(kernel: Kernel, Y, rows, x_c, radius, proj, stream=None):
+    """R x 12 float32 features of the targets Y[rows] for a node (x_c, radius)."""
+    _dev(Y, "Y"), _dev(rows, "rows"), _dev(x_c, "x_c"), _dev(proj, "proj")
+    M, d = Y.shape
+    R = rows.numel()
+    F = torch.empty((max(R, 1), N_FEATURES), dtype=torch.float32, device=Y.device)
+    _check(lib().ffc_features(kernel.c_struct(), _ptr(Y), _dtype_code(Y), M, d, _ptr(rows), R, _ptr(x_c),
+                              float(radius), _ptr(proj), _ptr(F), _stream(stream)))
+    return F[:R]
+
+
+def ffc_mlp_forward(params, feats, stream=None):
+    """Logits (float32, one per feature row) of the proposal network."""
+    _dev(params, "params"), _dev(feats, "feats")
+    R = feats.shape[0]
+    out = torch.empty(max(R, 1), dtype=torch.float32, device=feats.device)
+    _check(lib().ffc_mlp_forward(_ptr(params), _ptr(feats), R, _ptr(out), _stream(stream)))
+    return out[:R]
+
+
+def ffc_sample_weighted(pool, logits, s, seed, stream_id, stream=None):
+    """min(s, P) pool rows drawn without replacement with the mixed network weights."""
+    _dev(pool, "pool"), _dev(logits, "logits")
+    P = pool.numel()
+    n = min(int(s), P)
+    rows = torch.empty(max(n, 1), dtype=torch.int64, device=pool.device)
+    _check(lib().ffc_sample_weighted(_ptr(pool), _ptr(logits), P, int(s), ctypes.c_uint64(int(seed)),
+                                     ctypes.c_uint64(int(stream_id)), _ptr(rows), _stream(stream)))
+    return rows[:n]
+
+
+def ffc_propose_rows(kernel: Kernel, Y, s, seed, stream_id, x_c, radius, proj, params, xi=1.0, ex_begin=0,
+                     ex_end=0, pool_rows=0, stream=None):
+    """Learned proposal of s far-field rows (pool_rows = 0: the whole far field is the candidate pool).
+
+    Returns (rows int64[s_out], far_count, status)."""
+    _dev(Y, "Y"), _dev(x_c, "x_c"), _dev(proj, "proj"), _dev(params, "params")
+    M, d = Y.shape
+    rows = torch.empty(max(int(s), 1), dtype=torch.int64, device=Y.device)
+    s_out, fc = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _check(lib().ffc_propose_rows(kernel.c_struct(), _ptr(Y), _dtype_code(Y), M, d, _ptr(x_c), float(radius),
+                                       float(xi), int(ex_begin), int(ex_end), _ptr(proj), _ptr(params),
+                                       int(pool_rows), int(s), ctypes.c_uint64(int(seed)),
+                                       ctypes.c_uint64(int(stream_id)), _ptr(rows), ctypes.byref(s_out),
+                                       ctypes.byref(fc), _stream(stream)))
+    return rows[: s_out.value], fc.value, st
+
+
+def ffc_mlp_loss_grad(params, feats, targets, node_off, grad=None, stream=None):
+    """(loss, grad float32[MLP_PARAMS]) of the per-node softmax cross-entropy (targets float64)."""
+    for t, nm in ((params, "params"), (feats, "feats"), (targets, "targets"), (node_off, "node_off")):
+        _dev(t, nm)
+    if grad is None:
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=params.device)
+    loss = ctypes.c_double(0.0)
+    _check(lib().ffc_mlp_loss_grad(_ptr(params), _ptr(feats), _ptr(targets), _ptr(node_off), node_off.numel() - 1,
+                                   feats.shape[0], ctypes.byref(loss), _ptr(grad), _stream(stream)))
+    return loss.value, grad
+
+
+def ffc_adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """In-place Adam update of params (float32) with moments m, v (float32)."""
+    for t, nm in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v")):
+        _dev(t, nm)
+    _check(lib().ffc_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def ffc_leverage(Kcm, eps=1e-6, r_fixed=0, stream=None):
+    """Leverage scores of the rows of a column-major m x n block given as its (n, m) storage.
+
+    Returns (lev float64[m], sigma float64[n] decreasing, rank, status).
+    """
+    _dev(Kcm, "K")
+    n, m = Kcm.shape
+    lev = torch.empty(max(m, 1), dtype=torch.float64, device=Kcm.device)
+    sig = torch.empty(max(n, 1), dtype=torch.float64, device=Kcm.device)
+    rank = ctypes.c_int64(0)
+    st = _check(lib().ffc_leverage(_ptr(Kcm), m, n, m, float(eps), int(r_fixed), _ptr(lev), _ptr(sig),
+                                   ctypes.byref(rank), _stream(stream)))
+    return lev[:m], sig[:n], rank.value, st

@@ -122,3 +122,38 @@ def test_compress_full_size_gaussian_d16():
     nodes = sorted(g.choice(out["node"], 12, replace=False).tolist())
     _compare_nodes(out, t_o, Pp, o_kernels.Kernel(o_kernels.GAUSSIAN, h=2.0), 1e-6, nodes, 128, 2048,
                    check_error=False)
+
+
+def test_compress_tree_learned_sampler_matches_oracle():
+    """Learned sampler, FP64: nodes whose drawn rows equal the oracle's (the FP32
+    logits may swap rows whose keys tie within their rounding) must have the
+    oracle's ID; every node's rows are distinct far-field rows."""
+    from oracle.sampling import far_field_mask
+    P = workloads.gaussian_mixture(N=4096, d=4, k=4, seed=3)
+    t_o, t_g = _build_both(P, 256)
+    Pp = P[t_o.perm]
+    ko = o_kernels.Kernel(o_kernels.GAUSSIAN, h=1.0)
+    g = np.random.default_rng(1)
+    theta = (workloads.mlp_init(4).astype(np.float64) + 0.05 * g.standard_normal(workloads.MLP_N_PARAMS))
+    theta = theta.astype(np.float32)
+    proj = workloads.projections(4, seed=5)
+    res = ffc.ffc_compress_tree(cu(Pp), t_g, ffc.Kernel(ffc.GAUSSIAN, h=1.0), tol=1e-6, s0=32, s_max=512,
+                                proposal=(cu(theta), cu(proj)))
+    out = ffc.tree_result_to_host(res)
+    prop = o_compress.Proposal(theta, proj)
+    nodes = [i for i in range(t_o.n_nodes) if t_o.level[i] >= 2]
+    same = 0
+    for i, node in enumerate(out["node"]):
+        node = int(node)
+        b, n = int(t_o.begin[node]), int(t_o.count[node])
+        s = int(out["s"][i])
+        rows = out["rows"][out["rows_off"][i]: out["rows_off"][i] + s]
+        far = far_field_mask(Pp, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n)
+        assert np.unique(rows).size == s and np.all(far[rows])
+        ref = o_compress.compress_node(Pp, t_o, node, ko, 1e-6, 0, 32, 512, proposal=prop)
+        if ref.s != s or not np.array_equal(rows, ref.rows):
+            continue
+        same += 1
+        assert int(out["status"][i]) == ref.status and int(out["rank"][i]) == ref.rank, node
+        assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
+    assert same >= 0.8 * len(nodes), (same, len(nodes))
