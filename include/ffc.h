@@ -352,8 +352,8 @@ ffc_status ffc_tree_profile_get(const ffc_tree_result* result, ffc_tree_profile*
  *        (rho/r)^(d-2); polynomial (y.x_c/h + c)^p / (||y|| ||x_c||/h + c)^p
  *   f2 = ||y|| / rho;  f3 = rho / h (h = 1 for Laplace)
  *   f4..f11 = <g_k, delta> / rho for the rows g_k of proj_dev (8 x d FP64).
- * The O(d) sums run in FP32 on coordinates rounded to FP32, the per-row
- * transforms in FP64; stored as FP32 row-major R x 12 in feats_dev.
+ * Computed in FP32 (coordinates, centroid and directions rounded to FP32);
+ * stored as FP32 row-major R x 12 in feats_dev. d <= 5000.
  * rows_dev: R indices in [0, M). x_c_dev: d doubles. Asynchronous.
  */
 ffc_status ffc_features(ffc_kernel k, const void* Y_dev, int32_t dtype, int64_t M, int32_t d,
@@ -434,6 +434,17 @@ ffc_status ffc_adam_step(float* params_dev, const float* grad_dev, float* m_dev,
  */
 ffc_status ffc_leverage(const double* K_dev, int64_t m, int64_t n, int64_t ldk, double eps, int64_t r_fixed,
                         double* lev_dev, double* sigma_dev, int64_t* rank_host, void* stream);
+
+/*
+ * ffc_leverage_batched - ffc_leverage of B blocks at once (the eigen-
+ * decompositions run concurrently, one CTA per block). Host arrays of B
+ * entries: K_dev[b] (m[b] x n[b], ld ldk[b]), lev_dev[b] (m[b]),
+ * sigma_dev[b] (n[b]); rank_host[b] receives r. Synchronises; returns the
+ * first non-OK status (FFC_E_TOL_NOT_REACHED if some Jacobi did not converge).
+ */
+ffc_status ffc_leverage_batched(int32_t B, const double* const* K_dev, const int64_t* m, const int64_t* n,
+                                const int64_t* ldk, double eps, int64_t r_fixed, double* const* lev_dev,
+                                double* const* sigma_dev, int64_t* rank_host, void* stream);
 
 #ifdef __cplusplus
 }

@@ -209,8 +209,20 @@ ffc_status ffc_adam_step(float* params_dev, const float* grad_dev, float* m_dev,
 ffc_status ffc_leverage(const double* K_dev, int64_t m, int64_t n, int64_t ldk, double eps, int64_t r_fixed,
                         double* lev_dev, double* sigma_dev, int64_t* rank_host, void* stream) {
   FFC_REQUIRE(K_dev && lev_dev && sigma_dev, "ffc_leverage: null pointer");
-  return launch_leverage(K_dev, m, n, ldk, eps, r_fixed, lev_dev, sigma_dev, rank_host, nullptr,
-                         as_stream(stream));
+  int64_t r = 0;
+  ffc_status rc = launch_leverage_batched(1, &K_dev, &m, &n, &ldk, eps, r_fixed, &lev_dev, &sigma_dev, &r, nullptr,
+                                          as_stream(stream));
+  if (rank_host) *rank_host = r;
+  return rc;
+}
+
+ffc_status ffc_leverage_batched(int32_t B, const double* const* K_dev, const int64_t* m, const int64_t* n,
+                                const int64_t* ldk, double eps, int64_t r_fixed, double* const* lev_dev,
+                                double* const* sigma_dev, int64_t* rank_host, void* stream) {
+  FFC_REQUIRE(B >= 1 && K_dev && m && n && ldk && lev_dev && sigma_dev && rank_host,
+              "ffc_leverage_batched: null argument");
+  return launch_leverage_batched(B, K_dev, m, n, ldk, eps, r_fixed, lev_dev, sigma_dev, rank_host, nullptr,
+                                 as_stream(stream));
 }
 
 }  // extern "C"

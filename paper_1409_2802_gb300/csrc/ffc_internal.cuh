@@ -198,8 +198,9 @@ ffc_status launch_build_tree(const void* points, int dtype, int64_t N, int d, in
                              const int64_t* begin_host, const int64_t* count_host, const int64_t* begin_dev,
                              const int64_t* count_dev, double* centroid, double* radius, cudaStream_t st);
 
+// cap_max: largest item cap (rows reserved per item)
 ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const FeatItem* items_dev, int n_items,
-                           int64_t total, const double* proj, float* out, cudaStream_t st);
+                           int64_t cap_max, const double* proj, float* out, cudaStream_t st);
 ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st);
 // keep_max: largest min(s, P) over the items (<= 8192); any pool size P
 ffc_status launch_select(const SelectItem* items_dev, int n_items, int64_t keep_max, uint64_t seed, cudaStream_t st);
@@ -213,8 +214,9 @@ ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const d
 int mlp_backward_grid(int64_t R);
 ffc_status launch_adam(float* theta, const float* g, float* m, float* v, int64_t n, int64_t step, double lr,
                        double b1, double b2, double eps, cudaStream_t st);
-ffc_status launch_leverage(const double* K, int64_t m, int64_t n, int64_t ldk, double eps, int64_t r_fixed,
-                           double* lev, double* sigma, int64_t* rank_host, int32_t* sweeps_host, cudaStream_t st);
+ffc_status launch_leverage_batched(int B, const double* const* K, const int64_t* m, const int64_t* n,
+                                   const int64_t* ldk, double eps, int64_t r_fixed, double* const* lev,
+                                   double* const* sigma, int64_t* rank_host, int32_t* sweeps_host, cudaStream_t st);
 
 // host helpers
 int sm_count();

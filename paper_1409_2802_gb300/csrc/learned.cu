@@ -40,75 +40,111 @@ __device__ __forceinline__ float gelu_prime_f(float z) {
 }
 
 // ----------------------------------------------------------------------------
-// features (one warp per row)
+// features
+//
+// Grid: blockIdx.y = item, blockIdx.x strides over the item's rows. The
+// node's centroid and the 8 projection directions are staged in shared
+// memory as FP32. Small d: one thread per row; large d: one warp per row.
+// All sums and transforms are FP32 (coordinates rounded to FP32 first).
 
-template <typename TP>
-__global__ void __launch_bounds__(256) features_kernel(const TP* __restrict__ Y, int d, const FeatItem* items,
-                                                       int n_items, int64_t total, ffc_kernel k,
-                                                       const double* __restrict__ proj, float* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t f = warp_global; f < total; f += nwarps) {
-    int lo = 0, hi = n_items - 1;
-    while (lo < hi) {              // last item with out_begin <= f
-      int mid = (lo + hi + 1) >> 1;
-      if (items[mid].out_begin <= f) lo = mid; else hi = mid - 1;
-    }
-    const FeatItem& it = items[lo];
-    const int64_t i = f - it.out_begin;
-    const int64_t cnt = it.count ? *it.count : it.cap;
-    float* o = out + f * NF;
-    if (i >= cnt) {
-      if (lane < NF) o[lane] = 0.0f;
-      continue;
-    }
-    const TP* y = Y + it.rows[i] * (int64_t)d;
-    const double* xc = it.x_c;
-    // O(d) sums in FP32 (coordinates rounded to FP32 first); the per-row
-    // transforms below are FP64
-    float sdd = 0.0f, syy = 0.0f, syx = 0.0f, sxx = 0.0f;
-    float sp[8];
+constexpr int FEAT_THREADS = 256;
+constexpr int FEAT_SMALL_D = 64;
+
+struct FeatSums { float dd, yy, yx, xx, p[8]; };
+
+__device__ __forceinline__ void feature_values(const FeatSums& S, float rho, ffc_kernel k, int d, float out[NF]) {
+  const float r = sqrtf(S.dd);
+  const float inv_rho = 1.0f / rho;
+  out[0] = r * inv_rho;
+  float kc;
+  if (k.kind == FFC_GAUSSIAN) {
+    kc = expf(-S.dd / (2.0f * (float)(k.h * k.h)));
+  } else if (k.kind == FFC_LAPLACE) {
+    kc = exp2f((float)(d - 2) * log2f(rho / r));
+  } else {
+    const float num = S.yx / (float)k.h + (float)k.c;
+    const float den = sqrtf(S.yy) * sqrtf(S.xx) / (float)k.h + (float)k.c;
+    kc = powf(num / den, (float)k.p);
+  }
+  out[1] = kc;
+  out[2] = sqrtf(S.yy) * inv_rho;
+  out[3] = rho / (k.kind == FFC_LAPLACE ? 1.0f : (float)k.h);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sp[q] = 0.0f;
-    for (int c = lane; c < d; c += 32) {
-      const float yv = (float)__ldg(y + c), xv = (float)xc[c];
-      const float dl = yv - xv;
-      sdd = fmaf(dl, dl, sdd); syy = fmaf(yv, yv, syy); syx = fmaf(yv, xv, syx); sxx = fmaf(xv, xv, sxx);
+  for (int q = 0; q < 8; ++q) out[4 + q] = S.p[q] * inv_rho;
+}
+
+template <typename TP, bool WARP_PER_ROW>
+__global__ void __launch_bounds__(FEAT_THREADS) features_kernel(const TP* __restrict__ Y, int d, const FeatItem* items,
+                                                                ffc_kernel k, const double* __restrict__ proj,
+                                                                float* __restrict__ out) {
+  extern __shared__ __align__(16) float fsm[];   // xc[d], proj[8][d]
+  const FeatItem& it = items[blockIdx.y];
+  const int64_t cnt = it.count ? *it.count : it.cap;
+  const int64_t per_cta = WARP_PER_ROW ? FEAT_THREADS / 32 : FEAT_THREADS;
+  if ((int64_t)blockIdx.x * per_cta >= it.cap) return;
+  float* xc = fsm;
+  float* pj = fsm + d;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) xc[c] = (float)it.x_c[c];
+  for (int c = threadIdx.x; c < 8 * d; c += blockDim.x) pj[c] = (float)proj[c];
+  __syncthreads();
+  float rho = (float)(it.radius ? *it.radius : it.radius_host);
+  if (!(rho > 0.0f)) rho = 1.0f;
+  const int64_t stride = (int64_t)gridDim.x * per_cta;
+  if (!WARP_PER_ROW) {
+    for (int64_t i = (int64_t)blockIdx.x * per_cta + threadIdx.x; i < it.cap; i += stride) {
+      float* o = out + (it.out_begin + i) * NF;
+      if (i >= cnt) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) sp[q] = fmaf((float)proj[(int64_t)q * d + c], dl, sp[q]);
+        for (int f = 0; f < NF; ++f) o[f] = 0.0f;
+        continue;
+      }
+      const TP* y = Y + it.rows[i] * (int64_t)d;
+      FeatSums S{0.f, 0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+      for (int c = 0; c < d; ++c) {
+        const float yv = (float)y[c], xv = xc[c];
+        const float dl = yv - xv;
+        S.dd = fmaf(dl, dl, S.dd); S.yy = fmaf(yv, yv, S.yy); S.yx = fmaf(yv, xv, S.yx); S.xx = fmaf(xv, xv, S.xx);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S.p[q] = fmaf(pj[q * d + c], dl, S.p[q]);
+      }
+      float v[NF];
+      feature_values(S, rho, k, d, v);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) o[f] = v[f];
     }
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i = (int64_t)blockIdx.x * per_cta + warp; i < it.cap; i += stride) {
+      float* o = out + (it.out_begin + i) * NF;
+      if (i >= cnt) {
+        if (lane < NF) o[lane] = 0.0f;
+        continue;
+      }
+      const TP* y = Y + it.rows[i] * (int64_t)d;
+      FeatSums S{0.f, 0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+      for (int c = lane; c < d; c += 32) {
+        const float yv = (float)__ldg(y + c), xv = xc[c];
+        const float dl = yv - xv;
+        S.dd = fmaf(dl, dl, S.dd); S.yy = fmaf(yv, yv, S.yy); S.yx = fmaf(yv, xv, S.yx); S.xx = fmaf(xv, xv, S.xx);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      sdd += __shfl_xor_sync(0xffffffffu, sdd, off);
-      syy += __shfl_xor_sync(0xffffffffu, syy, off);
-      syx += __shfl_xor_sync(0xffffffffu, syx, off);
-      sxx += __shfl_xor_sync(0xffffffffu, sxx, off);
+        for (int q = 0; q < 8; ++q) S.p[q] = fmaf(pj[q * d + c], dl, S.p[q]);
+      }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) sp[q] += __shfl_xor_sync(0xffffffffu, sp[q], off);
+      for (int off = 16; off > 0; off >>= 1) {
+        S.dd += __shfl_xor_sync(0xffffffffu, S.dd, off);
+        S.yy += __shfl_xor_sync(0xffffffffu, S.yy, off);
+        S.yx += __shfl_xor_sync(0xffffffffu, S.yx, off);
+        S.xx += __shfl_xor_sync(0xffffffffu, S.xx, off);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S.p[q] += __shfl_xor_sync(0xffffffffu, S.p[q], off);
+      }
+      if (lane == 0) {
+        float v[NF];
+        feature_values(S, rho, k, d, v);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) o[f] = v[f];
+      }
     }
-    double rho = it.radius ? *it.radius : it.radius_host;
-    if (!(rho > 0.0)) rho = 1.0;
-    const double dd = sdd, r = sqrt(dd);
-    double v = 0.0;
-    if (lane == 0) {
-      v = r / rho;
-    } else if (lane == 1) {
-      if (k.kind == FFC_GAUSSIAN) v = exp(-dd / (2.0 * k.h * k.h));
-      else if (k.kind == FFC_LAPLACE) v = pow(rho / r, (double)(d - 2));
-      else v = pow((double)syx / k.h + k.c, (double)k.p) /
-               pow(sqrt((double)syy) * sqrt((double)sxx) / k.h + k.c, (double)k.p);
-    } else if (lane == 2) {
-      v = sqrt((double)syy) / rho;
-    } else if (lane == 3) {
-      v = rho / (k.kind == FFC_LAPLACE ? 1.0 : k.h);
-    } else if (lane < NF) {
-      float pv = sp[0];
-#pragma unroll
-      for (int q = 1; q < 8; ++q) if (lane - 4 == q) pv = sp[q];
-      v = (double)pv / rho;
-    }
-    if (lane < NF) o[lane] = (float)v;
   }
 }
 
@@ -669,14 +705,30 @@ static int net_grid(int64_t R, int per_sm) {
 }
 
 ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const FeatItem* items_dev, int n_items,
-                           int64_t total, const double* proj, float* out, cudaStream_t st) {
-  if (total <= 0 || n_items <= 0) return FFC_OK;
-  const int64_t warps = total;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sm_count() * 16));
-  if (dtype == FFC_F64)
-    features_kernel<double><<<grid, 256, 0, st>>>((const double*)Y, d, items_dev, n_items, total, k, proj, out);
-  else
-    features_kernel<float><<<grid, 256, 0, st>>>((const float*)Y, d, items_dev, n_items, total, k, proj, out);
+                           int64_t cap_max, const double* proj, float* out, cudaStream_t st) {
+  if (cap_max <= 0 || n_items <= 0) return FFC_OK;
+  FFC_REQUIRE(n_items <= 65535, "features: at most 65535 items per launch");
+  const size_t smem = (size_t)9 * d * sizeof(float);
+  FFC_REQUIRE(smem <= 200 * 1024, "features: d = %d too large", d);
+  const bool warp_rows = d > FEAT_SMALL_D;
+  const int64_t per_cta = warp_rows ? FEAT_THREADS / 32 : FEAT_THREADS;
+  // enough CTAs for about 8 per SM over all items, each striding over its item
+  int64_t gx = std::max<int64_t>(1, std::min<int64_t>((cap_max + per_cta - 1) / per_cta,
+                                                      std::max<int64_t>(1, (int64_t)sm_count() * 8 / n_items)));
+  gx = std::min<int64_t>(gx, 65535);
+  const dim3 grid((unsigned)gx, (unsigned)n_items);
+#define FFC_FEAT_LAUNCH(TP, WR)                                                                              \
+  do {                                                                                                       \
+    auto kfn = features_kernel<TP, WR>;                                                                      \
+    FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));             \
+    kfn<<<grid, FEAT_THREADS, smem, st>>>((const TP*)Y, d, items_dev, k, proj, out);                         \
+  } while (0)
+  if (dtype == FFC_F64) {
+    if (warp_rows) FFC_FEAT_LAUNCH(double, true); else FFC_FEAT_LAUNCH(double, false);
+  } else {
+    if (warp_rows) FFC_FEAT_LAUNCH(float, true); else FFC_FEAT_LAUNCH(float, false);
+  }
+#undef FFC_FEAT_LAUNCH
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
 }

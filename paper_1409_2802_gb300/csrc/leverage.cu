@@ -16,6 +16,7 @@
 // not resolved. Training targets need far less.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ffc_internal.cuh"
 
@@ -26,6 +27,17 @@ constexpr int G_ROWS = 16;           // rows staged per step
 constexpr int LEV_MAX_N = 1024;
 constexpr int JAC_THREADS = 1024;
 constexpr int JAC_MAX_SWEEPS = 40;
+
+struct LevJob {
+  double* G;         // n x n Gram matrix, overwritten by the eigenvalues
+  double* V;         // n x n eigenvectors
+  double* W;         // n x r: V_r Sigma_r^-1
+  int* perm;         // eigenpairs by decreasing eigenvalue
+  double* sigma;     // n singular values, decreasing
+  int64_t* rank;     // device
+  int32_t* sweeps;   // device
+  int n, pad;
+};
 
 // Gpart[c] (n x n row-major) = K(rows of chunk c, :)^T K(rows of chunk c, :),
 // computed for the upper tiles (ti <= tj) and mirrored.
@@ -111,8 +123,12 @@ __device__ __forceinline__ void round_pair(int np, int k, int i, int& p, int& q)
 // |g_pq| <= 1e-17 max_k g_kk (below the rounding of the Gram matrix itself).
 // All pairs of a round are disjoint, so the update G'[P_i, P_k] =
 // J_i^T G[P_i, P_k] J_k of every 2 x 2 block reads only that block.
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(double* __restrict__ G, double* __restrict__ V, int n,
-                                                             int32_t* __restrict__ sweeps_out) {
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const LevJob* jobs) {
+  const LevJob& jb = jobs[blockIdx.x];
+  double* __restrict__ G = jb.G;
+  double* __restrict__ V = jb.V;
+  const int n = jb.n;
+  int32_t* sweeps_out = jb.sweeps;
   __shared__ double cs[LEV_MAX_N / 2], sn[LEV_MAX_N / 2];
   __shared__ int pp[LEV_MAX_N / 2], qq[LEV_MAX_N / 2];
   __shared__ unsigned char act[LEV_MAX_N / 2];
@@ -198,10 +214,15 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(double* __restrict_
 
 // Order the eigenpairs by decreasing eigenvalue (ties: lower index first),
 // sigma_out[k] = sqrt(max(lambda, 0)), rank r, and W = V_r Sigma_r^-1 (n x r).
-__global__ void __launch_bounds__(1024) eig_order_kernel(const double* __restrict__ G, const double* __restrict__ V,
-                                                         int n, double eps, int64_t r_fixed, double* __restrict__ sigma,
-                                                         int* __restrict__ perm, double* __restrict__ W,
-                                                         int64_t* __restrict__ rank_out) {
+__global__ void __launch_bounds__(1024) eig_order_kernel(const LevJob* jobs, double eps, int64_t r_fixed) {
+  const LevJob& jb = jobs[blockIdx.x];
+  const double* __restrict__ G = jb.G;
+  const double* __restrict__ V = jb.V;
+  const int n = jb.n;
+  double* __restrict__ sigma = jb.sigma;
+  int* __restrict__ perm = jb.perm;
+  double* __restrict__ W = jb.W;
+  int64_t* __restrict__ rank_out = jb.rank;
   __shared__ int r_sh;
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
     const double la = G[(int64_t)a * n + a];
@@ -235,7 +256,9 @@ __global__ void __launch_bounds__(1024) eig_order_kernel(const double* __restric
 
 // lev[i] = sum_k (K(i, :) W(:, k))^2, 64 rows per CTA, W in 64-column tiles.
 __global__ void __launch_bounds__(256) leverage_kernel(const double* __restrict__ K, int64_t m, int n, int64_t ldk,
-                                                       const double* __restrict__ W, int r, double* __restrict__ lev) {
+                                                       const double* __restrict__ W, const int64_t* __restrict__ rank,
+                                                       double* __restrict__ lev) {
+  const int r = (int)*rank;
   __shared__ double Ks[G_ROWS][GT];   // [j][row]
   __shared__ double Ws[G_ROWS][GT];   // [j][col]
   __shared__ double red[GT][17];
@@ -288,54 +311,79 @@ __global__ void __launch_bounds__(256) leverage_kernel(const double* __restrict_
   }
 }
 
-ffc_status launch_leverage(const double* K, int64_t m, int64_t n64, int64_t ldk, double eps, int64_t r_fixed,
-                           double* lev, double* sigma, int64_t* rank_host, int32_t* sweeps_host, cudaStream_t st) {
-  FFC_REQUIRE(n64 >= 1 && n64 <= LEV_MAX_N, "leverage: need 1 <= n <= %d", LEV_MAX_N);
-  FFC_REQUIRE(m >= 1 && ldk >= m, "leverage: need m >= 1 and ldk >= m");
-  const int n = (int)n64;
-  const int nt = (n + GT - 1) / GT;
-  const int pairs = nt * (nt + 1) / 2;
-  // row chunks: about 4 CTAs per SM over all tile pairs, chunks of >= 1024 rows
-  int64_t chunks = std::max<int64_t>(1, (4LL * sm_count()) / pairs);
-  chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, m / 1024));
-  chunks = std::min<int64_t>(chunks, 65535);
-  const int64_t chunk_rows = (m + chunks - 1) / chunks;
-  const int64_t nn = (int64_t)n * n;
+ffc_status launch_leverage_batched(int B, const double* const* K, const int64_t* m, const int64_t* n,
+                                   const int64_t* ldk, double eps, int64_t r_fixed, double* const* lev,
+                                   double* const* sigma, int64_t* rank_host, int32_t* sweeps_host, cudaStream_t st) {
+  FFC_REQUIRE(B >= 1, "leverage: need B >= 1");
+  for (int b = 0; b < B; ++b) {
+    FFC_REQUIRE(n[b] >= 1 && n[b] <= LEV_MAX_N, "leverage: need 1 <= n <= %d", LEV_MAX_N);
+    FFC_REQUIRE(m[b] >= 1 && ldk[b] >= m[b], "leverage: need m >= 1 and ldk >= m");
+    FFC_REQUIRE(K[b] && lev[b] && sigma[b], "leverage: null pointer");
+  }
+  // per block: G, V, W (n^2 each), perm (n), rank, sweeps; one Gram partial buffer shared in stream order
+  size_t per = 0, gpart = 0;
+  std::vector<size_t> off(B);
+  std::vector<int64_t> chunks(B), crow(B);
+  for (int b = 0; b < B; ++b) {
+    const int64_t nn = n[b] * n[b];
+    off[b] = per;
+    per += ((3 * nn * sizeof(double) + n[b] * sizeof(int) + 64) + 255) & ~size_t(255);
+    const int nt = (int)((n[b] + GT - 1) / GT);
+    const int pairs = nt * (nt + 1) / 2;
+    int64_t c = std::max<int64_t>(1, (4LL * sm_count()) / pairs);
+    c = std::min<int64_t>(c, std::max<int64_t>(1, m[b] / 1024));
+    c = std::min<int64_t>(c, 65535);
+    chunks[b] = c;
+    crow[b] = (m[b] + c - 1) / c;
+    gpart = std::max(gpart, (size_t)(c * nn) * sizeof(double));
+  }
+  const size_t jobs_off = (per + gpart + 255) & ~size_t(255);
   char* ws = nullptr;
-  const size_t bytes = (size_t)(chunks + 3) * nn * sizeof(double) + (size_t)n * sizeof(int) + 1024;
-  FFC_CUDA(cudaMallocAsync((void**)&ws, bytes, st));
-  double* Gpart = reinterpret_cast<double*>(ws);
-  double* G = Gpart + chunks * nn;
-  double* V = G + nn;
-  double* W = V + nn;
-  int* perm = reinterpret_cast<int*>(W + nn);
-  int64_t* rank_dev = reinterpret_cast<int64_t*>(((uintptr_t)(perm + n) + 15) & ~(uintptr_t)15);
-  int32_t* sweeps_dev = reinterpret_cast<int32_t*>(rank_dev + 1);
-  ffc_status rc = FFC_OK;
-  gram_kernel<<<dim3(pairs, (unsigned)chunks), 256, 0, st>>>(K, m, n, ldk, chunk_rows, Gpart);
-  gram_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Gpart, (int)chunks, nn, G);
-  jacobi_kernel<<<1, JAC_THREADS, 0, st>>>(G, V, n, sweeps_dev);
-  eig_order_kernel<<<1, 1024, 0, st>>>(G, V, n, eps, r_fixed, sigma, perm, W, rank_dev);
+  FFC_CUDA(cudaMallocAsync((void**)&ws, jobs_off + sizeof(LevJob) * B + (size_t)B * 16, st));
+  double* Gpart = reinterpret_cast<double*>(ws + per);
+  LevJob* d_jobs = reinterpret_cast<LevJob*>(ws + jobs_off);
+  int64_t* ranks = reinterpret_cast<int64_t*>(d_jobs + B);
+  int32_t* sweeps = reinterpret_cast<int32_t*>(ranks + B);
+  std::vector<LevJob> jobs(B);
+  for (int b = 0; b < B; ++b) {
+    const int64_t nn = n[b] * n[b];
+    LevJob& j = jobs[b];
+    j.G = reinterpret_cast<double*>(ws + off[b]);
+    j.V = j.G + nn;
+    j.W = j.V + nn;
+    j.perm = reinterpret_cast<int*>(j.W + nn);
+    j.n = (int)n[b];
+    j.sigma = sigma[b];
+    j.rank = ranks + b;
+    j.sweeps = sweeps + b;
+  }
+  FFC_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(LevJob) * B, cudaMemcpyHostToDevice, st));
+  for (int b = 0; b < B; ++b) {
+    const int nt = (int)((n[b] + GT - 1) / GT);
+    const int pairs = nt * (nt + 1) / 2;
+    const int64_t nn = n[b] * n[b];
+    gram_kernel<<<dim3(pairs, (unsigned)chunks[b]), 256, 0, st>>>(K[b], m[b], (int)n[b], ldk[b], crow[b], Gpart);
+    gram_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Gpart, (int)chunks[b], nn, jobs[b].G);
+  }
+  jacobi_kernel<<<B, JAC_THREADS, 0, st>>>(d_jobs);
+  eig_order_kernel<<<B, 1024, 0, st>>>(d_jobs, eps, r_fixed);
+  for (int b = 0; b < B; ++b)
+    leverage_kernel<<<(unsigned)((m[b] + GT - 1) / GT), 256, 0, st>>>(K[b], m[b], (int)n[b], ldk[b], jobs[b].W,
+                                                                    jobs[b].rank, lev[b]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(e, "leverage kernels"); }
-  int64_t r = 0;
-  int32_t sw = 0;
-  FFC_CUDA(cudaMemcpyAsync(&r, rank_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  FFC_CUDA(cudaMemcpyAsync(&sw, sweeps_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  FFC_CUDA(cudaStreamSynchronize(st));
-  if (r > 0) {
-    leverage_kernel<<<(unsigned)((m + GT - 1) / GT), 256, 0, st>>>(K, m, n, ldk, W, (int)r, lev);
-  } else {
-    FFC_CUDA(cudaMemsetAsync(lev, 0, (size_t)m * sizeof(double), st));
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) { cudaFreeAsync(ws, st); return cuda_fail(e, "leverage_kernel"); }
+  std::vector<int32_t> sw(B);
+  FFC_CUDA(cudaMemcpyAsync(rank_host, ranks, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaMemcpyAsync(sw.data(), sweeps, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   FFC_CUDA(cudaFreeAsync(ws, st));
-  if (rank_host) *rank_host = r;
-  if (sweeps_host) *sweeps_host = sw;
-  if (sw < 0) {
-    set_error("leverage: Jacobi did not converge in %d sweeps", JAC_MAX_SWEEPS);
-    rc = FFC_E_TOL_NOT_REACHED;
+  FFC_CUDA(cudaStreamSynchronize(st));
+  ffc_status rc = FFC_OK;
+  for (int b = 0; b < B; ++b) {
+    if (sweeps_host) sweeps_host[b] = sw[b];
+    if (sw[b] < 0 && rc == FFC_OK) {
+      set_error("leverage: Jacobi did not converge in %d sweeps (block %d)", JAC_MAX_SWEEPS, b);
+      rc = FFC_E_TOL_NOT_REACHED;
+    }
   }
   return rc;
 }

@@ -305,7 +305,8 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     } else {
       rc = launch_sample(X, R->dtype, d, d_smp, g, R->N, P.pool_rows, P.seed, cnt, fc, sst, scratch, st);
     }
-    if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, tot, P.proj_dev, feats, st);
+    const int64_t cap_max = *std::max_element(cap.begin(), cap.end());
+    if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, cap_max, P.proj_dev, feats, st);
     if (rc == FFC_OK) rc = launch_mlp_forward(P.mlp_dev, feats, tot, logits, st);
     if (rc == FFC_OK) rc = launch_select(d_si, g, P.s_max, P.seed, st);
     if (rc != FFC_OK) return rc;

@@ -36,7 +36,7 @@ EXPORTS = (
     "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
     "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
     "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
-    "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage",
+    "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched",
 )
 MLP_PARAMS = 18305
 N_FEATURES = 12
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
     L.ffc_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i32, i64, pdbl, vp, vp]
     L.ffc_adam_step.argtypes = [vp, vp, vp, vp, i64, i64, dbl, dbl, dbl, dbl, vp]
     L.ffc_leverage.argtypes = [vp, i64, i64, i64, dbl, i64, vp, vp, pi64, vp]
+    L.ffc_leverage_batched.argtypes = [i32, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
             getattr(L, name).restype = ctypes.c_int
@@ -459,3 +460,24 @@ def ffc_leverage(Kcm, eps=1e-6, r_fixed=0, stream=None):
     st = _check(lib().ffc_leverage(_ptr(Kcm), m, n, m, float(eps), int(r_fixed), _ptr(lev), _ptr(sig),
                                    ctypes.byref(rank), _stream(stream)))
     return lev[:m], sig[:n], rank.value, st
+
+
+def ffc_leverage_batched(Kcms, eps=1e-6, r_fixed=0, stream=None):
+    """ffc_leverage of several column-major blocks (each given as its (n, m) storage) at once.
+
+    Returns a list of (lev float64[m], sigma float64[n], rank) and the status.
+    """
+    B = len(Kcms)
+    for K in Kcms:
+        _dev(K, "K")
+    P = ctypes.c_void_p * B
+    I = ctypes.c_int64 * B
+    ns = [int(K.shape[0]) for K in Kcms]
+    ms = [int(K.shape[1]) for K in Kcms]
+    levs = [torch.empty(max(m, 1), dtype=torch.float64, device=K.device) for m, K in zip(ms, Kcms)]
+    sigs = [torch.empty(max(n, 1), dtype=torch.float64, device=K.device) for n, K in zip(ns, Kcms)]
+    ranks = I()
+    st = _check(lib().ffc_leverage_batched(B, P(*[K.data_ptr() for K in Kcms]), I(*ms), I(*ns), I(*ms),
+                                           float(eps), int(r_fixed), P(*[t.data_ptr() for t in levs]),
+                                           P(*[t.data_ptr() for t in sigs]), ranks, _stream(stream)))
+    return [(levs[b][:ms[b]], sigs[b][:ns[b]], int(ranks[b])) for b in range(B)], st

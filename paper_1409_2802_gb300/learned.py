@@ -42,8 +42,8 @@ class TrainingSet:
         return len(self.node_rows)
 
 
-def node_training_rows(points_perm, tree: ffc.DeviceTree, node: int, kernel: ffc.Kernel, proj, eps=1e-6, xi=1.0):
-    """(features m x 12, leverage m, rank) of one node's full far field."""
+def node_block(points_perm, tree: ffc.DeviceTree, node: int, kernel: ffc.Kernel, proj, xi=1.0):
+    """(far-field block K as (n, m) storage, features m x 12) of one node, or None."""
     b = int(tree.begin[node].item())
     n = int(tree.count[node].item())
     x_c = tree.centroid[node].contiguous()
@@ -52,27 +52,43 @@ def node_training_rows(points_perm, tree: ffc.DeviceTree, node: int, kernel: ffc
     m = far.numel()
     if m == 0:
         return None
-    X = points_perm[b:b + n]
     K = torch.empty((n, m), dtype=torch.float64, device=points_perm.device)
-    ffc.ffc_eval_block(kernel, points_perm, far, X, precision=ffc.FP64, K=K)
-    lev, _, r, _ = ffc.ffc_leverage(K, eps)
-    del K
+    ffc.ffc_eval_block(kernel, points_perm, far, points_perm[b:b + n], precision=ffc.FP64, K=K)
     F = ffc.ffc_features(kernel, points_perm, far, x_c, rho, proj)
-    return F, lev, r
+    return K, F
 
 
-def build_training_set(sources, eps=1e-6, batch_nodes=8, seed=0, xi=1.0) -> TrainingSet:
+def build_training_set(sources, eps=1e-6, batch_nodes=8, seed=0, xi=1.0, block_bytes=24 << 30) -> TrainingSet:
     """``sources``: iterable of (points_perm, tree, nodes, kernel, proj) tuples.
 
-    Nodes are stored in a seeded random order and grouped into batches of
-    ``batch_nodes`` consecutive nodes.
+    The leverage targets of up to ``block_bytes`` of far-field blocks are
+    computed in one batched call. Nodes are stored in a seeded random order
+    and grouped into training batches of ``batch_nodes`` consecutive nodes.
     """
     parts = []
+    pending, held = [], 0
+
+    def flush():
+        nonlocal pending, held
+        if not pending:
+            return
+        outs, _ = ffc.ffc_leverage_batched([K for K, _ in pending], eps)
+        for (K, F), (lev, _, r) in zip(pending, outs):
+            if r > 0:
+                parts.append((F, lev, r))
+        pending, held = [], 0
+
     for points_perm, tree, nodes, kernel, proj in sources:
         for node in nodes:
-            out = node_training_rows(points_perm, tree, int(node), kernel, proj, eps, xi)
-            if out is not None and out[2] > 0:
-                parts.append(out)
+            out = node_block(points_perm, tree, int(node), kernel, proj, xi)
+            if out is None:
+                continue
+            nbytes = out[0].numel() * 8
+            if pending and held + nbytes > block_bytes:
+                flush()
+            pending.append(out)
+            held += nbytes
+    flush()
     if not parts:
         raise ValueError("no training node has a far field")
     order = np.random.Generator(np.random.PCG64(seed)).permutation(len(parts))
