@@ -133,3 +133,59 @@ def train(ts: TrainingSet, params0, epochs=20, lr=1e-3, seed=0, beta1=0.9, beta2
             ffc.ffc_adam_step(params, grad, m, v, step, lr, beta1, beta2, eps)
             losses.append(loss)
     return params, losses
+
+
+# ---------------------------------------------------------------------------
+# the standard training recipe: leaf nodes of the d = 128 and d = 1000 generators
+
+def recipe_sources(seed: int = 0, nodes_d128: int = 100, nodes_d1000: int = 100, device="cuda"):
+    """(points_perm, tree, nodes, kernel, proj) of the two training generators.
+
+    d = 128: N = 262,144 points of the decaying 16-component mixture, leaf 256,
+    Laplace kernel; d = 1000: N = 100,000 points of intrinsic dimension 10,
+    leaf 512, Gaussian kernel with h = the median pairwise distance. Nodes are
+    a seeded choice among the leaves.
+    """
+    import workloads
+    out = []
+    specs = (
+        (workloads.decaying_mixture(262144, 128, 16, seed=seed), 256, None, nodes_d128),
+        (workloads.low_intrinsic(100000, 10, 1000, seed=seed), 512, "median", nodes_d1000),
+    )
+    for X, leaf, h, count in specs:
+        kernel = (ffc.Kernel(ffc.LAPLACE) if h is None
+                  else ffc.Kernel(ffc.GAUSSIAN, h=workloads.median_pairwise_distance(X)))
+        Xd = torch.as_tensor(X).to(device)
+        tree = ffc.ffc_build_tree(Xd, leaf)
+        Xp = Xd[tree.perm].contiguous()
+        first = (1 << tree.depth) - 1
+        leaves = np.arange(first, tree.n_nodes)
+        pick = np.random.Generator(np.random.PCG64(seed + leaf)).choice(leaves, size=min(count, leaves.size),
+                                                                        replace=False)
+        proj = torch.as_tensor(workloads.projections(X.shape[1], seed=seed + 7)).to(device)
+        out.append((Xp, tree, sorted(int(i) for i in pick), kernel, proj))
+    return out
+
+
+def train_standard(seed: int = 0, epochs: int = 30, lr: float = 2e-3, nodes_per_generator: int = 100,
+                   device="cuda"):
+    """Train the proposal with the standard recipe; returns (params, info dict)."""
+    import time
+
+    import workloads
+    t0 = time.perf_counter()
+    ts = build_training_set(recipe_sources(seed, nodes_per_generator, nodes_per_generator, device), eps=1e-6,
+                            batch_nodes=8, seed=seed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    theta0 = workloads.mlp_init(seed + 1)
+    loss0 = mean_loss(ts, torch.as_tensor(theta0).to(device))
+    params, losses = train(ts, theta0, epochs=epochs, lr=lr, seed=seed)
+    loss1 = mean_loss(ts, params)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"nodes": ts.n_nodes, "rows": int(ts.feats.shape[0]), "targets_s": round(t1 - t0, 1),
+            "train_s": round(t2 - t1, 1), "adam_steps": len(losses), "loss_start": round(loss0, 4),
+            "loss_end": round(loss1, 4), "epochs": epochs, "lr": lr}
+    del ts
+    return params, info

@@ -21,6 +21,10 @@ Workloads (sizes of the paper's experiments, §4.1, and of the benchmark suite):
                         Gaussian noise (§4.1.1 "Low intrinsic dimension").
 * ``standard_normal``   the §4.1.1 "Normal" data set.
 
+Workload parameter: ``median_pairwise_distance`` gives the Gaussian bandwidth
+of the d = 1000 workload (the exact median over all pairs of the first 4,096
+points).
+
 Random inputs of the learned proposal (drawn here so both sides share them):
 
 * ``mlp_init``          initial FP32 parameters of the 12-128-128-1 network
@@ -41,6 +45,7 @@ __all__ = [
     "random_matrix",
     "mlp_init",
     "projections",
+    "median_pairwise_distance",
     "MLP_LAYOUT",
     "MLP_N_PARAMS",
 ]
@@ -152,3 +157,12 @@ def mlp_init(seed: int = 0) -> np.ndarray:
 def projections(d: int, seed: int = 0, k: int = 8) -> np.ndarray:
     """k x d matrix of independent N(0, 1/d) entries (float64)."""
     return np.ascontiguousarray(_rng(seed).standard_normal((k, d)) / np.sqrt(d))
+
+
+def median_pairwise_distance(points: np.ndarray, k: int = 4096) -> float:
+    """Exact median of ||x_i - x_j|| over all pairs i < j of the first k points."""
+    S = np.asarray(points[:k], dtype=np.float64)
+    sq = np.sum(S * S, axis=1)
+    D2 = np.maximum(sq[:, None] + sq[None, :] - 2.0 * (S @ S.T), 0.0)
+    iu = np.triu_indices(S.shape[0], 1)
+    return float(np.median(np.sqrt(D2[iu])))
