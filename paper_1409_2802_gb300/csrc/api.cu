@@ -225,7 +225,8 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   size_t bytes = 16 * 256 + round_up(sizeof(CpqrItem)) + round_up(sizeof(TrsmItem)) +
                  round_up(sizeof(CtaAssign) * g) + round_up(sizeof(int32_t) * rc_cap) +
                  round_up(sizeof(double) * rc_cap) + 2 * round_up(sizeof(double) * n) + round_up((size_t)n) +
-                 round_up(sizeof(Slot) * 2 * g) + round_up((size_t)rc_cap * rc_cap * sizeof(double));
+                 round_up(sizeof(Slot) * 2 * g) + round_up((size_t)rc_cap * rc_cap * sizeof(double)) +
+                 round_up(12 * sizeof(unsigned long long));
   FFC_CUDA(cudaMallocAsync((void**)&ar.base, bytes, st));
   CpqrItem* d_item = ar.take<CpqrItem>(1);
   TrsmItem* d_titem = ar.take<TrsmItem>(1);
@@ -238,13 +239,14 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   Slot* slots = ar.take<Slot>(2 * g);
   double* R11 = ar.take<double>((size_t)rc_cap * rc_cap);
   unsigned* barrier = ar.take<unsigned>(1);
+  unsigned long long* red = ar.take<unsigned long long>(12);
   int32_t* rank = ar.take<int32_t>(1);
   double* r22 = ar.take<double>(1);
   int32_t* status = ar.take<int32_t>(1);
   CpqrItem hi = {};
   hi.A = K_dev; hi.lda = ldk; hi.s = (int32_t)s; hi.n = (int32_t)n; hi.r_max = kcap; hi.tol = tol;
   hi.piv = piv; hi.beta = beta; hi.vn1 = vn1; hi.vn2 = vn2; hi.selected = sel; hi.slots = slots;
-  hi.barrier = barrier; hi.rank_out = rank; hi.r22_out = r22; hi.status_out = status;
+  hi.barrier = barrier; hi.red = red; hi.rank_out = rank; hi.r22_out = r22; hi.status_out = status;
   std::vector<CtaAssign> asg(g);
   for (int c = 0; c < g; ++c) asg[c] = CtaAssign{0, c, g, 0};
   TrsmItem ti = {};
@@ -256,6 +258,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   FFC_CUDA(cudaMemcpyAsync(d_assign, asg.data(), sizeof(CtaAssign) * g, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(barrier, 0, sizeof(unsigned), st));
   FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * g, st));   // the QR's group accumulators start at zero
+  FFC_CUDA(cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 12, st));
   FFC_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   FFC_CUDA(cudaMemsetAsync(rank, 0, sizeof(int32_t), st));
   ffc_status rc = launch_cpqr(precision, d_item, d_assign, g, (int)std::max<int64_t>(s, 1), st);

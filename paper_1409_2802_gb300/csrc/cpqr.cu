@@ -11,9 +11,11 @@
 // move: a pivot is marked selected and its rows >= k are never read again,
 // so R is formed in place in the original column positions. One step k:
 //   1. every CTA folds its best (squared norm, column) key into the group's
-//      step accumulator with a 64-bit atomicMax and its sum of squared norms
-//      with an FP64 atomicAdd (both at L2), then joins the group barrier and
-//      reads back the winner and ||R22||^2;
+//      step accumulator with a 64-bit atomicMax and its sum of squared norms,
+//      as a 128-bit fixed-point number in three 40-bit limbs, with 64-bit
+//      atomicAdds (all at L2; integer sums do not depend on the order), joins
+//      the group barrier and reads back the winner and ||R22||^2 (step 0,
+//      which fixes the fixed-point exponent, goes through per-CTA slots);
 //   2. every CTA loads the pivot column (rows k..s-1) from L2 and forms the
 //      LAPACK dlarfg reflector redundantly in shared memory;
 //   3. each warp applies the reflector to its owned columns, two at a time:
@@ -42,6 +44,10 @@ namespace ffc {
 
 namespace {
 
+// CTAs per SM the QR kernel is compiled for (register budget 65536 / (256 x this))
+#ifndef FFC_QR_MIN_BLOCKS
+#define FFC_QR_MIN_BLOCKS 3
+#endif
 constexpr int QR_THREADS = 256;
 constexpr int QR_WARPS = QR_THREADS / 32;
 // Columns one CTA may own: their norms and flags live in shared memory.
@@ -142,6 +148,30 @@ __device__ __forceinline__ void fix_add(Fix128& a, const Fix128& b) {
 // value of a Fix128 aligned to emax (one thread; FP64 arithmetic)
 __device__ __forceinline__ double fix_value(const Fix128& a, int emax) {
   return scalbn((double)a.hi, emax - 1075) + scalbn((double)a.lo, emax - 1075 - 64);
+}
+
+// Group reduction of steps k >= 1 through 64-bit atomics at L2: red[4 (k % 3)]
+// holds the step's max pivot key and the 128-bit fixed-point sum as three
+// 40-bit limbs, each summed in its own 64-bit word (integer adds commute, so
+// the result does not depend on the arrival order, and up to 2^24 CTAs add
+// without a limb overflowing). Rank 0 zeroes the buffer of step k + 2 after
+// the barrier of step k, when every CTA has read step k - 1's buffer.
+constexpr unsigned long long LIMB40 = (1ull << 40) - 1ull;
+
+__device__ __forceinline__ void red_publish(unsigned long long* rb, unsigned long long key, const Fix128& f) {
+  const unsigned __int128 F = ((unsigned __int128)f.hi << 64) | f.lo;
+  atomicMax(rb, key);
+  atomicAdd(rb + 1, (unsigned long long)(F & LIMB40));
+  atomicAdd(rb + 2, (unsigned long long)((F >> 40) & LIMB40));
+  atomicAdd(rb + 3, (unsigned long long)(F >> 80));
+}
+
+__device__ __forceinline__ void red_read(const unsigned long long* rb, unsigned long long& key, Fix128& f) {
+  key = __ldcg(rb);
+  const unsigned __int128 F = (unsigned __int128)__ldcg(rb + 1) + ((unsigned __int128)__ldcg(rb + 2) << 40) +
+                              ((unsigned __int128)__ldcg(rb + 3) << 80);
+  f.hi = (unsigned long long)(F >> 64);
+  f.lo = (unsigned long long)F;
 }
 
 struct QrShared {
@@ -312,6 +342,37 @@ __device__ void cta_reduce(unsigned long long key, double part, QrShared& sh) {
   __syncthreads();
 }
 
+// FP64 norm downdate of the columns held by the lanes with `mine` set (lane
+// c: column j, row-k entry akj), LAPACK xLAQP2 style; a column whose downdate
+// is unsafe is recomputed by the whole warp (rare); then each lane folds its
+// column into its pivot key and norm sum. Column j's data: base + (j - jb) lda.
+template <typename T>
+__device__ __forceinline__ void downdate_lane(bool mine, int j, double akj, const T* __restrict__ base, int64_t lda,
+                                              int k, int s, int lane, double tol3z, double* __restrict__ vn1s,
+                                              double* __restrict__ vn2s, int c0, unsigned long long& key,
+                                              double& psum, int jb) {
+  int unsafe = 0;
+  if (mine) {
+    const double rest = fma(-akj, akj, vn1s[j]);
+    if (rest <= tol3z * vn2s[j]) unsafe = 1;
+    else vn1s[j] = rest;
+  }
+  unsigned um = __ballot_sync(0xffffffffu, unsafe);
+  while (um) {
+    const int src = __ffs(um) - 1;
+    um &= um - 1u;
+    const int jj = __shfl_sync(0xffffffffu, j, src);
+    const double nr = column_norm2<T>(base + (int64_t)(jj - jb) * lda, k + 1, s, lane);
+    if (lane == 0) { vn1s[jj] = nr; vn2s[jj] = nr; }
+  }
+  __syncwarp();
+  if (mine) {
+    const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+    key = kj > key ? kj : key;
+    psum += vn1s[j];
+  }
+}
+
 // One warp updates NC adjacent owned columns per pass (those not selected):
 // v^T a for all of them, then a -= tau (v^T a) v, with NC loads per lane per
 // row chunk in flight; lane 0 then downdates each column's squared norm in
@@ -363,28 +424,14 @@ __device__ __forceinline__ void update_columns(T* __restrict__ A, int64_t lda, i
 #pragma unroll
       for (int c = 0; c < NC; ++c) ak[c] = va[c] ? base[(int64_t)c * lda + k] : (T)0;
     }
+    // lane c downdates column j0 + c: one FP64 instruction stream for all NC
+    // columns (a warp-wide FP64 instruction costs the same for 1 or NC lanes)
+    T my_ak = ak[0];
+    bool mine = va[0] && lane == 0;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (!va[c]) continue;
-      const int j = j0 + c;
-      int unsafe = 0;
-      if (lane == 0) {
-        const double akj = (double)ak[c];
-        const double rest = fma(-akj, akj, vn1s[j]);
-        if (rest <= tol3z * vn2s[j]) unsafe = 1;
-        else vn1s[j] = rest;
-      }
-      unsafe = __shfl_sync(0xffffffffu, unsafe, 0);
-      if (unsafe) {
-        const double nr = column_norm2<T>(base + (int64_t)c * lda, k + 1, s, lane);
-        if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
-      }
-      if (lane == 0) {
-        const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
-        key = kj > key ? kj : key;
-        psum += vn1s[j];
-      }
-    }
+    for (int c = 1; c < NC; ++c)
+      if (lane == c) { my_ak = ak[c]; mine = va[c]; }
+    downdate_lane(mine, j0 + lane, (double)my_ak, base, lda, k, s, lane, tol3z, vn1s, vn2s, c0, key, psum, j0);
   }
 }
 
@@ -429,30 +476,43 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (tid == 0) {
       sh.stop = 0;
       if (a.g > 1) {
-        StepSlot* sl = slots + (k & 1) * a.g + a.rank;
-        sl->key = sh.key;
-        sl->sum = sh.sum;
+        if (k == 0) {   // step 0 fixes the fixed-point exponent: slots, read by warp 0 below
+          StepSlot* sl = slots + a.rank;
+          sl->key = sh.key;
+          sl->sum = sh.sum;
+        } else {
+          Fix128 f = {0ull, 0ull};
+          fix_add(f, sh.sum, sh.emax);
+          red_publish(it.red + 4 * (k % 3), sh.key, f);
+        }
         if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1))) {
           sh.stop = 1;
           sh.status = FFC_E_TIMEOUT;
+        } else if (k > 0) {
+          unsigned long long kk;
+          Fix128 f;
+          red_read(it.red + 4 * (k % 3), kk, f);
+          sh.key = kk;
+          sh.sum = fix_value(f, sh.emax);
+          if (a.rank == 0) {
+            unsigned long long* z = it.red + 4 * ((k + 2) % 3);
+            z[0] = 0ull; z[1] = 0ull; z[2] = 0ull; z[3] = 0ull;
+          }
         }
       }
     }
     __syncthreads();
-    if (a.g > 1 && !sh.stop && warp == 0) {
-      const StepSlot* base = slots + (k & 1) * a.g;
+    if (a.g > 1 && !sh.stop && k == 0 && warp == 0) {
+      const StepSlot* base = slots;
       unsigned long long kk = 0ull;
       // every later step's sums are below step 0's total, so its exponent
       // (plus one) bounds them; 128-bit fixed point keeps ~2^-116 of it
-      int emax = sh.emax;
-      if (k == 0) {
-        emax = 1;
-        for (int t = lane; t < a.g; t += 32) emax = max(emax, dbl_exponent(__ldcg(&base[t].sum)));
+      int emax = 1;
+      for (int t = lane; t < a.g; t += 32) emax = max(emax, dbl_exponent(__ldcg(&base[t].sum)));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        emax = min(emax + 11, 2046);   // room for the sum of up to 2^11 slots
-        if (lane == 0) sh.emax = emax;
-      }
+      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      emax = min(emax + 11, 2046);   // room for the sum of up to 2^11 slots
+      if (lane == 0) sh.emax = emax;
       Fix128 f = {0ull, 0ull};
       for (int t = lane; t < a.g; t += 32) {
         const unsigned long long kt = __ldcg(&base[t].key);
@@ -555,32 +615,11 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
         if (va) ka = A[(int64_t)(c0 + j0) * lda + k];
         if (vb) kb = A[(int64_t)(c0 + jb) * lda + k];
       }
-      // FP64 norm downdate of the two columns by lane 0, right behind their
-      // update (its latency hides behind the other warps' column passes); the
-      // whole warp recomputes a norm when the downdate is unsafe
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const bool valid = h == 0 ? va : vb;
-        if (!valid) continue;
-        const int j = h == 0 ? j0 : jb;
-        int unsafe = 0;
-        if (lane == 0) {
-          const double akj = (double)(h == 0 ? ka : kb);
-          const double rest = fma(-akj, akj, vn1s[j]);
-          if (rest <= TOL3Z * vn2s[j]) unsafe = 1;
-          else vn1s[j] = rest;
-        }
-        unsafe = __shfl_sync(0xffffffffu, unsafe, 0);
-        if (unsafe) {
-          const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, k + 1, s, lane);
-          if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; }
-        }
-        if (lane == 0) {
-          const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
-          key = kj > key ? kj : key;
-          psum += vn1s[j];
-        }
-      }
+      // FP64 norm downdate of the two columns by lanes 0 and 1, right behind
+      // their update (its latency hides behind the other warps' passes)
+      const bool mine = (lane == 0 && va) || (lane == 1 && vb);
+      downdate_lane(mine, lane == 0 ? j0 : jb, (double)(lane == 0 ? ka : kb), A + (int64_t)c0 * lda, lda, k, s,
+                    lane, TOL3Z, vn1s, vn2s, c0, key, psum, 0);
     }
     }
     cta_reduce(key, psum, sh);
@@ -600,7 +639,7 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(QR_THREADS)
+__global__ void __launch_bounds__(QR_THREADS, FFC_QR_MIN_BLOCKS)
 cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
             const int32_t* __restrict__ cta_off) {
   // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries

@@ -110,7 +110,8 @@ struct CpqrItem {
   double* vn1;          // n  current residual norms
   double* vn2;          // n  reference norms (downdating safeguard)
   uint8_t* selected;    // n
-  void* slots;          // 2 x g Slot
+  void* slots;          // g step-0 slots (16 B each)
+  unsigned long long* red;  // 12 words: the group reduction of steps >= 1, zeroed before the launch
   unsigned int* barrier;
   int32_t* rank_out;
   double* r22_out;      // ||R22||_F / ||K'||_F

@@ -48,7 +48,9 @@ struct Scalars {
   int32_t status;
   int32_t pad;
   double r22;
+  unsigned long long red[12];   // the QR's group reduction words (steps >= 1)
 };
+static_assert(sizeof(Scalars) <= 256, "scalars fit their scratch slot");
 
 // Writes the work tables into the scratch array and clears what must start
 // at zero (the array keeps the previous call's contents).
@@ -65,6 +67,7 @@ __global__ void noalloc_setup_kernel(CpqrItem item, TrsmItem titem, int g, Scala
     sc->status = FFC_OK;
     sc->r22 = 0.0;
   }
+  if (t < 12) sc->red[t] = 0ull;
   for (int c = t; c < g; c += gridDim.x * blockDim.x) d_assign[c] = CtaAssign{0, c, g, 0};
 }
 
@@ -131,7 +134,8 @@ extern "C" ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t 
   hi.vn2 = reinterpret_cast<double*>(base + OFF_VN2);
   hi.selected = reinterpret_cast<uint8_t*>(base + OFF_SEL);
   hi.slots = base + OFF_SLOTS;
-  hi.barrier = &sc->barrier; hi.rank_out = &sc->rank; hi.r22_out = &sc->r22; hi.status_out = &sc->status;
+  hi.barrier = &sc->barrier; hi.red = sc->red; hi.rank_out = &sc->rank; hi.r22_out = &sc->r22;
+  hi.status_out = &sc->status;
   TrsmItem ti = {};
   ti.A = K_dev; ti.lda = ldk; ti.n = (int32_t)n; ti.rank = &sc->rank; ti.piv = hi.piv; ti.beta = hi.beta;
   ti.selected = hi.selected; ti.skel_perm = skel_perm_dev; ti.R11 = reinterpret_cast<double*>(base + OFF_R11);

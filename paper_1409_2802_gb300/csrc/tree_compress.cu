@@ -212,6 +212,9 @@ ffc_status grow(char** buf, size_t* have, size_t want, cudaStream_t st) {
   return FFC_OK;
 }
 
+// Bytes of sampled blocks one QR launch may hold: below the 129 MB L2.
+constexpr size_t QR_L2_BUDGET = 96ull << 20;
+
 // Learned sampler: for every output node, the candidate pool (whole far field
 // or a uniform pool), features, network logits and the weighted draw of its
 // min(s_max, P) best rows, in key order. The keys do not depend on s, so
@@ -352,43 +355,70 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   }
   const int cap = cpqr_max_ctas(P.precision, (int)s_nom);
   if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
-  // Group sizes: about 16K elements per CTA when everything fits in one
-  // co-resident launch; otherwise shrink the groups in proportion so the
-  // whole round is still one launch, with CTAs shared round-robin between
-  // items (each CTA walks its items in increasing order).
-  int64_t G = 0;
-  for (int q = 0; q < W; ++q)
-    G += std::max<int64_t>(cpqr_min_group(R->count_h[items[q]]), group_size_tree(s_nom, R->count_h[items[q]], 4096));
-  const bool shared_ctas = G > cap;
-  const int64_t per_cta = shared_ctas ? std::max<int64_t>(1, elems / cap) : 16384;
-  G = 0;
-  for (int q = 0; q < W; ++q) {
-    const int64_t n = R->count_h[items[q]];
-    int64_t gq = shared_ctas ? (s_nom * n) / per_cta : group_size_tree(s_nom, n, 4096);
-    gq = std::max<int64_t>(1, std::min<int64_t>({gq, (int64_t)cap, std::max<int64_t>(1, n / 4)}));
-    gq = std::max<int64_t>(gq, cpqr_min_group(n));   // per-CTA column cap (<= cap for N <= 1.5M)
-    g[q] = (int)gq;
-    goff[q] = G;
-    G += g[q];
-  }
-  const int grid = shared_ctas ? cap : (int)G;
-  // per-CTA entry lists, items in increasing order within each list
-  std::vector<std::vector<CtaAssign>> lists(grid);
+  // The round's QR runs as one cooperative launch per sub-batch of
+  // consecutive items whose blocks together fit in QR_L2_BUDGET bytes: the
+  // unblocked QR streams each block once per step, so a sub-batch that stays
+  // L2-resident runs its steps from L2 instead of HBM.
+  // Group sizes within a sub-batch: about 16K elements per CTA when it fits
+  // in one co-resident launch; otherwise the groups shrink in proportion and
+  // CTAs are shared round-robin between items (each CTA walks its items in
+  // increasing order).
+  std::vector<int> sb;   // sub-batch starts, then W
   {
-    int64_t ptr = 0;
+    size_t acc = 0;
     for (int q = 0; q < W; ++q) {
+      const size_t bq = esz * (size_t)s_nom * (size_t)R->count_h[items[q]];
+      if (q == 0 || acc + bq > QR_L2_BUDGET) {
+        sb.push_back(q);
+        acc = 0;
+      }
+      acc += bq;
+    }
+    sb.push_back(W);
+  }
+  const int n_sb = (int)sb.size() - 1;
+  std::vector<int> sb_grid(n_sb), sb_as(n_sb), sb_coff(n_sb);
+  std::vector<int32_t> hoff;
+  std::vector<CtaAssign> ha;
+  int64_t G = 0;
+  for (int b = 0; b < n_sb; ++b) {
+    const int q0 = sb[b], q1 = sb[b + 1];
+    int64_t Gb = 0, elems_b = 0;
+    for (int q = q0; q < q1; ++q) {
+      const int64_t n = R->count_h[items[q]];
+      Gb += std::max<int64_t>(cpqr_min_group(n), group_size_tree(s_nom, n, 4096));
+      elems_b += s_nom * n;
+    }
+    const bool shared_ctas = Gb > cap;
+    const int64_t per_cta = shared_ctas ? std::max<int64_t>(1, elems_b / cap) : 16384;
+    int64_t Gsum = 0;
+    for (int q = q0; q < q1; ++q) {
+      const int64_t n = R->count_h[items[q]];
+      int64_t gq = shared_ctas ? (s_nom * n) / per_cta : group_size_tree(s_nom, n, 4096);
+      gq = std::max<int64_t>(1, std::min<int64_t>({gq, (int64_t)cap, std::max<int64_t>(1, n / 4)}));
+      gq = std::max<int64_t>(gq, cpqr_min_group(n));   // per-CTA column cap (<= cap for N <= 1.5M)
+      g[q] = (int)gq;
+      goff[q] = G;
+      G += g[q];
+      Gsum += g[q];
+    }
+    const int grid = shared_ctas ? cap : (int)Gsum;
+    std::vector<std::vector<CtaAssign>> lists(grid);
+    int64_t ptr = 0;
+    for (int q = q0; q < q1; ++q) {
       for (int c = 0; c < g[q]; ++c) lists[(ptr + c) % grid].push_back(CtaAssign{q, c, g[q], 0});
       ptr = (ptr + g[q]) % grid;
     }
+    sb_grid[b] = grid;
+    sb_as[b] = (int)ha.size();
+    sb_coff[b] = (int)hoff.size();
+    const int32_t base = (int32_t)ha.size();
+    for (int c = 0; c < grid; ++c) {
+      hoff.push_back((int32_t)ha.size() - base);
+      ha.insert(ha.end(), lists[c].begin(), lists[c].end());
+    }
+    hoff.push_back((int32_t)ha.size() - base);
   }
-  std::vector<int32_t> hoff(grid + 1, 0);
-  std::vector<CtaAssign> ha;
-  ha.reserve(G);
-  for (int b = 0; b < grid; ++b) {
-    hoff[b] = (int32_t)ha.size();
-    ha.insert(ha.end(), lists[b].begin(), lists[b].end());
-  }
-  hoff[grid] = (int32_t)ha.size();
   // triangular-solve tiles
   std::vector<int64_t> ttiles(W);
   int64_t ttot = 0;
@@ -398,13 +428,14 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   const bool learned = P.sampler == FFC_SAMPLE_LEARNED;
   Layout L;
   const size_t o_si = L.add<SampleItem>(W), o_ei = L.add<EvalItem>(W), o_qi = L.add<CpqrItem>(W),
-               o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(G), o_coff = L.add<int32_t>(grid + 1),
+               o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(ha.size()), o_coff = L.add<int32_t>(hoff.size()),
                o_sout = L.add<int64_t>(W),
                o_fc = L.add<int64_t>(W), o_sst = L.add<int32_t>(W), o_md = L.add<double>(W), o_ls = L.add<double>(W),
                o_est = L.add<int32_t>(W), o_K = L.add<double>((size_t)s_nom * SN),
                o_piv = L.add<int32_t>((size_t)W * rcap_round), o_beta = L.add<double>((size_t)W * rcap_round),
                o_vn1 = L.add<double>(SN), o_vn2 = L.add<double>(SN), o_sel = L.add<uint8_t>(SN),
-               o_slots = L.add<Slot>(2 * G), o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
+               o_slots = L.add<Slot>(2 * G), o_red = L.add<unsigned long long>(12 * (size_t)W),
+               o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
                o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
                o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W);
@@ -438,6 +469,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   double* vn2 = (double*)(b + o_vn2);
   uint8_t* sel = (uint8_t*)(b + o_sel);
   Slot* slots = (Slot*)(b + o_slots);
+  unsigned long long* red = (unsigned long long*)(b + o_red);
   unsigned* bar = (unsigned*)(b + o_bar);
   int32_t* qrank = (int32_t*)(b + o_rank);
   double* qr22 = (double*)(b + o_r22);
@@ -470,7 +502,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     qi.A = (void*)((char*)K + esz * koff[q]); qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;
     qi.piv = piv + (size_t)q * rcap_round; qi.beta = beta + (size_t)q * rcap_round;
     qi.vn1 = vn1 + noff[q]; qi.vn2 = vn2 + noff[q]; qi.selected = sel + noff[q];
-    qi.slots = slots + 2 * goff[q]; qi.barrier = bar + q; qi.rank_out = qrank + q; qi.r22_out = qr22 + q;
+    qi.slots = slots + 2 * goff[q]; qi.red = red + 12 * (size_t)q; qi.barrier = bar + q; qi.rank_out = qrank + q;
+    qi.r22_out = qr22 + q;
     qi.status_out = qst + q;
     TrsmItem& ti = ht[q];
     ti = TrsmItem{};
@@ -483,12 +516,13 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   FFC_CUDA(cudaMemcpyAsync(d_ei, he.data(), sizeof(EvalItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_qi, hq.data(), sizeof(CpqrItem) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_ti, ht.data(), sizeof(TrsmItem) * W, cudaMemcpyHostToDevice, st));
-  FFC_CUDA(cudaMemcpyAsync(d_as, ha.data(), sizeof(CtaAssign) * G, cudaMemcpyHostToDevice, st));
-  FFC_CUDA(cudaMemcpyAsync(d_coff, hoff.data(), sizeof(int32_t) * (grid + 1), cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_as, ha.data(), sizeof(CtaAssign) * ha.size(), cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(d_coff, hoff.data(), sizeof(int32_t) * hoff.size(), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(oidx, ho.data(), sizeof(int32_t) * W, cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(est, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * W, st));
   FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * G, st));   // the QR's group accumulators start at zero
+  FFC_CUDA(cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 12 * (size_t)W, st));
   FFC_CUDA(cudaMemsetAsync(qst, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, st));
   FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, st));
@@ -508,10 +542,12 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
   if (rc != FFC_OK) return rc;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
-  // one cooperative QR launch for the whole round
-  rc = launch_cpqr(P.precision, d_qi, d_as, grid, (int)s_nom, st, d_coff);
-  if (rc != FFC_OK) return rc;
-  const int qr_launches = 1;
+  // one cooperative QR launch per L2-sized sub-batch of the round
+  for (int bb = 0; bb < n_sb; ++bb) {
+    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb]);
+    if (rc != FFC_OK) return rc;
+  }
+  const int qr_launches = n_sb;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[3], st));
   gate_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_nom, P.s_max, s_out, qst, qrank, trank);
   rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
