@@ -361,7 +361,9 @@ ffc_status ffc_features(ffc_kernel k, const void* Y_dev, int32_t dtype, int64_t 
                         const double* proj_dev, float* feats_dev, void* stream);
 
 /* ffc_mlp_forward - logits_dev[i] (R floats) of the feature rows feats_dev
- * (R x 12 FP32). Asynchronous. */
+ * (R x 12 FP32): the proposal's inference pass, whose 128 x 128 product takes
+ * FP16 operands (first-layer activations rounded to FP16) and accumulates in
+ * FP32 on the tensor cores. Asynchronous. */
 ffc_status ffc_mlp_forward(const float* params_dev, const float* feats_dev, int64_t R, float* logits_dev,
                            void* stream);
 

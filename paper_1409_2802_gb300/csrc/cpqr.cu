@@ -176,12 +176,15 @@ __device__ __forceinline__ void red_read(const unsigned long long* rb, unsigned 
 
 struct QrShared {
   unsigned long long kw[QR_WARPS];
+  unsigned long long fh[QR_WARPS], fl[QR_WARPS];
   double psum[QR_THREADS];
   float fw[QR_WARPS];
   double dw[QR_WARPS];
   unsigned long long key;
+  Fix128 fsum, thr;       // ||R22||^2 of the step and tol^2 ||K'||^2, fixed point at emax
   double sum, fro2, tau, beta;
-  int stop, status, n_rc, emax;
+  float tauf;
+  int stop, status, n_rc, emax, apply;
 };
 
 // Exact square x*x = p + e (FMA), accumulated with a compensated sum (FP32 only).
@@ -350,7 +353,7 @@ template <typename T>
 __device__ __forceinline__ void downdate_lane(bool mine, int j, double akj, const T* __restrict__ base, int64_t lda,
                                               int k, int s, int lane, double tol3z, double* __restrict__ vn1s,
                                               double* __restrict__ vn2s, int c0, unsigned long long& key,
-                                              double& psum, int jb) {
+                                              Fix128& psum, int emax, int jb) {
   int unsafe = 0;
   if (mine) {
     const double rest = fma(-akj, akj, vn1s[j]);
@@ -367,10 +370,45 @@ __device__ __forceinline__ void downdate_lane(bool mine, int j, double akj, cons
   }
   __syncwarp();
   if (mine) {
-    const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+    const double v = vn1s[j];
+    const unsigned long long kj = pivot_key(v, c0 + j);
     key = kj > key ? kj : key;
-    psum += vn1s[j];
+    fix_add(psum, v, emax);
   }
+}
+
+// CTA-wide: max key and the exact fixed-point sum of per-thread partials into sh.key, sh.fsum
+// (integer operations only).
+__device__ void cta_reduce_fix(unsigned long long key, Fix128 part, QrShared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  key = warp_max_u64(key);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Fix128 g2;
+    g2.hi = __shfl_xor_sync(0xffffffffu, part.hi, o);
+    g2.lo = __shfl_xor_sync(0xffffffffu, part.lo, o);
+    fix_add(part, g2);
+  }
+  if (lane == 0) { sh.kw[warp] = key; sh.fh[warp] = part.hi; sh.fl[warp] = part.lo; }
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long kk = lane < QR_WARPS ? sh.kw[lane] : 0ull;
+    Fix128 f = {lane < QR_WARPS ? sh.fh[lane] : 0ull, lane < QR_WARPS ? sh.fl[lane] : 0ull};
+    kk = warp_max_u64(kk);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      Fix128 g2;
+      g2.hi = __shfl_xor_sync(0xffffffffu, f.hi, o);
+      g2.lo = __shfl_xor_sync(0xffffffffu, f.lo, o);
+      fix_add(f, g2);
+    }
+    if (lane == 0) { sh.key = kk; sh.fsum = f; }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool fix_le(const Fix128& a, const Fix128& b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
 }
 
 // One warp updates NC adjacent owned columns per pass (those not selected):
@@ -383,7 +421,7 @@ __device__ __forceinline__ void update_columns(T* __restrict__ A, int64_t lda, i
                                                const uint8_t* __restrict__ sels, const T* __restrict__ vsh, T ttau,
                                                bool apply, int k, int s, int warp, int lane, double tol3z,
                                                double* __restrict__ vn1s, double* __restrict__ vn2s,
-                                               unsigned long long& key, double& psum) {
+                                               unsigned long long& key, Fix128& psum, int emax) {
   for (int j0 = warp * NC; j0 < ncols; j0 += QR_WARPS * NC) {
     bool va[NC];
     T* base = A + (int64_t)(c0 + j0) * lda;
@@ -431,7 +469,8 @@ __device__ __forceinline__ void update_columns(T* __restrict__ A, int64_t lda, i
 #pragma unroll
     for (int c = 1; c < NC; ++c)
       if (lane == c) { my_ak = ak[c]; mine = va[c]; }
-    downdate_lane(mine, j0 + lane, (double)my_ak, base, lda, k, s, lane, tol3z, vn1s, vn2s, c0, key, psum, j0);
+    downdate_lane(mine, j0 + lane, (double)my_ak, base, lda, k, s, lane, tol3z, vn1s, vn2s, c0, key, psum, emax,
+                  j0);
   }
 }
 
@@ -481,9 +520,7 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
           sl->key = sh.key;
           sl->sum = sh.sum;
         } else {
-          Fix128 f = {0ull, 0ull};
-          fix_add(f, sh.sum, sh.emax);
-          red_publish(it.red + 4 * (k % 3), sh.key, f);
+          red_publish(it.red + 4 * (k % 3), sh.key, sh.fsum);
         }
         if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1))) {
           sh.stop = 1;
@@ -493,12 +530,14 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
           Fix128 f;
           red_read(it.red + 4 * (k % 3), kk, f);
           sh.key = kk;
-          sh.sum = fix_value(f, sh.emax);
+          sh.fsum = f;
           if (a.rank == 0) {
             unsigned long long* z = it.red + 4 * ((k + 2) % 3);
             z[0] = 0ull; z[1] = 0ull; z[2] = 0ull; z[3] = 0ull;
           }
         }
+      } else if (k == 0) {   // one CTA: its own total fixes the exponent
+        sh.emax = min(dbl_exponent(sh.sum) + 11, 2046);
       }
     }
     __syncthreads();
@@ -532,8 +571,19 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     __syncthreads();
     if (tid == 0) {
       if (!sh.stop) {
-        if (k == 0) sh.fro2 = sh.sum;
-        if (it.tol > 0.0 && sqrt(sh.sum) <= it.tol * sqrt(sh.fro2)) {
+        // ||R22||_F <= tol ||K'||_F compared as squares; from step 1 on in the
+        // exact fixed-point domain (no FP64 instruction per step)
+        bool reached;
+        if (k == 0) {
+          sh.fro2 = sh.sum;
+          Fix128 t = {0ull, 0ull};
+          if (it.tol > 0.0) fix_add(t, it.tol * it.tol * sh.fro2, sh.emax);
+          sh.thr = t;
+          reached = it.tol > 0.0 && sh.sum <= it.tol * it.tol * sh.fro2;
+        } else {
+          reached = it.tol > 0.0 && fix_le(sh.fsum, sh.thr);
+        }
+        if (reached) {
           sh.stop = 1;
           sh.status = FFC_OK;
         } else if (k >= kmax || (sh.key >> 20) == 0ull) {
@@ -565,12 +615,17 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
       const T alpha = vsh[k];
       if (xn2 == (T)0) {
         sh.tau = 0.0;
+        sh.tauf = 0.0f;
+        sh.apply = 0;
         sh.beta = (double)alpha;
       } else {
         const T nrm = sqrt(fma(alpha, alpha, xn2));
         const T beta = alpha >= (T)0 ? -nrm : nrm;
         const T scale = (T)1 / (alpha - beta);
-        sh.tau = (double)((beta - alpha) / beta);
+        const T tt = (beta - alpha) / beta;
+        sh.tau = (double)tt;
+        sh.tauf = (float)tt;
+        sh.apply = 1;
         sh.beta = (double)beta;
         vsh[k] = scale;   // read below, then replaced by 1
       }
@@ -578,8 +633,8 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
       if (p >= c0 && p < c1) sels[p - c0] = 1;
     }
     __syncthreads();
-    const double tau = sh.tau;
-    if (tau != 0.0) {
+    const bool apply = sh.apply != 0;
+    if (apply) {
       const T scale = vsh[k];
       for (int i = k + 1 + tid; i < s; i += QR_THREADS) vsh[i] = vsh[i] * scale;
     }
@@ -590,21 +645,22 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
 
     // apply H_k to the owned free columns: short columns NC at a time per
     // warp (many loads in flight), long ones two at a time
-    const T ttau = (T)tau;
+    const T ttau = sizeof(T) == 8 ? (T)sh.tau : (T)sh.tauf;
+    const int emax = sh.emax;
     unsigned long long key = 0ull;
-    double psum = 0.0;
+    Fix128 psum = {0ull, 0ull};
     if (s - k <= 256) {
-      update_columns<T, 8>(A, lda, c0, ncols, sels, vsh, ttau, tau != 0.0, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
-                           psum);
+      update_columns<T, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
+                           psum, emax);
     } else if (s - k <= 1024) {
-      update_columns<T, 4>(A, lda, c0, ncols, sels, vsh, ttau, tau != 0.0, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
-                           psum);
+      update_columns<T, 4>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
+                           psum, emax);
     } else {
     for (int j0 = warp; j0 < ncols; j0 += 2 * QR_WARPS) {
       const int jb = j0 + QR_WARPS;
       const bool va = !sels[j0], vb = jb < ncols && !sels[jb];
       T ka = (T)0, kb = (T)0;
-      if (tau != 0.0) {
+      if (apply) {
         if (va && vb) {
           apply_reflector2(A + (int64_t)(c0 + j0) * lda, A + (int64_t)(c0 + jb) * lda, vsh, ttau, k, s, lane, ka, kb);
         } else {
@@ -619,10 +675,10 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
       // their update (its latency hides behind the other warps' passes)
       const bool mine = (lane == 0 && va) || (lane == 1 && vb);
       downdate_lane(mine, lane == 0 ? j0 : jb, (double)(lane == 0 ? ka : kb), A + (int64_t)c0 * lda, lda, k, s,
-                    lane, TOL3Z, vn1s, vn2s, c0, key, psum, 0);
+                    lane, TOL3Z, vn1s, vn2s, c0, key, psum, emax, 0);
     }
     }
-    cta_reduce(key, psum, sh);
+    cta_reduce_fix(key, psum, sh);
   }
 
   // outputs; status_out starts at FFC_OK and a timeout anywhere in the group wins
@@ -630,7 +686,8 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (sh.status == FFC_E_TIMEOUT) atomicExch(it.status_out, (int)FFC_E_TIMEOUT);
     if (a.rank == 0) {
       *it.rank_out = k;
-      *it.r22_out = sh.fro2 > 0.0 ? sqrt(sh.sum) / sqrt(sh.fro2) : 0.0;
+      const double fin = k == 0 ? sh.sum : fix_value(sh.fsum, sh.emax);
+      *it.r22_out = sh.fro2 > 0.0 ? sqrt(fin) / sqrt(sh.fro2) : 0.0;
       if (sh.status != FFC_E_TIMEOUT) atomicCAS(it.status_out, (int)FFC_OK, sh.status);
     }
   }

@@ -279,6 +279,116 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_kernel(const float* _
 }
 
 // ----------------------------------------------------------------------------
+// inference forward on the tensor cores: the 128 x 128 layer as FP16 x FP16
+// products with FP32 accumulation (mma.sync m16n8k16); the first layer (K = 12)
+// on the FP32 pipes, its activations rounded to FP16 as the product's operand
+
+constexpr int TC_ROWS = 128;       // rows per tile: 8 warps x 16
+constexpr int HS = NH + 8;         // FP16 row stride in shared memory (272 B: ldmatrix rows hit distinct banks)
+
+struct TcSmem {
+  alignas(16) __half W2[NH * HS];        // W2[j][k]: the B operand (k x n, "col")
+  alignas(16) __half H1[TC_ROWS * HS];   // h1[r][k]: the A operand (row-major)
+  alignas(16) float W1T[NF * NH];
+  alignas(16) float X[TC_ROWS * NF];
+  alignas(16) float b1[NH];
+  alignas(16) float b2[NH];
+  alignas(16) float w3[NH];
+  float b3;
+};
+
+__device__ __forceinline__ void ldsm_x4(const void* p, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                          unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float* __restrict__ P,
+                                                                     const float* __restrict__ F, int64_t R,
+                                                                     float* __restrict__ logits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < NH * NH; e += blockDim.x) S.W2[(e / NH) * HS + (e % NH)] = __float2half_rn(P[OFF_W2 + e]);
+  for (int e = tid; e < NH * NF; e += blockDim.x) S.W1T[(e % NF) * NH + (e / NF)] = half_round(P[OFF_W1 + e]);
+  for (int j = tid; j < NH; j += blockDim.x) {
+    S.b1[j] = half_round(P[OFF_B1 + j]);
+    S.b2[j] = half_round(P[OFF_B2 + j]);
+    S.w3[j] = half_round(P[OFF_W3 + j]);
+  }
+  if (tid == 0) S.b3 = half_round(P[OFF_B3]);
+  __syncthreads();
+  // layer 1: thread owns unit j for rows r0, r0 + 2, ...
+  const int j = tid & (NH - 1), r_first = tid >> 7;
+  float w1[NF];
+#pragma unroll
+  for (int kk = 0; kk < NF; ++kk) w1[kk] = S.W1T[kk * NH + j];
+  const float b1j = S.b1[j];
+  const int64_t tiles = (R + TC_ROWS - 1) / TC_ROWS;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t row0 = t * TC_ROWS;
+    __syncthreads();
+    for (int e = tid; e < TC_ROWS * NF; e += blockDim.x) {
+      const int64_t r = row0 + e / NF;
+      S.X[e] = r < R ? F[row0 * NF + e] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = r_first; r < TC_ROWS; r += 2) {
+      float z = b1j;
+#pragma unroll
+      for (int kk = 0; kk < NF; ++kk) z = fmaf(w1[kk], S.X[r * NF + kk], z);
+      S.H1[r * HS + j] = __float2half_rn(gelu_f(z));
+    }
+    __syncthreads();
+    // layer 2: warp w, rows 16 w .. 16 w + 15, all 128 units (16 n-tiles of 8)
+    float acc[16][4];
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) { acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f; }
+    const int q = lane >> 3;   // ldmatrix: the matrix this lane addresses a row of
+#pragma unroll
+    for (int ks = 0; ks < NH / 16; ++ks) {
+      unsigned a0, a1, a2, a3;
+      ldsm_x4(&S.H1[(16 * warp + (lane & 15)) * HS + ks * 16 + (lane >> 4) * 8], a0, a1, a2, a3);
+#pragma unroll
+      for (int np = 0; np < 8; ++np) {
+        unsigned b0, b1, b2, b3;
+        ldsm_x4(&S.W2[(np * 16 + (q >> 1) * 8 + (lane & 7)) * HS + ks * 16 + (q & 1) * 8], b0, b1, b2, b3);
+        mma_16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
+        mma_16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+    // epilogue: h2 = GELU(z2 + b2), o = w3 . h2 + b3; lane holds rows lane/4 and lane/4 + 8,
+    // columns 8 nt + 2 (lane % 4) + {0, 1}
+    float po0 = 0.0f, po1 = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      const int c = nt * 8 + 2 * (lane & 3);
+      po0 = fmaf(S.w3[c], gelu_f(acc[nt][0] + S.b2[c]), po0);
+      po0 = fmaf(S.w3[c + 1], gelu_f(acc[nt][1] + S.b2[c + 1]), po0);
+      po1 = fmaf(S.w3[c], gelu_f(acc[nt][2] + S.b2[c]), po1);
+      po1 = fmaf(S.w3[c + 1], gelu_f(acc[nt][3] + S.b2[c + 1]), po1);
+    }
+    po0 += __shfl_xor_sync(0xffffffffu, po0, 1);
+    po0 += __shfl_xor_sync(0xffffffffu, po0, 2);
+    po1 += __shfl_xor_sync(0xffffffffu, po1, 1);
+    po1 += __shfl_xor_sync(0xffffffffu, po1, 2);
+    if ((lane & 3) == 0) {
+      const int64_t ra = row0 + 16 * warp + (lane >> 2), rb = ra + 8;
+      if (ra < R) logits[ra] = po0 + S.b3;
+      if (rb < R) logits[rb] = po1 + S.b3;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // training: per-node softmax cross-entropy and the backward pass
 
 template <typename T>
@@ -733,11 +843,25 @@ ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const 
   return FFC_OK;
 }
 
-ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st) {
+// training forward: FP32 activations throughout (the backward recomputes them the same way)
+static ffc_status launch_mlp_forward_f32(const float* params, const float* feats, int64_t R, float* logits,
+                                         cudaStream_t st) {
   if (R <= 0) return FFC_OK;
   const size_t smem = sizeof(FwdSmem);
   FFC_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   mlp_forward_kernel<<<net_grid(R, 2), NET_THREADS, smem, st>>>(params, feats, R, logits);
+  FFC_CUDA(cudaGetLastError());
+  return FFC_OK;
+}
+
+// inference forward: the 128 x 128 layer on the tensor cores (FP16 operands)
+ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st) {
+  if (R <= 0) return FFC_OK;
+  const size_t smem = sizeof(TcSmem);
+  FFC_CUDA(cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tiles = (R + TC_ROWS - 1) / TC_ROWS;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 2));
+  mlp_forward_tc_kernel<<<grid, NET_THREADS, smem, st>>>(params, feats, R, logits);
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
 }
@@ -780,7 +904,7 @@ ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const d
                                 const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,
                                 double* loss_part, float* part, int n_part, float* grad, cudaStream_t st) {
   FFC_REQUIRE(n_part >= 1, "gradient partial count must be >= 1");
-  ffc_status rc = launch_mlp_forward(params, feats, R, logits, st);
+  ffc_status rc = launch_mlp_forward_f32(params, feats, R, logits, st);
   if (rc != FFC_OK) return rc;
   node_ce_kernel<<<n_nodes, 256, 0, st>>>(logits, targets, node_off_dev, n_nodes, g_o, loss_part);
   FFC_CUDA(cudaGetLastError());

@@ -77,12 +77,18 @@ def test_features_match_oracle(ffc, kind, pts):
     assert np.all(np.abs(Fg[:, 4:] - Fo[:, 4:]) <= 2e-5 * scale[:, None])
 
 
-def test_forward_matches_oracle(ffc):
+@pytest.mark.parametrize("R", [1000, 1, 128, 50000])
+def test_forward_matches_oracle(ffc, R):
+    """Inference forward (tensor-core product, FP16 first-layer activations)."""
     th = _params(3)
-    F = 1.5 * np.random.default_rng(4).standard_normal((1000, 12))      # 15 tiles + a ragged 40
-    og = ffc.ffc_mlp_forward(_t(th), _t(F, torch.float32)).cpu().numpy()
-    oo, _ = omlp.forward(omlp.half_weights(th), F.astype(np.float32))
-    assert np.max(np.abs(og - oo) / (1.0 + np.abs(oo))) < 2e-5
+    F = (1.5 * np.random.default_rng(4).standard_normal((R, 12))).astype(np.float32)   # ragged tails
+    og = ffc.ffc_mlp_forward(_t(th), _t(F)).cpu().numpy()
+    oo, _ = omlp.forward(omlp.half_weights(th), F.astype(np.float64), h1_half=True)
+    err = np.abs(og - oo) / (1.0 + np.abs(oo))
+    # FP32 accumulation; a few activations may round to the neighbouring FP16
+    # value where the FP32 and FP64 GELU straddle a rounding boundary
+    assert np.max(err) < 2e-3
+    assert np.mean(err < 3e-5) > 0.9
 
 
 def test_loss_grad_match_oracle_and_are_deterministic(ffc):
@@ -158,7 +164,7 @@ def test_proposal_is_a_valid_draw_from_the_oracle_pool(ffc, pool_rows):
         # keys of the oracle (FP64 network); the GPU's FP32 logits may only
         # swap rows whose keys are within the logits' rounding of the cut
         F = oprop.features(Y, pool, x_c, rho, kern, proj)
-        o, _ = omlp.forward(omlp.half_weights(th), F)
+        o, _ = omlp.forward(omlp.half_weights(th), F, h1_half=True)
         keys = oprop.es_keys(oprop.mixed_weights(o), 9, 77)
         pos = {int(r): i for i, r in enumerate(pool)}
         sel = np.array([pos[int(r)] for r in rows_g])
