@@ -474,6 +474,177 @@ __device__ __forceinline__ void update_columns(T* __restrict__ A, int64_t lda, i
   }
 }
 
+// ---- vectorised column updates (16-byte loads; the column base and lda must be
+// 16-byte aligned). Vector q of a lane covers rows kb + W q .. kb + W q + W - 1
+// with kb = k rounded down to W; rows outside [k, s) are left unchanged.
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ float vget(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4& v, int e, float x) {
+  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void vset(double2& v, int e, double x) { if (e == 0) v.x = x; else v.y = x; }
+
+// NC columns per warp pass, M vectors per lane per column, the whole
+// segment [kb, s) held in registers (s - kb <= 32 W M): one round of loads
+// for the dot, the axpy from registers, then the lane-parallel downdate.
+template <typename T, int NC, int M>
+__device__ __forceinline__ void update_columns_vec(T* __restrict__ A, int64_t lda, int c0, int ncols,
+                                                   const uint8_t* __restrict__ sels, const T* __restrict__ vsh,
+                                                   T ttau, bool apply, int k, int s, int warp, int lane,
+                                                   double tol3z, double* __restrict__ vn1s,
+                                                   double* __restrict__ vn2s, unsigned long long& key,
+                                                   Fix128& psum, int emax) {
+  using V4 = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int kb = k & ~(W - 1);
+  for (int j0 = warp * NC; j0 < ncols; j0 += QR_WARPS * NC) {
+    bool va[NC];
+    T* base = A + (int64_t)(c0 + j0) * lda;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) va[c] = (j0 + c < ncols) && !sels[j0 + c];
+    T ak[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ak[c] = (T)0;
+    if (apply) {
+      V4 x[NC][M];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = kb + W * (lane + 32 * m);
+          if (va[c] && r0 < s) x[c][m] = *reinterpret_cast<const V4*>(base + (int64_t)c * lda + r0);
+          else x[c][m] = V4{};
+        }
+      T acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = (T)0;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int r0 = kb + W * (lane + 32 * m);
+        if (r0 < s) {
+          const V4 vv = *reinterpret_cast<const V4*>(vsh + r0);
+#pragma unroll
+          for (int e = 0; e < W; ++e) {
+            const int r = r0 + e;
+            const T v = (r >= k && r < s) ? vget(vv, e) : (T)0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = fma(v, vget(x[c][m], e), acc[c]);
+          }
+        }
+      }
+      T tw[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) tw[c] = ttau * warp_sum(acc[c]);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int r0 = kb + W * (lane + 32 * m);
+        if (r0 < s) {
+          const V4 vv = *reinterpret_cast<const V4*>(vsh + r0);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (!va[c]) continue;
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+              const int r = r0 + e;
+              if (r >= k && r < s) vset(x[c][m], e, fma(-tw[c], vget(vv, e), vget(x[c][m], e)));
+            }
+            *reinterpret_cast<V4*>(base + (int64_t)c * lda + r0) = x[c][m];
+          }
+        }
+      }
+      // row k sits in lane 0's first vector, component k - kb
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ak[c] = __shfl_sync(0xffffffffu, vget(x[c][0], k - kb), 0);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ak[c] = va[c] ? base[(int64_t)c * lda + k] : (T)0;
+    }
+    T my_ak = ak[0];
+    bool mine = va[0] && lane == 0;
+#pragma unroll
+    for (int c = 1; c < NC; ++c)
+      if (lane == c) { my_ak = ak[c]; mine = va[c]; }
+    downdate_lane(mine, j0 + lane, (double)my_ak, base, lda, k, s, lane, tol3z, vn1s, vn2s, c0, key, psum, emax,
+                  j0);
+  }
+}
+
+// One column per warp pass, rows in chunks of 32 W 8 (longer columns): the
+// dot streams the chunks, the axpy reloads them (L1/L2 hits).
+template <typename T>
+__device__ __forceinline__ void update_column_vec_chunked(T* __restrict__ A, int64_t lda, int c0, int ncols,
+                                                          const uint8_t* __restrict__ sels,
+                                                          const T* __restrict__ vsh, T ttau, bool apply, int k,
+                                                          int s, int warp, int lane, double tol3z,
+                                                          double* __restrict__ vn1s, double* __restrict__ vn2s,
+                                                          unsigned long long& key, Fix128& psum, int emax) {
+  using V4 = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W, M = 8;
+  const int kb = k & ~(W - 1);
+  for (int j = warp; j < ncols; j += QR_WARPS) {
+    const bool va = !sels[j];
+    T* col = A + (int64_t)(c0 + j) * lda;
+    T ak = (T)0;
+    if (va && apply) {
+      T acc = (T)0, acc2 = (T)0;
+      for (int cb = kb; cb < s; cb += 32 * W * M) {
+        V4 x[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = cb + W * (lane + 32 * m);
+          x[m] = r0 < s ? *reinterpret_cast<const V4*>(col + r0) : V4{};
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = cb + W * (lane + 32 * m);
+          if (r0 < s) {
+            const V4 vv = *reinterpret_cast<const V4*>(vsh + r0);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+              const int r = r0 + e;
+              const T v = (r >= k && r < s) ? vget(vv, e) : (T)0;
+              if (e & 1) acc2 = fma(v, vget(x[m], e), acc2); else acc = fma(v, vget(x[m], e), acc);
+            }
+          }
+        }
+      }
+      const T tw = ttau * warp_sum(acc + acc2);
+      for (int cb = kb; cb < s; cb += 32 * W * M) {
+        V4 x[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = cb + W * (lane + 32 * m);
+          x[m] = r0 < s ? *reinterpret_cast<const V4*>(col + r0) : V4{};
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = cb + W * (lane + 32 * m);
+          if (r0 < s) {
+            const V4 vv = *reinterpret_cast<const V4*>(vsh + r0);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+              const int r = r0 + e;
+              if (r >= k && r < s) vset(x[m], e, fma(-tw, vget(vv, e), vget(x[m], e)));
+            }
+            *reinterpret_cast<V4*>(col + r0) = x[m];
+            if (cb == kb && m == 0) ak = vget(x[0], k - kb);
+          }
+        }
+      }
+      ak = __shfl_sync(0xffffffffu, ak, 0);
+    } else if (va) {
+      ak = col[k];
+    }
+    downdate_lane(va && lane == 0, j, (double)ak, A + (int64_t)c0 * lda, lda, k, s, lane, tol3z, vn1s, vn2s, c0,
+                  key, psum, emax, 0);
+  }
+}
+
 template <typename T>
 __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
                             double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
@@ -490,6 +661,8 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
   // stored in: the downdate subtracts a_kj^2, and a_kj is only as accurate as
   // the stored data, so FP32 columns need sqrt(2^-24), not sqrt(2^-53)
   const double TOL3Z = sizeof(T) == 4 ? 2.44140625e-04 : 1.0536712127723509e-08;
+  // 16-byte vector access to the columns needs an aligned base and leading dimension
+  const bool vec_ok = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (((uint64_t)lda * sizeof(T)) % 16 == 0);
 
   // initial squared column norms, kept in shared memory for the whole factorisation
   for (int j = warp; j < ncols; j += QR_WARPS) {
@@ -649,7 +822,25 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     const int emax = sh.emax;
     unsigned long long key = 0ull;
     Fix128 psum = {0ull, 0ull};
-    if (s - k <= 256) {
+    constexpr int W = Vec<T>::W;
+    const int vrows = s - (k & ~(W - 1));
+    if (vec_ok) {
+      if (vrows <= 32 * W)
+        update_columns_vec<T, 8, 1>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                    key, psum, emax);
+      else if (vrows <= 64 * W)
+        update_columns_vec<T, 4, 2>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                    key, psum, emax);
+      else if (vrows <= 128 * W)
+        update_columns_vec<T, 2, 4>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                    key, psum, emax);
+      else if (vrows <= 256 * W)
+        update_columns_vec<T, 1, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                    key, psum, emax);
+      else
+        update_column_vec_chunked<T>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                     key, psum, emax);
+    } else if (s - k <= 256) {
       update_columns<T, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s, key,
                            psum, emax);
     } else if (s - k <= 1024) {
@@ -829,7 +1020,10 @@ trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
 
 template <typename T>
 size_t cpqr_smem_bytes(int s_max) {
-  return QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) + (size_t)std::max(s_max, 1) * sizeof(T);
+  // the Householder vector is last; 8 spare elements keep the vector loads of
+  // its final (partial) 16-byte group inside the allocation
+  return QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) +
+         (size_t)(std::max(s_max, 1) + 8) * sizeof(T);
 }
 
 template <typename T>

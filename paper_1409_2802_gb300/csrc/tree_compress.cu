@@ -213,7 +213,10 @@ ffc_status grow(char** buf, size_t* have, size_t want, cudaStream_t st) {
 }
 
 // Bytes of sampled blocks one QR launch may hold: below the 129 MB L2.
-constexpr size_t QR_L2_BUDGET = 96ull << 20;
+#ifndef FFC_QR_L2_BUDGET_MB
+#define FFC_QR_L2_BUDGET_MB 96
+#endif
+constexpr size_t QR_L2_BUDGET = (size_t)FFC_QR_L2_BUDGET_MB << 20;
 
 // Learned sampler: for every output node, the candidate pool (whole far field
 // or a uniform pool), features, network logits and the weighted draw of its
