@@ -41,11 +41,66 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = {
-    "workload": "tree_compress_gaussian_mixture_N65536_d16",
-    "N": 65536, "d": 16, "components": 8, "data_seed": 0, "leaf_size": 256, "kernel": "gaussian", "h": 2.0,
-    "tol": 1e-6, "s0": 128, "s_max": 2048, "min_level": 2, "xi": 1.0, "sample_seed": 0,
+WORKLOADS = {
+    # N = 65,536 in d = 16, 8-component mixture, leaf 256 (levels 2..8, 508 nodes), Gaussian h = 2
+    "c2": {"workload": "tree_compress_gaussian_mixture_N65536_d16", "gen": "gaussian_mixture", "N": 65536, "d": 16,
+           "components": 8, "data_seed": 0, "leaf_size": 256, "kernel": "gaussian", "h": 2.0, "points": "f64"},
+    # N = 262,144 in d = 128 with per-coordinate variance 1/k, leaf 256 (levels 2..10, 2,044 nodes)
+    "c3-laplace": {"workload": "tree_compress_decaying_mixture_N262144_d128_laplace", "gen": "decaying_mixture",
+                   "N": 262144, "d": 128, "components": 16, "data_seed": 1000, "leaf_size": 256, "kernel": "laplace",
+                   "points": "f64"},
+    "c3-poly": {"workload": "tree_compress_decaying_mixture_N262144_d128_poly3", "gen": "decaying_mixture",
+                "N": 262144, "d": 128, "components": 16, "data_seed": 1000, "leaf_size": 256, "kernel": "polynomial",
+                "h": 128.0, "c": 1.0, "p": 3, "points": "f64"},
+    # N = 100,000 of intrinsic dimension 10 in d = 1,000 (FP32), leaf 512 (levels 2..8, 508 nodes),
+    # Gaussian with h = the median pairwise distance
+    "c4": {"workload": "tree_compress_low_intrinsic_N100000_d1000_gaussian", "gen": "low_intrinsic", "N": 100000,
+           "d": 1000, "d_i": 10, "data_seed": 1000, "leaf_size": 512, "kernel": "gaussian", "h": "median",
+           "points": "f32"},
 }
+COMMON = {"tol": 1e-6, "s0": 128, "s_max": 2048, "min_level": 2, "xi": 1.0, "sample_seed": 0}
+WORKLOAD = dict(WORKLOADS["c2"], **COMMON)
+
+
+def select_workload(name: str):
+    global WORKLOAD
+    WORKLOAD = dict(WORKLOADS[name], **COMMON)
+    WORKLOAD["name"] = name
+
+
+def workload_points(seed_offset: int = 0):
+    """The workload's synthetic points (numpy, float64 or float32 as the workload stores them)."""
+    import workloads
+    W = WORKLOAD
+    seed = W["data_seed"] + seed_offset
+    if W["gen"] == "gaussian_mixture":
+        return workloads.gaussian_mixture(N=W["N"], d=W["d"], k=W["components"], seed=seed)
+    if W["gen"] == "decaying_mixture":
+        return workloads.decaying_mixture(N=W["N"], d=W["d"], k=W["components"], seed=seed)
+    return workloads.low_intrinsic(N=W["N"], d_i=W["d_i"], d_e=W["d"], seed=seed)
+
+
+def workload_kernel(kernels_mod, P):
+    """Kernel description for ``kernels_mod`` (the binding or the oracle) on the points P."""
+    import workloads
+    W = WORKLOAD
+    kind = {"gaussian": "GAUSSIAN", "laplace": "LAPLACE", "polynomial": "POLYNOMIAL"}[W["kernel"]]
+    code = getattr(kernels_mod, kind)
+    h = W.get("h", 1.0)
+    if h == "median":
+        h = workloads.median_pairwise_distance(P)
+    return kernels_mod.Kernel(code, h=float(h), c=float(W.get("c", 1.0)), p=int(W.get("p", 3)))
+
+
+def kernel_label(h_value=None):
+    W = WORKLOAD
+    if W["kernel"] == "gaussian":
+        return f"gaussian h={W['h'] if h_value is None else round(h_value, 6)}"
+    if W["kernel"] == "laplace":
+        return f"laplace |x-y|^-{W['d'] - 2}"
+    return f"polynomial (x.y/{W['h']:g} + {W['c']:g})^{W['p']}"
+
+
 METRIC = "nodes compressed/sec at ID rel. error <=1e-6; chosen form vs plain FP64 GPU"
 UNIT = "nodes/s"
 
@@ -124,24 +179,21 @@ class ClockSampler:
 
 
 def build_inputs(torch, dev):
-    import workloads
     from paper_1409_2802_gb300 import ffc
-    W = WORKLOAD
     rank, _, _ = _env_rank()
-    P = workloads.gaussian_mixture(N=W["N"], d=W["d"], k=W["components"], seed=W["data_seed"] + rank)
+    P = workload_points(rank)
     Pd = torch.tensor(P, device=dev)
-    tree = ffc.ffc_build_tree(Pd, W["leaf_size"])
+    tree = ffc.ffc_build_tree(Pd, WORKLOAD["leaf_size"])
     Pp = Pd[tree.perm].contiguous()
-    return P, tree, Pp
+    return P, tree, Pp, workload_kernel(ffc, P)
 
 
 def precision_code(ffc, name):
     return ffc.FP64 if name == "fp64" else ffc.MIXED
 
 
-def run_gpu_steps(torch, ffc, Pp, tree, precision, steps, warmup, flush_buf, stream, result=None, proposal=None):
+def run_gpu_steps(torch, ffc, Pp, tree, k, precision, steps, warmup, flush_buf, stream, result=None, proposal=None):
     W = WORKLOAD
-    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
 
     def step(res):
         return ffc.ffc_compress_tree(Pp, tree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
@@ -168,7 +220,7 @@ def run_gpu_steps(torch, ffc, Pp, tree, precision, steps, warmup, flush_buf, str
     return res, times, prof
 
 
-def run_e2e(torch, ffc, P_host_perm, tree, precision, steps, warmup, stream, proposal=None):
+def run_e2e(torch, ffc, P_host_perm, tree, k, precision, steps, warmup, stream, proposal=None):
     """Same metric through host buffers: pinned H2D inputs, compress, D2H results, every step."""
     W = WORKLOAD
     dev = P_host_perm.device if P_host_perm.is_cuda else torch.device("cuda")
@@ -177,7 +229,6 @@ def run_e2e(torch, ffc, P_host_perm, tree, precision, steps, warmup, stream, pro
     dP = torch.empty_like(hP, device=dev)
     dT = {n: torch.empty_like(v, device=dev) for n, v in tree_host.items()}
     dtree = ffc.DeviceTree(tree.depth, tree.perm, dT["begin"], dT["count"], dT["centroid"], dT["radius"])
-    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
     res = None
     h2d = hP.numel() * hP.element_size() + sum(v.numel() * v.element_size() for v in tree_host.values())
     d2h_bytes = []
@@ -217,12 +268,11 @@ def run_e2e(torch, ffc, P_host_perm, tree, precision, steps, warmup, stream, pro
 # --------------------------------------------------------------------------- oracle legs
 
 def oracle_setup():
-    import workloads
+    from oracle import kernels as o_kernels
     from oracle import tree as o_tree
-    W = WORKLOAD
-    P = workloads.gaussian_mixture(N=W["N"], d=W["d"], k=W["components"], seed=W["data_seed"])
-    t = o_tree.build_tree(P, W["leaf_size"])
-    return P[t.perm], t
+    P = workload_points()
+    t = o_tree.build_tree(P, WORKLOAD["leaf_size"])
+    return P[t.perm].astype("float64"), t, workload_kernel(o_kernels, P)
 
 
 def oracle_nodes_in_order(t, seed=12345):
@@ -231,22 +281,21 @@ def oracle_nodes_in_order(t, seed=12345):
     return list(np.random.default_rng(seed).permutation(nodes))
 
 
-def oracle_compress(Pp, t, node):
+def oracle_compress(Pp, t, kernel, node):
     from oracle import compress as o_compress
-    from oracle.kernels import GAUSSIAN, Kernel
     W = WORKLOAD
-    return o_compress.compress_node(Pp, t, int(node), Kernel(GAUSSIAN, h=W["h"]), W["tol"], W["sample_seed"],
-                                    W["s0"], W["s_max"], W["xi"])
+    return o_compress.compress_node(Pp, t, int(node), kernel, W["tol"], W["sample_seed"], W["s0"], W["s_max"],
+                                    W["xi"])
 
 
 def cpu_leg() -> int:
     """Child process: compress nodes in a seeded random order, one JSON line per finished node."""
-    Pp, t = oracle_setup()
+    Pp, t, kernel = oracle_setup()
     order = oracle_nodes_in_order(t)
     print(json.dumps({"ready": True, "of": len(order)}), flush=True)
     t0 = time.perf_counter()
     for i, node in enumerate(order):
-        oracle_compress(Pp, t, node)
+        oracle_compress(Pp, t, kernel, node)
         print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
     return 0
 
@@ -263,7 +312,8 @@ class OracleStream:
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
         for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
             env.pop(k, None)
-        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", "1"], env=env,
+        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", "1",
+                                      "--workload", WORKLOAD.get("name", "c2")], env=env,
                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         self.of, self.ready_t, self.done = None, None, 0
         self.thread = threading.Thread(target=self._read, daemon=True)
@@ -390,47 +440,47 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src):
     }
 
 
-def accuracy_sample(torch, ffc, Pp, tree, results, n_sample=12, seed=7):
-    """Full-block ID error of a seeded sample of nodes for each timed arm (outside the timed region).
-
-    For each pair of arms that differ only in precision (same sampler, hence
-    the same rows), the largest |e_mixed - e_fp64| is the reading of the
-    accuracy gate |e_mixed - e_oracle| <= 1e-6: the FP64 GPU path equals the
-    oracle's ID on the same rows (tests), so it stands in for the oracle here.
-    """
+def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7):
+    """Full-block ID error of a seeded sample of nodes of one arm's result (outside the timed region)."""
     import numpy as np
     W = WORKLOAD
-    k = ffc.Kernel(ffc.GAUSSIAN, h=W["h"])
-    host = {p: ffc.tree_result_to_host(r) for p, r in results.items()}
-    views = {p: ffc.tree_result_views(r) for p, r in results.items()}
-    any_p = next(iter(host))
-    nodes = host[any_p]["node"]
+    h = ffc.tree_result_to_host(res)
+    v = ffc.tree_result_views(res)
+    nodes = h["node"]
     pick = sorted(np.random.default_rng(seed).choice(len(nodes), min(n_sample, len(nodes)), replace=False).tolist())
     begin, count = tree.begin.cpu().numpy(), tree.count.cpu().numpy()
-    errs = {p: [] for p in results}
+    errs = []
     for i in pick:
         node = int(nodes[i])
         b, n = int(begin[node]), int(count[node])
         far = ffc.ffc_far_field(Pp, x_c=tree.centroid[node].contiguous(), radius=float(tree.radius[node]), xi=W["xi"],
                                 ex_begin=b, ex_end=b + n)
-        for p in results:
-            h, v = host[p], views[p]
-            r = int(h["rank"][i])
-            skel = v["skel"][int(h["skel_off"][i]): int(h["skel_off"][i]) + n]
-            off = int(h["T_off"][i])
-            T = v["T"][off: off + r * (n - r)].view(n - r, r).t() if r else torch.zeros((0, n), device=Pp.device,
-                                                                                          dtype=torch.float64)
-            errs[p].append(ffc.ffc_id_error(k, Pp, Pp[b:b + n], skel, T, r, rows=far))
-    out = {"nodes_checked": [int(nodes[i]) for i in pick]}
-    for p in errs:
-        e = np.asarray(errs[p])
+        r = int(h["rank"][i])
+        skel = v["skel"][int(h["skel_off"][i]): int(h["skel_off"][i]) + n]
+        off = int(h["T_off"][i])
+        T = v["T"][off: off + r * (n - r)].view(n - r, r).t() if r else torch.zeros((0, n), device=Pp.device,
+                                                                                      dtype=torch.float64)
+        errs.append(ffc.ffc_id_error(k, Pp, Pp[b:b + n], skel, T, r, rows=far))
+    return {"nodes": [int(nodes[i]) for i in pick], "errors": errs, "mean_rank": float(h["rank"].mean()),
+            "mean_s": float(h["s"].mean())}
+
+
+def accuracy_summary(per_arm):
+    """Per-arm error statistics; for each pair of arms that differ only in precision (same sampler, hence
+    the same rows), the largest |e_mixed - e_fp64| is the reading of the accuracy gate
+    |e_mixed - e_oracle| <= 1e-6: the FP64 GPU path equals the oracle's ID on the same rows (tests), so it
+    stands in for the oracle here."""
+    import numpy as np
+    out = {"nodes_checked": next(iter(per_arm.values()))["nodes"]}
+    for p, a in per_arm.items():
+        e = np.asarray(a["errors"])
         out[p] = {"median_full_block_error": float(np.median(e)), "max_full_block_error": float(e.max()),
-                  "nodes_at_or_below_1e-5": int(np.sum(e <= 1e-5)), "mean_rank": float(host[p]["rank"].mean()),
-                  "mean_s": float(host[p]["s"].mean())}
+                  "nodes_at_or_below_1e-5": int(np.sum(e <= 1e-5)), "mean_rank": a["mean_rank"],
+                  "mean_s": a["mean_s"]}
     for samp in ("learned", "uniform"):
         a, b = f"mixed_{samp}", f"fp64_{samp}"
-        if a in errs and b in errs:
-            dmax = float(max(abs(x - y) for x, y in zip(errs[a], errs[b])))
+        if a in per_arm and b in per_arm:
+            dmax = float(max(abs(x - y) for x, y in zip(per_arm[a]["errors"], per_arm[b]["errors"])))
             out[f"max_abs_diff_mixed_vs_fp64_{samp}"] = dmax
             out[f"within_1e-6_{samp}"] = dmax <= 1e-6
     return out
@@ -453,8 +503,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2 (default, the headline): d=16 mixture; c3-laplace / c3-poly: d=128; c4: d=1000 FP32")
     ap.add_argument("--_cpu-leg", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    select_workload(args.workload)
 
     if args._cpu_leg is not None:
         return cpu_leg()
@@ -480,7 +533,7 @@ def main():
         proj = torch.as_tensor(workloads.projections(WORKLOAD["d"], seed=7)).to(dev)
         proposal = (params, proj)
         torch.cuda.empty_cache()
-    P, tree, Pp = build_inputs(torch, dev)
+    P, tree, Pp, kern = build_inputs(torch, dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prec = precision_code(ffc, args.precision)
@@ -490,7 +543,7 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, prec_code, steps, warmup, flush, stream,
+        res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, kern, prec_code, steps, warmup, flush, stream,
                                          proposal=prop)
         torch.cuda.synchronize()
         total = sum(times)
@@ -513,7 +566,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == ffc.FP64 else "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["workload"], "precision": args.precision, "sampler": args.sampler,
-                   "nodes": n_nodes, "levels": "2..8", "kernel": "gaussian h=2", "tol": WORKLOAD["tol"],
+                   "nodes": n_nodes, "levels": f"2..{tree.depth}", "kernel": kernel_label(kern.h),
+                   "points": WORKLOAD["points"], "tol": WORKLOAD["tol"],
                    "s": "128 doubling to 2048", "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk, "gpu_launches": int(prof["launches"]),
@@ -521,7 +575,13 @@ def main():
     }
     if train_info is not None:
         line["config"]["proposal_training"] = train_info
-    results = {arm: res}
+    # each arm's sampled errors are taken as soon as it has run and its result is released, so
+    # that only one arm's workspace is resident at a time
+    errors = {}
+    if not args.no_accuracy and rank == 0:
+        errors[arm] = arm_errors(torch, ffc, Pp, tree, kern, res)
+    res.close()
+    del res
     if not args.no_fp64_compare:
         fsteps = max(3, args.steps // 3)
         arms = [("fp64", "uniform")]
@@ -536,16 +596,19 @@ def main():
             v_ = n_nodes * fsteps * world / (ms_ / 1e3)
             other[key] = {"value": v_, "unit": UNIT, "ms_per_step": ms_ / fsteps, "steps": fsteps,
                           "roofline": qr_roofline(pf_, fsteps, pname, peaks, peak_src)}
-            results[key] = r_
+            if not args.no_accuracy and rank == 0:
+                errors[key] = arm_errors(torch, ffc, Pp, tree, kern, r_)
+            r_.close()
+            del r_
         if "fp64_uniform" in other:
             line["fp64_plain"] = other.pop("fp64_uniform")
             line["speedup_vs_fp64"] = value / line["fp64_plain"]["value"]
         if other:
             line["arms"] = other
-    if not args.no_accuracy and rank == 0:
-        line["accuracy"] = accuracy_sample(torch, ffc, Pp, tree, results)
+    if errors:
+        line["accuracy"] = accuracy_summary(errors)
     if not args.no_e2e:
-        line["e2e"] = run_e2e(torch, ffc, Pp, tree, prec, max(3, args.steps // 2), 2, stream, proposal=proposal)
+        line["e2e"] = run_e2e(torch, ffc, Pp, tree, kern, prec, max(3, args.steps // 2), 2, stream, proposal=proposal)
     if oracle is not None:
         line["cpu_baseline"] = finish_cpu_baseline(oracle, args.cpu_seconds)
     if rank == 0:

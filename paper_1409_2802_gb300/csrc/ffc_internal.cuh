@@ -167,7 +167,55 @@ struct SelectItem {
   uint64_t stream_id;
   int64_t* rows_out;     // capacity s
   int64_t* s_out;        // device: rows written (may be NULL)
+  uint64_t* keys;        // capacity P: sort keys kept between passes, or NULL (recomputed)
 };
+
+// ----------------------------------------------------------------------------
+// far-field membership (FP64, the uniform sampler's test) and the proposal's
+// feature transform, shared by the per-node and the tiled tree kernels
+
+template <typename TP>
+__device__ __forceinline__ bool far_member(const TP* __restrict__ Y, int d, int64_t j, const FarItem& it,
+                                           double thr2) {
+  if (j >= it.M || (j >= it.ex_begin && j < it.ex_end)) return false;
+  const TP* y = Y + j * (int64_t)d;
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double df = ld_point(y + k) - __ldg(it.x_c + k);
+    acc = fma(df, df, acc);
+  }
+  return acc >= thr2;
+}
+
+__device__ __forceinline__ double far_thr2(const FarItem& it) {
+  const double thr = it.xi * (it.radius ? *it.radius : it.radius_host);
+  return thr * thr;
+}
+
+// FP32 sums of one (target row, node) pair and the 12 features made from them
+constexpr int FEAT_NF = 12;
+struct FeatSums { float dd, yy, yx, xx, p[8]; };
+
+__device__ __forceinline__ void feature_values(const FeatSums& S, float rho, ffc_kernel k, int d, float out[FEAT_NF]) {
+  const float r = sqrtf(S.dd);
+  const float inv_rho = 1.0f / rho;
+  out[0] = r * inv_rho;
+  float kc;
+  if (k.kind == FFC_GAUSSIAN) {
+    kc = expf(-S.dd / (2.0f * (float)(k.h * k.h)));
+  } else if (k.kind == FFC_LAPLACE) {
+    kc = exp2f((float)(d - 2) * log2f(rho / r));
+  } else {
+    const float num = S.yx / (float)k.h + (float)k.c;
+    const float den = sqrtf(S.yy) * sqrtf(S.xx) / (float)k.h + (float)k.c;
+    kc = powf(num / den, (float)k.p);
+  }
+  out[1] = kc;
+  out[2] = sqrtf(S.yy) * inv_rho;
+  out[3] = rho / (k.kind == FFC_LAPLACE ? 1.0f : (float)k.h);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[4 + q] = S.p[q] * inv_rho;
+}
 
 // ----------------------------------------------------------------------------
 // launchers (implemented in the .cu files; all enqueue on `st`)
@@ -205,10 +253,19 @@ ffc_status launch_features(ffc_kernel k, const void* Y, int dtype, int d, const 
 ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st);
 // keep_max: largest min(s, P) over the items (<= 8192); any pool size P
 ffc_status launch_select(const SelectItem* items_dev, int n_items, int64_t keep_max, uint64_t seed, cudaStream_t st);
-// far-field lists of n_items nodes; tile_cnt: n_items x far_list_tiles(M_max) int64 workspace
-ffc_status launch_far_lists(const void* Y, int dtype, int d, const FarItem* items_dev, int n_items, int64_t M_max,
-                            int64_t* tile_cnt, cudaStream_t st);
-int64_t far_list_tiles(int64_t M);
+// Tiled far-field lists and features of n_items nodes over all N points (candidates [0, N)):
+// yy, yg from launch_point_stats (N and N x 8 floats); node_ws: far_tiles_node_bytes(n_items, d);
+// tile_cnt: n_items x far_tiles_count(N) int64; mask: n_items x 4 far_tiles_count(N) words.
+// Writes each item's ascending list, *count and the features of its rows [0, count); rows
+// [count, cap) of the features are zeroed.
+int64_t far_tiles_count(int64_t N);
+size_t far_tiles_node_bytes(int n_items, int d);
+ffc_status launch_point_stats(const void* Y, int dtype, int64_t N, int d, const double* proj, float* yy, float* yg,
+                              cudaStream_t st);
+ffc_status launch_far_features_tiled(ffc_kernel k, const void* Y, int dtype, int64_t N, int d,
+                                     const FarItem* items_dev, const FeatItem* fitems_dev, int n_items,
+                                     const double* proj, const float* yy, const float* yg, void* node_ws,
+                                     int64_t* tile_cnt, uint32_t* mask, float* feats, cudaStream_t st);
 ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const double* targets,
                                 const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,
                                 double* loss_part, float* part, int n_part, float* grad, cudaStream_t st);

@@ -50,29 +50,6 @@ __device__ __forceinline__ float gelu_prime_f(float z) {
 constexpr int FEAT_THREADS = 256;
 constexpr int FEAT_SMALL_D = 64;
 
-struct FeatSums { float dd, yy, yx, xx, p[8]; };
-
-__device__ __forceinline__ void feature_values(const FeatSums& S, float rho, ffc_kernel k, int d, float out[NF]) {
-  const float r = sqrtf(S.dd);
-  const float inv_rho = 1.0f / rho;
-  out[0] = r * inv_rho;
-  float kc;
-  if (k.kind == FFC_GAUSSIAN) {
-    kc = expf(-S.dd / (2.0f * (float)(k.h * k.h)));
-  } else if (k.kind == FFC_LAPLACE) {
-    kc = exp2f((float)(d - 2) * log2f(rho / r));
-  } else {
-    const float num = S.yx / (float)k.h + (float)k.c;
-    const float den = sqrtf(S.yy) * sqrtf(S.xx) / (float)k.h + (float)k.c;
-    kc = powf(num / den, (float)k.p);
-  }
-  out[1] = kc;
-  out[2] = sqrtf(S.yy) * inv_rho;
-  out[3] = rho / (k.kind == FFC_LAPLACE ? 1.0f : (float)k.h);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) out[4 + q] = S.p[q] * inv_rho;
-}
-
 template <typename TP, bool WARP_PER_ROW>
 __global__ void __launch_bounds__(FEAT_THREADS) features_kernel(const TP* __restrict__ Y, int d, const FeatItem* items,
                                                                 ffc_kernel k, const double* __restrict__ proj,
@@ -659,8 +636,18 @@ __device__ __forceinline__ uint64_t es_sort_key(float logit, double mx, double m
 }
 
 // One CTA per pool: the min(s, P) pool rows with the largest keys, in key
-// order. Pools above SEL_CAP entries are streamed in chunks behind the
-// running best rows.
+// order, ties to the lower pool position. Pools of at most SEL_CAP rows are
+// sorted whole in shared memory. Larger pools: the sort keys of the whole
+// pool are computed once (kept in it.keys when given, else recomputed per
+// pass); a radix select on their bit patterns (SEL_BITS per level, a
+// histogram in shared memory) narrows a key prefix until the keys at or
+// below it hold the n_keep best and number at most SEL_CAP; those are
+// gathered and sorted. Only exact ties of more than SEL_CAP keys (not met
+// with distinct draws) take the ordered tie path.
+constexpr int SEL_BITS = 12, SEL_BINS = 1 << SEL_BITS;
+
+size_t select_smem_bytes() { return (size_t)SEL_CAP * (sizeof(uint64_t) + sizeof(uint32_t)) + SEL_BINS * sizeof(int); }
+
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* items, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SelectItem& it = items[blockIdx.x];
@@ -668,142 +655,136 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
   const int64_t n_keep = P < it.s ? P : it.s;
   if (threadIdx.x == 0 && it.s_out) *it.s_out = n_keep;
   if (n_keep <= 0) return;
+  if (P > SEL_CAP && n_keep > SEL_MAX_KEEP) return;   // rejected on the host
   uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
   uint32_t* pos = reinterpret_cast<uint32_t*>(key + SEL_CAP);
+  int* hist = reinterpret_cast<int*>(pos + SEL_CAP);
   __shared__ double redd[32];
   __shared__ float redf[32];
+  __shared__ int s_bin, s_fill;
+  __shared__ long long s_lt, s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float mx = -INFINITY;
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) mx = fmaxf(mx, it.logits[i]);
+  for (int64_t i = tid; i < P; i += blockDim.x) mx = fmaxf(mx, it.logits[i]);
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = mx;
+  if (lane == 0) redf[warp] = mx;
   __syncthreads();
   mx = redf[0];
   for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, redf[i]);
   double sw = 0.0;
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sw += exp((double)it.logits[i] - (double)mx);
+  for (int64_t i = tid; i < P; i += blockDim.x) sw += exp((double)it.logits[i] - (double)mx);
   for (int off = 16; off > 0; off >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, off);
-  if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = sw;
+  if (lane == 0) redd[warp] = sw;
   __syncthreads();
   sw = 0.0;
   for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sw += redd[i];
   const double mean = sw / (double)P;
   const double dmx = (double)mx;
-  auto fill = [&](int lo, int hi, int64_t base) {   // entries [lo, hi) <- positions base, base + 1, ...
-    for (int e = lo + (int)threadIdx.x; e < hi; e += blockDim.x) {
-      const int64_t i = base + (e - lo);
-      if (i < P) {
-        key[e] = es_sort_key(it.logits[i], dmx, mean, seed, it.stream_id, i);
-        pos[e] = (uint32_t)i;
-      } else {
-        key[e] = ~0ull;
-        pos[e] = 0xFFFFFFFFu;
+  auto key_of = [&](int64_t i) -> uint64_t { return es_sort_key(it.logits[i], dmx, mean, seed, it.stream_id, i); };
+  int m = 0;
+  if (P <= SEL_CAP) {
+    m = (int)P;
+    for (int e = tid; e < m; e += blockDim.x) {
+      key[e] = key_of(e);
+      pos[e] = (uint32_t)e;
+    }
+  } else {
+    const bool stored = it.keys != nullptr;
+    uint64_t pv = 0;        // the top pl bits of the selected prefix
+    int pl = 0;
+    long long c_lt = 0;     // keys below the prefix range
+    long long c_in = P;     // keys inside it
+    for (int level = 0; pl < 64 && c_lt + c_in > SEL_CAP; ++level) {
+      const int nb = min(SEL_BITS, 64 - pl);
+      const int sh = 64 - pl - nb;
+      const int bins = 1 << nb;
+      for (int b = tid; b < bins; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for (int64_t i = tid; i < P; i += blockDim.x) {
+        uint64_t k;
+        if (level == 0) {
+          k = key_of(i);
+          if (stored) it.keys[i] = k;
+        } else {
+          k = stored ? it.keys[i] : key_of(i);
+        }
+        if (pl == 0 || (k >> (64 - pl)) == pv) atomicAdd(&hist[(int)((k >> sh) & (uint64_t)(bins - 1))], 1);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // the bin where c_lt + (keys in lower bins) + (its own keys) first reaches n_keep
+        const int per = (bins + 31) / 32;
+        const int b0 = lane * per;
+        long long own = 0;
+        for (int b = b0; b < b0 + per && b < bins; ++b) own += hist[b];
+        long long inc = own;
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long v = __shfl_up_sync(0xffffffffu, inc, off);
+          if (lane >= off) inc += v;
+        }
+        const long long excl = inc - own;
+        const bool cross = c_lt + excl < n_keep && c_lt + inc >= n_keep;
+        if (cross) {
+          long long run = c_lt + excl;
+          for (int b = b0; b < b0 + per && b < bins; ++b) {
+            if (run + hist[b] >= n_keep) {
+              s_bin = b;
+              s_lt = run;
+              s_cnt = hist[b];
+              break;
+            }
+            run += hist[b];
+          }
+        }
+      }
+      __syncthreads();
+      pv = (pv << nb) | (uint64_t)s_bin;
+      pl += nb;
+      c_lt = s_lt;
+      c_in = s_cnt;
+      __syncthreads();
+    }
+    if (tid == 0) s_fill = 0;
+    __syncthreads();
+    const bool ties = c_lt + c_in > SEL_CAP;   // pl == 64: more than SEL_CAP keys equal pv
+    for (int64_t i = tid; i < P; i += blockDim.x) {
+      const uint64_t k = stored ? it.keys[i] : key_of(i);
+      const bool take = ties ? k < pv : (k >> (64 - pl)) <= pv;
+      if (take) {
+        const int slot = atomicAdd(&s_fill, 1);
+        key[slot] = k;
+        pos[slot] = (uint32_t)i;
       }
     }
-  };
-  if (P > SEL_CAP && n_keep > SEL_MAX_KEEP) return;   // rejected on the host; no endless chunk loop
-  if (P <= SEL_CAP) {
-    int Pp = 1;
-    while (Pp < P) Pp <<= 1;
-    fill(0, Pp, 0);
     __syncthreads();
-    bitonic_sort(key, pos, Pp);
-  } else {
-    int keep2 = 1;
-    while (keep2 < n_keep) keep2 <<= 1;
-    fill(0, SEL_CAP, 0);
-    __syncthreads();
-    bitonic_sort(key, pos, SEL_CAP);
-    for (int64_t base = SEL_CAP; base < P; base += SEL_CAP - keep2) {
-      fill(keep2, SEL_CAP, base);   // the best keep2 so far stay in [0, keep2)
-      __syncthreads();
-      bitonic_sort(key, pos, SEL_CAP);
+    if (ties && warp == 0) {
+      // the lowest positions among the keys equal to pv, in position order
+      int fill = s_fill;
+      for (int64_t base = 0; base < P && fill < n_keep; base += 32) {
+        const int64_t i = base + lane;
+        const bool eq = i < P && (stored ? it.keys[i] : key_of(i)) == pv;
+        const unsigned bal = __ballot_sync(0xffffffffu, eq);
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        if (eq && fill + rank < n_keep) {
+          key[fill + rank] = pv;
+          pos[fill + rank] = (uint32_t)i;
+        }
+        fill = min((int)n_keep, fill + __popc(bal));
+      }
+      if (lane == 0) s_fill = fill;
     }
-  }
-  for (int64_t i = threadIdx.x; i < n_keep; i += blockDim.x) it.rows_out[i] = it.pool[pos[i]];
-}
-
-// ----------------------------------------------------------------------------
-// far-field lists of many nodes at once (ascending candidate order), with the
-// same FP64 distance test as the uniform sampler
-
-constexpr int FL_TILE = 256;
-
-template <typename TP>
-__device__ __forceinline__ bool far_member(const TP* __restrict__ Y, int d, int64_t j, const FarItem& it,
-                                           double thr2) {
-  if (j >= it.M || (j >= it.ex_begin && j < it.ex_end)) return false;
-  const TP* y = Y + j * (int64_t)d;
-  double acc = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double df = ld_point(y + k) - __ldg(it.x_c + k);
-    acc = fma(df, df, acc);
-  }
-  return acc >= thr2;
-}
-
-__device__ __forceinline__ double far_thr2(const FarItem& it) {
-  const double thr = it.xi * (it.radius ? *it.radius : it.radius_host);
-  return thr * thr;
-}
-
-// blockIdx.y = item, blockIdx.x = tile of FL_TILE candidates
-template <typename TP>
-__global__ void __launch_bounds__(FL_TILE) far_count_kernel(const TP* __restrict__ Y, int d, const FarItem* items,
-                                                            int64_t tiles, int64_t* tile_cnt) {
-  __shared__ int wc[FL_TILE / 32];
-  const FarItem& it = items[blockIdx.y];
-  const int64_t j = (int64_t)blockIdx.x * FL_TILE + threadIdx.x;
-  const bool f = far_member(Y, d, j, it, far_thr2(it));
-  const unsigned b = __ballot_sync(0xffffffffu, f);
-  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(b);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < FL_TILE / 32; ++w) t += wc[w];
-    tile_cnt[(int64_t)blockIdx.y * tiles + blockIdx.x] = t;
-  }
-}
-
-// one CTA per item: exclusive scan of its tile counts, total to *count
-__global__ void far_scan_kernel(const FarItem* items, int64_t tiles, int64_t* tile_cnt) {
-  __shared__ int64_t part[1024];
-  __shared__ int64_t carry;
-  int64_t* tc = tile_cnt + (int64_t)blockIdx.x * tiles;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < tiles; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const int64_t v = i < tiles ? tc[i] : 0;
-    part[threadIdx.x] = v;
     __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-      const int64_t add = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (i < tiles) tc[i] = carry + part[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
-    __syncthreads();
+    m = s_fill;
   }
-  if (threadIdx.x == 0) *items[blockIdx.x].count = carry;
-}
-
-template <typename TP>
-__global__ void __launch_bounds__(FL_TILE) far_scatter_kernel(const TP* __restrict__ Y, int d, const FarItem* items,
-                                                              int64_t tiles, const int64_t* tile_off) {
-  __shared__ int wc[FL_TILE / 32];
-  const FarItem& it = items[blockIdx.y];
-  const int64_t j = (int64_t)blockIdx.x * FL_TILE + threadIdx.x;
-  const bool f = far_member(Y, d, j, it, far_thr2(it));
-  const unsigned b = __ballot_sync(0xffffffffu, f);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) wc[w] = __popc(b);
+  int Pp = 1;
+  while (Pp < m) Pp <<= 1;
+  for (int e = m + tid; e < Pp; e += blockDim.x) {
+    key[e] = ~0ull;
+    pos[e] = 0xFFFFFFFFu;
+  }
   __syncthreads();
-  int off = 0;
-  for (int q = 0; q < w; ++q) off += wc[q];
-  if (f) it.list[tile_off[(int64_t)blockIdx.y * tiles + blockIdx.x] + off + __popc(b & ((1u << lane) - 1u))] = j;
+  bitonic_sort(key, pos, Pp);
+  for (int64_t i = tid; i < n_keep; i += blockDim.x) it.rows_out[i] = it.pool[pos[i]];
 }
 
 // ----------------------------------------------------------------------------
@@ -872,33 +853,12 @@ ffc_status launch_select(const SelectItem* items_dev, int n_items, int64_t keep_
     set_error("weighted draw of %lld rows exceeds %d", (long long)keep_max, SEL_MAX_KEEP);
     return FFC_E_INVALID;
   }
-  const size_t smem = (size_t)SEL_CAP * (sizeof(uint64_t) + sizeof(uint32_t));
+  const size_t smem = select_smem_bytes();
   FFC_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   select_kernel<<<n_items, SEL_THREADS, smem, st>>>(items_dev, seed);
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
 }
-
-ffc_status launch_far_lists(const void* Y, int dtype, int d, const FarItem* items_dev, int n_items, int64_t M_max,
-                            int64_t* tile_cnt, cudaStream_t st) {
-  if (n_items <= 0 || M_max <= 0) return FFC_OK;
-  const int64_t tiles = (M_max + FL_TILE - 1) / FL_TILE;
-  FFC_REQUIRE(n_items <= 65535, "far lists: at most 65535 items per launch");
-  const dim3 grid((unsigned)tiles, (unsigned)n_items);
-  if (dtype == FFC_F64) {
-    far_count_kernel<double><<<grid, FL_TILE, 0, st>>>((const double*)Y, d, items_dev, tiles, tile_cnt);
-    far_scan_kernel<<<n_items, 1024, 0, st>>>(items_dev, tiles, tile_cnt);
-    far_scatter_kernel<double><<<grid, FL_TILE, 0, st>>>((const double*)Y, d, items_dev, tiles, tile_cnt);
-  } else {
-    far_count_kernel<float><<<grid, FL_TILE, 0, st>>>((const float*)Y, d, items_dev, tiles, tile_cnt);
-    far_scan_kernel<<<n_items, 1024, 0, st>>>(items_dev, tiles, tile_cnt);
-    far_scatter_kernel<float><<<grid, FL_TILE, 0, st>>>((const float*)Y, d, items_dev, tiles, tile_cnt);
-  }
-  FFC_CUDA(cudaGetLastError());
-  return FFC_OK;
-}
-
-int64_t far_list_tiles(int64_t M) { return (M + FL_TILE - 1) / FL_TILE; }
 
 ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const double* targets,
                                 const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,

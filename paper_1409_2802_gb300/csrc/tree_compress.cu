@@ -55,6 +55,9 @@ struct ffc_tree_result {
   int64_t *lcount = nullptr, *lfar = nullptr;
   char* pws = nullptr;
   size_t pws_bytes = 0;
+  // per-point sums of the tiled far-field kernels (N x 9 floats, grow-only)
+  char* pst = nullptr;
+  size_t pst_bytes = 0;
   // tracing
   ffc_tree_profile prof{};
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -234,6 +237,15 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     FFC_CUDA(cudaMalloc((void**)&R->lcount, sizeof(int64_t) * 2 * n_out));
     R->lfar = R->lcount + n_out;
   }
+  float *pyy = nullptr, *pyg = nullptr;
+  if (whole) {
+    ffc_status rc = grow(&R->pst, &R->pst_bytes, (size_t)R->N * 9 * sizeof(float), st);
+    if (rc != FFC_OK) return rc;
+    pyy = (float*)R->pst;
+    pyg = pyy + R->N;
+    rc = launch_point_stats(X, R->dtype, R->N, d, P.proj_dev, pyy, pyg, st);
+    if (rc != FFC_OK) return rc;
+  }
   int64_t o0 = 0;
   while (o0 < n_out) {
     // group [o0, o1)
@@ -251,13 +263,16 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
       base[i] = tot;
       tot += cap[i];
     }
-    const int64_t tiles = far_list_tiles(R->N);
+    const int64_t tiles = far_tiles_count(R->N);
     Layout L;
     const size_t o_far = L.add<FarItem>(g), o_smp = L.add<SampleItem>(g), o_fi = L.add<FeatItem>(g),
                  o_si = L.add<SelectItem>(g), o_pool = L.add<int64_t>(tot),
                  o_feat = L.add<float>((size_t)tot * FFC_N_FEATURES), o_lg = L.add<float>(tot),
+                 o_key = L.add<uint64_t>(tot),
                  o_cnt = L.add<int64_t>(g), o_fc = L.add<int64_t>(g), o_st = L.add<int32_t>(g),
                  o_tc = L.add<int64_t>(whole ? (size_t)g * tiles : 0),
+                 o_mask = L.add<uint32_t>(whole ? (size_t)g * tiles * 4 : 0),
+                 o_nst = L.add<char>(whole ? far_tiles_node_bytes(g, d) : 0),
                  o_scr = L.add<int32_t>(whole ? 0 : (size_t)std::min(g, 2048) * R->N);
     ffc_status rc = grow(&R->pws, &R->pws_bytes, L.off, st);
     if (rc != FFC_OK) return rc;
@@ -269,10 +284,13 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     int64_t* pool = (int64_t*)(b + o_pool);
     float* feats = (float*)(b + o_feat);
     float* logits = (float*)(b + o_lg);
+    uint64_t* skeys = (uint64_t*)(b + o_key);
     int64_t* cnt = (int64_t*)(b + o_cnt);
     int64_t* fc = (int64_t*)(b + o_fc);
     int32_t* sst = (int32_t*)(b + o_st);
     int64_t* tcnt = (int64_t*)(b + o_tc);
+    uint32_t* fmask = (uint32_t*)(b + o_mask);
+    void* nst = (void*)(b + o_nst);
     int32_t* scratch = (int32_t*)(b + o_scr);
     std::vector<FarItem> hfar(whole ? g : 0);
     std::vector<SampleItem> hsmp(whole ? 0 : g);
@@ -297,28 +315,31 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
       SelectItem& se = hsi[i];
       se.pool = pool + base[i]; se.count = cnt + i; se.P = cap[i]; se.logits = logits + base[i]; se.s = P.s_max;
       se.stream_id = (uint64_t)node; se.rows_out = R->rows + R->rows_off_h[o]; se.s_out = R->lcount + o;
+      se.keys = skeys + base[i];
     }
     if (whole) FFC_CUDA(cudaMemcpyAsync(d_far, hfar.data(), sizeof(FarItem) * g, cudaMemcpyHostToDevice, st));
     else FFC_CUDA(cudaMemcpyAsync(d_smp, hsmp.data(), sizeof(SampleItem) * g, cudaMemcpyHostToDevice, st));
     FFC_CUDA(cudaMemcpyAsync(d_fi, hfi.data(), sizeof(FeatItem) * g, cudaMemcpyHostToDevice, st));
     FFC_CUDA(cudaMemcpyAsync(d_si, hsi.data(), sizeof(SelectItem) * g, cudaMemcpyHostToDevice, st));
     if (whole) {
-      rc = launch_far_lists(X, R->dtype, d, d_far, g, R->N, tcnt, st);
+      // far-field lists and features together, tiled over (points x nodes)
+      rc = launch_far_features_tiled(P.kernel, X, R->dtype, R->N, d, d_far, d_fi, g, P.proj_dev, pyy, pyg, nst,
+                                     tcnt, fmask, feats, st);
       if (rc == FFC_OK) {
         copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, cnt, fc);
         FFC_CUDA(cudaGetLastError());
       }
     } else {
       rc = launch_sample(X, R->dtype, d, d_smp, g, R->N, P.pool_rows, P.seed, cnt, fc, sst, scratch, st);
+      const int64_t cap_max = *std::max_element(cap.begin(), cap.end());
+      if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, cap_max, P.proj_dev, feats, st);
     }
-    const int64_t cap_max = *std::max_element(cap.begin(), cap.end());
-    if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, cap_max, P.proj_dev, feats, st);
     if (rc == FFC_OK) rc = launch_mlp_forward(P.mlp_dev, feats, tot, logits, st);
     if (rc == FFC_OK) rc = launch_select(d_si, g, P.s_max, P.seed, st);
     if (rc != FFC_OK) return rc;
     copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, fc, R->lfar + o0);
     FFC_CUDA(cudaGetLastError());
-    if (R->prof.enabled) R->prof.launches += (whole ? 4 : 1) + 4;
+    if (R->prof.enabled) R->prof.launches += (whole ? 6 : 2) + 3;
     o0 = o1;
   }
   return FFC_OK;
@@ -705,6 +726,7 @@ void ffc_tree_result_free(ffc_tree_result* R) {
   if (R->out_mem) cudaFree(R->out_mem);
   if (R->ws) cudaFree(R->ws);
   if (R->pws) cudaFree(R->pws);
+  if (R->pst) cudaFree(R->pst);
   if (R->lcount) cudaFree(R->lcount);
   for (auto& e : R->ev)
     if (e) cudaEventDestroy(e);
