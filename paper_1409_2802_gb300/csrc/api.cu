@@ -34,8 +34,6 @@ int sm_count() {
 }
 
 // defined in the kernel translation units
-int64_t eval_tiles(int64_t s, int64_t n);
-int64_t eval_row_tiles(int64_t s);
 int64_t id_error_blocks(int64_t m, int64_t n, int64_t r);
 int cpqr_rows_per_lane(int s_max);
 size_t sample_smem_bytes(int64_t M_max, int d);
@@ -184,10 +182,11 @@ ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype, c
   EvalItem h;
   h.rows = rows_dev; h.s = s; h.x_begin = 0; h.n = n; h.K = K_dev; h.ldk = ldk; h.center = center_dev;
   h.tile_begin = 0;
-  h.row_tiles = eval_row_tiles(s);
+  const int shape = eval_shape(kernel, d, precision);
+  h.row_tiles = eval_row_tiles(s, shape);
   FFC_CUDA(cudaMemcpyAsync(item, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  ffc_status rc = launch_eval(kernel, Y_dev, dtype, X_dev, d, precision, item, 1, eval_tiles(s, n), mind2, lsc,
+  ffc_status rc = launch_eval(kernel, Y_dev, dtype, X_dev, d, precision, item, 1, eval_tiles(s, n, shape), mind2, lsc,
                               status, st);
   if (rc != FFC_OK) return rc;
   double hl = 0.0;

@@ -174,12 +174,26 @@ ffc_status launch_eval_t(ffc_kernel k, const TP* Y, const TP* X, int d, const Ev
 
 }  // namespace
 
-int64_t eval_tiles(int64_t s, int64_t n) { return ((s + TI - 1) / TI) * ((n + TJ - 1) / TJ); }
-int64_t eval_row_tiles(int64_t s) { return (s + TI - 1) / TI; }
+// Mixed precision, Gaussian or polynomial, d >= 64: the tensor-core path (its
+// 128 x 128 tiles); otherwise the SIMT path (64 x 32 tiles). At small d the
+// block is bound by its stores and the SIMT path's direct FP32 differences are
+// the more accurate form.
+constexpr int TC_MIN_D = 64;
+
+int eval_shape(ffc_kernel k, int d, int precision) {
+  return (precision == FFC_MIXED && (k.kind == FFC_GAUSSIAN || k.kind == FFC_POLYNOMIAL) && d >= TC_MIN_D) ? 1 : 0;
+}
+
+int64_t eval_tiles(int64_t s, int64_t n, int shape) {
+  return shape ? eval_tc_tiles(s, n) : ((s + TI - 1) / TI) * ((n + TJ - 1) / TJ);
+}
+int64_t eval_row_tiles(int64_t s, int shape) { return shape ? eval_tc_row_tiles(s) : (s + TI - 1) / TI; }
 
 ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
                        const EvalItem* items_dev, int n_items, int64_t total_tiles, double* min_d2,
                        double* log_scale, int32_t* status, cudaStream_t st) {
+  if (eval_shape(k, d, precision))
+    return launch_eval_tc(k, Y, dtype, X, d, items_dev, n_items, total_tiles, log_scale, st);
   if (precision == FFC_MIXED) {
     if (dtype == FFC_F64)
       return launch_eval_t<double, float, float>(k, (const double*)Y, (const double*)X, d, items_dev, n_items,

@@ -226,6 +226,15 @@ ffc_status launch_far_field(const void* Y, int dtype, int64_t M, int d, const do
 ffc_status launch_sample(const void* Y, int dtype, int d, const SampleItem* items_dev, int n_items,
                          int64_t M_max, int64_t s_max, uint64_t seed, int64_t* s_out, int64_t* far_count,
                          int32_t* status, int32_t* scratch, cudaStream_t st);
+// Tile decomposition of the evaluation: shape = eval_shape(k, d, precision); items' tile_begin and
+// row_tiles must come from eval_tiles / eval_row_tiles of that shape.
+int eval_shape(ffc_kernel k, int d, int precision);
+int64_t eval_tiles(int64_t s, int64_t n, int shape);
+int64_t eval_row_tiles(int64_t s, int shape);
+int64_t eval_tc_tiles(int64_t s, int64_t n);
+int64_t eval_tc_row_tiles(int64_t s);
+ffc_status launch_eval_tc(ffc_kernel k, const void* Y, int dtype, const void* X, int d, const EvalItem* items_dev,
+                          int n_items, int64_t total_tiles, double* log_scale, cudaStream_t st);
 ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
                        const EvalItem* items_dev, int n_items, int64_t total_tiles,
                        double* min_d2 /* n_items, Laplace */, double* log_scale /* n_items */,

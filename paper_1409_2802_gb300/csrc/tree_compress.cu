@@ -21,8 +21,6 @@
 #include "ffc_internal.cuh"
 
 namespace ffc {
-int64_t eval_tiles(int64_t s, int64_t n);
-int64_t eval_row_tiles(int64_t s);
 int cpqr_rows_per_lane(int s_max);
 size_t sample_smem_bytes(int64_t M_max, int d);
 }  // namespace ffc
@@ -374,7 +372,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const int64_t rc = std::min<int64_t>(n, rcap_round);
     RC += rc * rc;
     tiles[q] = tiles_tot;
-    tiles_tot += eval_tiles(s_nom, n);
+    tiles_tot += eval_tiles(s_nom, n, eval_shape(P.kernel, d, P.precision));
     n_max = std::max(n_max, n);
   }
   const int cap = cpqr_max_ctas(P.precision, (int)s_nom);
@@ -520,7 +518,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     EvalItem& ei = he[q];
     ei.rows = R->rows + R->rows_off_h[o]; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
     ei.center = P.precision == FFC_MIXED ? tree->centroid_dev + node * d : nullptr;
-    ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom);
+    ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom, eval_shape(P.kernel, d, P.precision));
     CpqrItem& qi = hq[q];
     qi = CpqrItem{};
     qi.A = (void*)((char*)K + esz * koff[q]); qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;

@@ -46,6 +46,39 @@ def test_mixed_eval_block_fp32_resolution(kind, d, h):
     assert np.max(np.abs(Kg - Ko)) <= 2e-6 * np.max(np.abs(Ko))
 
 
+@pytest.mark.parametrize("kind,d,pts", [(o_kernels.GAUSSIAN, 64, "f64"), (o_kernels.GAUSSIAN, 128, "f64"),
+                                        (o_kernels.GAUSSIAN, 1000, "f32"), (o_kernels.POLYNOMIAL, 128, "f64"),
+                                        (o_kernels.POLYNOMIAL, 1000, "f32")])
+def test_tensor_core_eval_matches_oracle(kind, d, pts):
+    """d >= 64, mixed precision: the block comes from the split-BF16 tensor-core product. Ragged
+    tiles (s = 300, n = 777); entries within the FP32 rounding bound of D2 (Gaussian) or of the
+    inner product (polynomial), and the pairs whose D2 cancels are recomputed directly."""
+    g = np.random.default_rng(d + (7 if kind == o_kernels.POLYNOMIAL else 0))
+    X = g.standard_normal((777, d)) * (1.0 / np.sqrt(d))
+    Y = g.standard_normal((900, d)) * (1.0 / np.sqrt(d)) + 0.4 / np.sqrt(d)
+    Y[:40] = X[:40] + 1e-3 * g.standard_normal((40, d)) / np.sqrt(d)      # near-coincident pairs
+    if pts == "f32":
+        X, Y = X.astype(np.float32), Y.astype(np.float32)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    rows = np.concatenate([np.arange(40), g.choice(np.arange(40, 900), 260, replace=False)]).astype(np.int64)
+    h = 0.8 if kind == o_kernels.GAUSSIAN else 1.0 / d
+    ko = o_kernels.Kernel(kind, h=h)
+    Ko, _ = o_kernels.kernel_block(ko, Y64[rows], X64)
+    centre = X64.mean(axis=0)
+    Kg, _ = ffc.ffc_eval_block(ffc.Kernel(kind, h=h), cu(Y), cu(rows), cu(X), precision=ffc.MIXED, center=cu(centre))
+    Kg = Kg.double().cpu().numpy()
+    u = 2.0 ** -24
+    if kind == o_kernels.GAUSSIAN:
+        yn = np.sum((Y64[rows] - centre) ** 2, axis=1)
+        xn = np.sum((X64 - centre) ** 2, axis=1)
+        bound = Ko * ((d + 16) * 4 * u * (yn[:, None] + xn[None, :]) / (2 * h * h) + 4 * u) + 1e-30
+    else:
+        dots = np.abs(Y64[rows]) @ np.abs(X64).T
+        base = Y64[rows] @ X64.T / h + 1.0
+        bound = 3 * np.abs(base) ** 2 * ((d + 16) * 4 * u * dots / h + 4 * u * np.abs(base)) + 1e-30
+    assert np.all(np.abs(Kg - Ko) <= bound), float(np.max(np.abs(Kg - Ko) / bound))
+
+
 def test_mixed_id_single_block_error_within_1e6_of_oracle():
     X, Y = workloads.single_block(0)
     ok = o_kernels.Kernel(o_kernels.GAUSSIAN, h=1.0)
