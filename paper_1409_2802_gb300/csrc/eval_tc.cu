@@ -28,12 +28,16 @@ namespace {
 
 constexpr int TC_M = 128, TC_N = 128, TC_K = 32, TC_LD = TC_K + 8, TC_THREADS = 256;
 
+constexpr int TC_MAX_D = 4096;   // the FP32 centre of a block is staged whole
+
 struct EvalTcSmem {
   alignas(16) __nv_bfloat16 A[3][TC_M * TC_LD];   // targets [i][k], planes hi / mid / lo
   alignas(16) __nv_bfloat16 B[3][TC_N * TC_LD];   // sources [j][k]
   float yn[TC_M];
   float xn[TC_N];
   int64_t yrow[TC_M];
+  alignas(16) float c32[TC_MAX_D];   // the centre rounded to FP32 (FP32 points)
+  float nsum[2 * TC_M][8];             // per row, the partial squared norms of its 8 staging threads
 };
 
 __device__ __forceinline__ void ldsm4(const void* p, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
@@ -58,44 +62,58 @@ __device__ __forceinline__ int find_item_tc(const EvalItem* items, int n_items, 
   return lo;
 }
 
-// one row (target or source) of a stage: coordinates [c0, c0 + TC_K), centred, FP32, split in three;
-// eight coordinates are packed per 16-byte shared-memory store
+// Split of one FP32 coordinate into three BF16 parts (each the rounding of the remainder).
+__device__ __forceinline__ void split3(float a, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(a);
+  const float r1 = a - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Four coordinates [k, k + 4) of one row, centred: FP32 points against the FP32 centre (its
+// rounding is common to targets and sources and cancels in their differences), FP64 points in
+// FP64 before rounding; zero beyond d.
 template <typename TP>
-__device__ __forceinline__ void stage_row(const TP* __restrict__ row, const double* __restrict__ ctr, int c0, int kc,
-                                          bool valid, __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo,
-                                          float& nrm) {
+__device__ __forceinline__ void load4(const TP* __restrict__ row, int k, int d, bool vec, const double* ctr,
+                                     const float* c32, float (&a)[4]);
+
+template <>
+__device__ __forceinline__ void load4<float>(const float* __restrict__ row, int k, int d, bool vec, const double* ctr,
+                                            const float* c32, float (&a)[4]) {
+  if (vec && k + 3 < d) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
+    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+  } else {
 #pragma unroll
-  for (int k8 = 0; k8 < TC_K; k8 += 8) {
-    __align__(16) __nv_bfloat16 ph[8], pm[8], pl[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int k = k8 + u;
-      float a = 0.0f;
-      if (valid && k < kc) {
-        double v = (double)__ldg(row + c0 + k);
-        if (ctr) v -= ctr[c0 + k];
-        a = (float)v;
-      }
-      nrm = fmaf(a, a, nrm);
-      const __nv_bfloat16 h = __float2bfloat16_rn(a);
-      const float r1 = a - __bfloat162float(h);
-      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-      const float r2 = r1 - __bfloat162float(m);
-      ph[u] = h;
-      pm[u] = m;
-      pl[u] = __float2bfloat16_rn(r2);
-    }
-    *reinterpret_cast<uint4*>(hi + k8) = *reinterpret_cast<const uint4*>(ph);
-    *reinterpret_cast<uint4*>(mid + k8) = *reinterpret_cast<const uint4*>(pm);
-    *reinterpret_cast<uint4*>(lo + k8) = *reinterpret_cast<const uint4*>(pl);
+    for (int e = 0; e < 4; ++e) a[e] = k + e < d ? __ldg(row + k + e) : 0.0f;
   }
+  if (ctr) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) a[e] = k + e < d ? a[e] - c32[k + e] : 0.0f;
+  }
+}
+
+template <>
+__device__ __forceinline__ void load4<double>(const double* __restrict__ row, int k, int d, bool vec,
+                                             const double* ctr, const float* c32, float (&a)[4]) {
+  double v[4];
+  if (vec && k + 3 < d) {
+    const double2 v01 = __ldg(reinterpret_cast<const double2*>(row + k));
+    const double2 v23 = __ldg(reinterpret_cast<const double2*>(row + k + 2));
+    v[0] = v01.x; v[1] = v01.y; v[2] = v23.x; v[3] = v23.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = k + e < d ? __ldg(row + k + e) : 0.0;
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) a[e] = k + e < d ? (float)(ctr ? v[e] - ctr[k + e] : v[e]) : 0.0f;
 }
 
 // MODE 0: Gaussian (centred distances), 2: polynomial (inner products)
 template <typename TP, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 eval_tc_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kernel kp,
-               const EvalItem* __restrict__ items, int n_items, int64_t total_tiles) {
+               const EvalItem* __restrict__ items, int n_items, int64_t total_tiles, bool vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EvalTcSmem& S = *reinterpret_cast<EvalTcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -111,25 +129,46 @@ eval_tc_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_ke
     const int64_t i0 = (local % rt) * TC_M, j0 = (local / rt) * TC_N;
     if (i0 >= s || j0 >= n) continue;   // uniform across the CTA
     const double* ctr = MODE == 0 ? it.center : nullptr;
-    const bool is_a = tid < TC_M;
-    const int rr = tid & (TC_M - 1);
-    const bool valid = is_a ? (i0 + rr < s) : (j0 + rr < n);
-    __syncthreads();   // the previous tile's epilogue reads S.yn / S.xn / S.yrow
-    if (is_a) S.yrow[rr] = valid ? it.rows[i0 + rr] : 0;
-    const TP* row = is_a ? (Y + (valid ? it.rows[i0 + rr] : 0) * (int64_t)d)
-                         : (X + (it.x_begin + (valid ? j0 + rr : 0)) * (int64_t)d);
-    float nrm = 0.0f;
+    __syncthreads();   // the previous tile's epilogue reads S.yn / S.xn / S.yrow / S.c32
+    for (int r = tid; r < TC_M; r += TC_THREADS) S.yrow[r] = i0 + r < s ? it.rows[i0 + r] : 0;
+    if (ctr && sizeof(TP) == 4)
+      for (int k = tid; k < d; k += TC_THREADS) S.c32[k] = (float)ctr[k];
+    __syncthreads();
+    // staging: rows 0..127 targets, 128..255 sources (rb + 32 it); 8 threads per row, 4 coordinates each
+    const int kq = tid & 7, rb = tid >> 3;
+#pragma unroll
+    for (int it2 = 0; it2 < 8; ++it2) S.nsum[rb + 32 * it2][kq] = 0.0f;
     float acc[4][4][4];
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
     for (int c0 = 0; c0 < d; c0 += TC_K) {
-      const int kc = min(TC_K, d - c0);
-      if (is_a)
-        stage_row(row, ctr, c0, kc, valid, &S.A[0][rr * TC_LD], &S.A[1][rr * TC_LD], &S.A[2][rr * TC_LD], nrm);
-      else
-        stage_row(row, ctr, c0, kc, valid, &S.B[0][rr * TC_LD], &S.B[1][rr * TC_LD], &S.B[2][rr * TC_LD], nrm);
+#pragma unroll
+      for (int it2 = 0; it2 < 8; ++it2) {
+        const int r = rb + 32 * it2;
+        const bool is_a = r < TC_M;
+        const int rr = r & (TC_M - 1);
+        const bool valid = is_a ? (i0 + rr < s) : (j0 + rr < n);
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) {
+          const TP* row = is_a ? Y + S.yrow[rr] * (int64_t)d : X + (it.x_begin + j0 + rr) * (int64_t)d;
+          load4<TP>(row, c0 + 4 * kq, d, vec, ctr, S.c32, a);
+        }
+        __align__(8) __nv_bfloat16 ph[4], pm[4], pl[4];
+        float nr = S.nsum[r][kq];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          nr = fmaf(a[e], a[e], nr);
+          split3(a[e], ph[e], pm[e], pl[e]);
+        }
+        S.nsum[r][kq] = nr;
+        __nv_bfloat16* base = is_a ? &S.A[0][rr * TC_LD + 4 * kq] : &S.B[0][rr * TC_LD + 4 * kq];
+        constexpr int plane = TC_M * TC_LD;
+        *reinterpret_cast<uint2*>(base) = *reinterpret_cast<const uint2*>(ph);
+        *reinterpret_cast<uint2*>(base + plane) = *reinterpret_cast<const uint2*>(pm);
+        *reinterpret_cast<uint2*>(base + 2 * plane) = *reinterpret_cast<const uint2*>(pl);
+      }
       __syncthreads();
 #pragma unroll
       for (int ks = 0; ks < TC_K / 16; ++ks) {
@@ -162,7 +201,13 @@ eval_tc_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_ke
       }
       __syncthreads();
     }
-    if (is_a) S.yn[rr] = nrm; else S.xn[rr] = nrm;
+    // row norms: the partial sums of a row's 8 staging threads, in a fixed order
+    for (int r = tid; r < 2 * TC_M; r += TC_THREADS) {
+      float v = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v += S.nsum[r][e];
+      if (r < TC_M) S.yn[r] = v; else S.xn[r - TC_M] = v;
+    }
     __syncthreads();
     float* K = reinterpret_cast<float*>(it.K);
 #pragma unroll
@@ -186,9 +231,18 @@ eval_tc_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_ke
               const TP* xr = X + (it.x_begin + j) * (int64_t)d;
               float a2 = 0.0f;
               for (int k = 0; k < d; ++k) {
-                double yv = (double)__ldg(yr + k), xv = (double)__ldg(xr + k);
-                if (ctr) { yv -= ctr[k]; xv -= ctr[k]; }
-                const float df = (float)yv - (float)xv;
+                float yv, xv;
+                if (sizeof(TP) == 4) {
+                  yv = (float)__ldg(yr + k);
+                  xv = (float)__ldg(xr + k);
+                  if (ctr) { yv -= S.c32[k]; xv -= S.c32[k]; }
+                } else {
+                  double y64 = (double)__ldg(yr + k), x64 = (double)__ldg(xr + k);
+                  if (ctr) { y64 -= ctr[k]; x64 -= ctr[k]; }
+                  yv = (float)y64;
+                  xv = (float)x64;
+                }
+                const float df = yv - xv;
                 a2 = fmaf(df, df, a2);
               }
               d2 = a2;
@@ -216,14 +270,18 @@ ffc_status launch_eval_tc(ffc_kernel k, const void* Y, int dtype, const void* X,
                           int n_items, int64_t total_tiles, double* log_scale, cudaStream_t st) {
   if (total_tiles <= 0) return FFC_OK;
   FFC_REQUIRE(k.kind == FFC_GAUSSIAN || k.kind == FFC_POLYNOMIAL, "tensor-core evaluation: Gaussian or polynomial");
+  FFC_REQUIRE(d <= TC_MAX_D, "tensor-core evaluation: d = %d above %d", d, TC_MAX_D);
   const int grid = (int)std::min<int64_t>(total_tiles, (int64_t)sm_count() * 2);
   const size_t smem = sizeof(EvalTcSmem);
+  const size_t esz = dtype == FFC_F64 ? 8 : 4;
+  const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(X)) % 16 == 0) &&
+                   ((size_t)d * esz) % 16 == 0;
 #define FFC_TC_LAUNCH(TP, MODE)                                                                               \
   do {                                                                                                        \
     FFC_CUDA(cudaFuncSetAttribute(eval_tc_kernel<TP, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                   (int)smem));                                                                \
     eval_tc_kernel<TP, MODE><<<grid, TC_THREADS, smem, st>>>((const TP*)Y, (const TP*)X, d, k, items_dev,     \
-                                                             n_items, total_tiles);                           \
+                                                             n_items, total_tiles, vec);                      \
   } while (0)
   if (dtype == FFC_F64) {
     if (k.kind == FFC_GAUSSIAN) FFC_TC_LAUNCH(double, 0); else FFC_TC_LAUNCH(double, 2);
