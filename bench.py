@@ -407,7 +407,28 @@ FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nomin
 
 
 
-def qr_roofline(prof, steps, precision_name, peaks, peak_src):
+def qr_traffic(precision_name, sampler):
+    """DRAM bytes per step of the QR launches from the committed ncu record, while the kernel source
+    still matches the one the counters were taken on; else None."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_1409_2802_gb300", "csrc", "cpqr.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "cpqr_traffic_*.md")):
+        rec = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("#", "|", "*", " ")):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        if (rec.get("cpqr_sha256") == h and rec.get("workload") == WORKLOAD["workload"]
+                and rec.get("precision") == precision_name and rec.get("sampler") == sampler):
+            return float(rec["traffic_bytes_per_step"]), os.path.relpath(path, ROOT)
+    return None, None
+
+
+def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned"):
     """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing.
 
     Algorithmic bytes: one read and one write of every sampled block K' (s x n)
@@ -427,9 +448,12 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src):
     else:
         alu_peak, kern, src = FP32_PEAK_TFLOPS, "cpqr_kernel<float> (pivoted QR, FP32 updates, FP64 norms)", \
             "nominal FP32 rate of GB300 (152 SMs x 128 lanes x 2.07 GHz)"
+    traffic, traffic_src = qr_traffic(precision_name, sampler)
     return {
         "kernel": kern, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-        "traffic": None, "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+        "traffic": traffic, "traffic_unit": "bytes per step (all QR launches of one call)",
+        "traffic_source": traffic_src,
+        "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
         "streamed_gbs": streamed, "streamed_frac": streamed / hbm,
         "alu": {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak, "source": src},
         "dominant_phase": max(phase_ms, key=phase_ms.get),
@@ -571,7 +595,7 @@ def main():
                    "s": "128 doubling to 2048", "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk, "gpu_launches": int(prof["launches"]),
-        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src),
+        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src, args.sampler),
     }
     if train_info is not None:
         line["config"]["proposal_training"] = train_info
@@ -595,7 +619,7 @@ def main():
             r_, ms_, pf_ = timed(precision_code(ffc, pname), fsteps, 1, proposal if sname == "learned" else None)
             v_ = n_nodes * fsteps * world / (ms_ / 1e3)
             other[key] = {"value": v_, "unit": UNIT, "ms_per_step": ms_ / fsteps, "steps": fsteps,
-                          "roofline": qr_roofline(pf_, fsteps, pname, peaks, peak_src)}
+                          "roofline": qr_roofline(pf_, fsteps, pname, peaks, peak_src, sname)}
             if not args.no_accuracy and rank == 0:
                 errors[key] = arm_errors(torch, ffc, Pp, tree, kern, r_)
             r_.close()
