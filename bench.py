@@ -188,6 +188,22 @@ def build_inputs(torch, dev):
     return P, tree, Pp, workload_kernel(ffc, P)
 
 
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest of the ranks' values (a job's time is its slowest rank's); all ranks get it."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nodes_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job nodes/s: every rank compresses its own replica of the workload (weak scaling)."""
+    return nodes_per_rank * steps * world / (max_ms / 1e3)
+
+
 def precision_code(ffc, name):
     return ffc.FP64 if name == "fp64" else ffc.MIXED
 
@@ -570,11 +586,8 @@ def main():
         res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, kern, prec_code, steps, warmup, flush, stream,
                                          proposal=prop)
         torch.cuda.synchronize()
-        total = sum(times)
+        total = max_over_ranks(sum(times), world, dev)
         if world > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
             torch.distributed.barrier()
         return res, total, prof
 
@@ -583,7 +596,7 @@ def main():
     res, total_ms, prof = timed(prec, args.steps, args.warmup, proposal)
     clk = clocks.stop()
     n_nodes = int(ffc.tree_result_views(res)["n_out"])
-    value = n_nodes * args.steps * world / (total_ms / 1e3)
+    value = job_throughput(n_nodes, args.steps, world, total_ms)
     arm = f"{args.precision}_{args.sampler}"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -617,7 +630,7 @@ def main():
             if key == arm:
                 continue
             r_, ms_, pf_ = timed(precision_code(ffc, pname), fsteps, 1, proposal if sname == "learned" else None)
-            v_ = n_nodes * fsteps * world / (ms_ / 1e3)
+            v_ = job_throughput(n_nodes, fsteps, world, ms_)
             other[key] = {"value": v_, "unit": UNIT, "ms_per_step": ms_ / fsteps, "steps": fsteps,
                           "roofline": qr_roofline(pf_, fsteps, pname, peaks, peak_src, sname)}
             if not args.no_accuracy and rank == 0:
