@@ -36,12 +36,36 @@ __device__ __forceinline__ void atomic_min_pos(double* addr, double v) {
 // OT: type of the stored block. With CT = float and a centre given, the
 // coordinates are centred at it in FP64 before rounding to FP32, so the
 // differences keep the precision of the node's scale rather than of |x|.
+// Squared distance in FP64 from the stored coordinates (the FP64 path's formula).
+template <typename TP>
+__device__ __forceinline__ double dist2_fp64(const TP* __restrict__ y, const TP* __restrict__ x, int d) {
+  double a = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double df = ld_point(y + k) - ld_point(x + k);
+    a = fma(df, df, a);
+  }
+  return a;
+}
+
+// Mixed-precision Laplace (CT = float, MODE 3 and 1): FP32 centred distances, with
+//  * an FP64 recompute where the FP32 distance cancels, D2 < (|y~|^2 + |x~|^2) / 16
+//    (the centred norms come with the tile);
+//  * in the map, an FP64 recompute of every entry the FP32 distance puts at or above
+//    LAP_RECOMPUTE of the block's largest: the map multiplies the distance's relative
+//    error by (d - 2) / 2, so only entries that small keep the FP32 distance.
+// The block is scaled by the minimum of these distances (the FP32 pass's), a constant
+// factor within FP32 rounding of the FP64 path's; J, T and every relative error are
+// invariant to it, and the scale is returned with the block.
+constexpr float LAP_RECOMPUTE = 1e-3f;
+
 template <typename TP, int MODE, typename CT, typename OT>
 __global__ void __launch_bounds__(EVAL_THREADS)
 eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kernel kp,
             const EvalItem* __restrict__ items, int n_items, int64_t total_tiles, double* min_d2) {
   __shared__ CT ys[TI][DC + 1];
   __shared__ CT xs[TJ][DC + 1];
+  constexpr bool lap32 = (MODE == 1 || MODE == 3) && sizeof(CT) == 4;
+  __shared__ float yns[lap32 ? TI : 1], xns[lap32 ? TJ : 1];
   const int tid = threadIdx.x;
   const int r = tid % TI, cg = tid / TI;   // row in tile, column group (0..3)
   constexpr bool centre = (sizeof(CT) == 4) && (MODE != 2);
@@ -57,6 +81,7 @@ eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kerne
     CT acc[TJ / 4];
 #pragma unroll
     for (int u = 0; u < TJ / 4; ++u) acc[u] = (CT)0;
+    float ynr = 0.0f, xnc = 0.0f;   // lap32: row r's and (tid < TJ) column tid's centred squared norms
     for (int k0 = 0; k0 < d; k0 += DC) {
       const int kc = min(DC, d - k0);
       for (int e = tid; e < TI * DC; e += EVAL_THREADS) {
@@ -78,6 +103,16 @@ eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kerne
         xs[cc][kk] = (CT)v;
       }
       __syncthreads();
+      if (lap32) {
+        for (int kk = 0; kk < kc; ++kk) {
+          const float yv = (float)ys[r][kk];
+          ynr = fmaf(yv, yv, ynr);
+          if (tid < TJ) {
+            const float xv = (float)xs[tid][kk];
+            xnc = fmaf(xv, xv, xnc);
+          }
+        }
+      }
       for (int kk = 0; kk < kc; ++kk) {
         const CT y = ys[r][kk];
 #pragma unroll
@@ -94,6 +129,21 @@ eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kerne
       __syncthreads();
     }
     const int64_t i = i0 + r;
+    if (lap32) {
+      if (cg == 0) yns[r] = ynr;
+      if (tid < TJ) xns[tid] = xnc;
+      __syncthreads();
+      if (i < s) {
+#pragma unroll
+        for (int u = 0; u < TJ / 4; ++u) {
+          const int c = cg + 4 * u;
+          const int64_t j = j0 + c;
+          if (j < n && (float)acc[u] < 0.0625f * (yns[r] + xns[c]))
+            acc[u] = (CT)dist2_fp64(Y + it.rows[i] * (int64_t)d, X + (it.x_begin + j) * (int64_t)d, d);
+        }
+      }
+      __syncthreads();   // the next tile restages the norms
+    }
     if (MODE == 3) {
       double mn = INFINITY;
 #pragma unroll
@@ -116,6 +166,15 @@ eval_kernel(const TP* __restrict__ Y, const TP* __restrict__ X, int d, ffc_kerne
         if (MODE == 0) v = (OT)exp(-a / (2.0 * kp.h * kp.h));
         else if (MODE == 1) v = (OT)exp(-(double)(d - 2) * (0.5 * log(a) - ln_rmin));
         else v = (OT)pow(a / kp.h + kp.c, (double)kp.p);
+      } else if (MODE == 1) {
+        const float lr = 0.5f * logf((float)acc[u]) - (float)ln_rmin;
+        const float v32 = expf(-(float)(d - 2) * lr);
+        if (v32 >= LAP_RECOMPUTE) {
+          const double a = dist2_fp64(Y + it.rows[i] * (int64_t)d, X + (it.x_begin + j) * (int64_t)d, d);
+          v = (OT)exp(-(double)(d - 2) * (0.5 * log(a) - ln_rmin));
+        } else {
+          v = (OT)v32;
+        }
       } else {
         const float a = (float)acc[u];
         if (MODE == 0) {
@@ -162,11 +221,12 @@ ffc_status launch_eval_t(ffc_kernel k, const TP* Y, const TP* X, int d, const Ev
     eval_kernel<TP, 2, CT, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
     if (log_scale) FFC_CUDA(cudaMemsetAsync(log_scale, 0, sizeof(double) * n_items, st));
   } else {
-    // Laplace: FP64 distances (the map amplifies their relative error (d-2)/2 times)
+    // Laplace: the map amplifies the distances' relative error (d-2)/2 times. FP64: FP64 distances.
+    // Mixed: FP32 centred distances with FP64 recomputes (cancellation; entries near the largest).
     fill_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(min_d2, n_items, INFINITY);
-    eval_kernel<TP, 3, double, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
+    eval_kernel<TP, 3, CT, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
     laplace_scale_kernel<<<(n_items + 255) / 256, 256, 0, st>>>(min_d2, n_items, d, log_scale, status);
-    eval_kernel<TP, 1, double, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
+    eval_kernel<TP, 1, CT, OT><<<grid, EVAL_THREADS, 0, st>>>(Y, X, d, k, items, n_items, total_tiles, min_d2);
   }
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
