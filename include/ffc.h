@@ -119,6 +119,16 @@ ffc_status ffc_sample_rows(const void* Y_dev, int32_t dtype, int64_t M, int32_t 
  * coordinates. log_scale_host: ln of the factor removed from a Laplace block
  * (0 for the other kernels). Synchronises `stream` (Laplace: to return the
  * scale). Returns FFC_E_SINGULAR for a Laplace block with a zero distance.
+ * FFC_MIXED arithmetic:
+ *   Gaussian, polynomial, d < 64: FP32 direct differences (inner products).
+ *   Gaussian, polynomial, d >= 64: tensor cores, each FP32 coordinate split
+ *     into three BF16 parts, FP32 accumulation; Gaussian D2 recomputed from
+ *     FP32 differences where ||y||^2 + ||x||^2 - 2 y.x cancels.
+ *   Laplace: FP32 distances; FP64 where they cancel and for every entry at or
+ *     above 1e-3 of the largest. The block is scaled by the minimum of those
+ *     distances: the same block as FP64's up to a constant factor within
+ *     FP32 rounding (J, T and relative errors do not depend on it), and
+ *     log_scale_host is that scale.
  */
 ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype,
                           const int64_t* rows_dev, int64_t s,
