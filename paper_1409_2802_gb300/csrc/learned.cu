@@ -626,13 +626,18 @@ __device__ void bitonic_sort(uint64_t* key, uint32_t* pos, int n) {
 
 // Sort key of pool position i: -ln(u_i) / w'_i > 0, whose bit pattern sorts
 // ascending exactly as the key ln(u_i) / w'_i sorts descending.
-__device__ __forceinline__ uint64_t es_sort_key(float logit, double mx, double mean, uint64_t seed,
-                                                uint64_t stream_id, int64_t i) {
-  const double w = exp((double)logit - mx);
+__device__ __forceinline__ uint64_t es_sort_key_w(double w, double mean, uint64_t seed, uint64_t stream_id,
+                                                  int64_t i) {
   const double wp = 0.9 * w / mean + 0.1;
   const uint64_t draw = philox_draw(seed, stream_id, DOMAIN_WEIGHTED_KEYS, (uint64_t)i);
   const double u = ((double)(draw >> 11) + 0.5) * 0x1.0p-53;
   return (uint64_t)__double_as_longlong(-log(u) / wp);
+}
+
+// the same key from the logit (w = exp(logit - max))
+__device__ __forceinline__ uint64_t es_sort_key(float logit, double mx, double mean, uint64_t seed,
+                                                uint64_t stream_id, int64_t i) {
+  return es_sort_key_w(exp((double)logit - mx), mean, seed, stream_id, i);
 }
 
 // One CTA per pool: the min(s, P) pool rows with the largest keys, in key
@@ -671,8 +676,14 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
   __syncthreads();
   mx = redf[0];
   for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, redf[i]);
+  // with a key buffer (large pools), w_i = exp(o_i - max) is kept there for the key pass
+  const bool keep_w = it.keys != nullptr && P > SEL_CAP;
   double sw = 0.0;
-  for (int64_t i = tid; i < P; i += blockDim.x) sw += exp((double)it.logits[i] - (double)mx);
+  for (int64_t i = tid; i < P; i += blockDim.x) {
+    const double w = exp((double)it.logits[i] - (double)mx);
+    if (keep_w) it.keys[i] = (uint64_t)__double_as_longlong(w);
+    sw += w;
+  }
   for (int off = 16; off > 0; off >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, off);
   if (lane == 0) redd[warp] = sw;
   __syncthreads();
@@ -703,7 +714,8 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
       for (int64_t i = tid; i < P; i += blockDim.x) {
         uint64_t k;
         if (level == 0) {
-          k = key_of(i);
+          k = stored ? es_sort_key_w(__longlong_as_double((long long)it.keys[i]), mean, seed, it.stream_id, i)
+                     : key_of(i);
           if (stored) it.keys[i] = k;
         } else {
           k = stored ? it.keys[i] : key_of(i);
