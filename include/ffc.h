@@ -125,7 +125,7 @@ ffc_status ffc_sample_rows(const void* Y_dev, int32_t dtype, int64_t M, int32_t 
  *     into three BF16 parts, FP32 accumulation; Gaussian D2 recomputed from
  *     FP32 differences where ||y||^2 + ||x||^2 - 2 y.x cancels.
  *   Laplace: FP32 distances; FP64 where they cancel and for every entry at or
- *     above 1e-3 of the largest. The block is scaled by the minimum of those
+ *     above 1e-6 of the largest. The block is scaled by the minimum of those
  *     distances: the same block as FP64's up to a constant factor within
  *     FP32 rounding (J, T and relative errors do not depend on it), and
  *     log_scale_host is that scale.

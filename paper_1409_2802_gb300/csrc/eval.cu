@@ -56,7 +56,7 @@ __device__ __forceinline__ double dist2_fp64(const TP* __restrict__ y, const TP*
 // The block is scaled by the minimum of these distances (the FP32 pass's), a constant
 // factor within FP32 rounding of the FP64 path's; J, T and every relative error are
 // invariant to it, and the scale is returned with the block.
-constexpr float LAP_RECOMPUTE = 1e-3f;
+constexpr float LAP_RECOMPUTE = 1e-6f;
 
 template <typename TP, int MODE, typename CT, typename OT>
 __global__ void __launch_bounds__(EVAL_THREADS)
