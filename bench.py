@@ -444,6 +444,31 @@ def qr_traffic(precision_name, sampler):
     return None, None
 
 
+def eval_roofline(prof, steps, precision_name, peaks, peak_src):
+    """The block evaluation as a GEMM: 2 s n d flops per block (the library counts the direct form's
+    3 s n d, or 2 s n d for the polynomial). Mixed precision at d >= 64 (Gaussian, polynomial) runs on
+    the tensor cores with six BF16 partial products per multiply-add; the rest is SIMT."""
+    W = WORKLOAD
+    ms = prof["ms"]["eval"] / max(steps, 1)
+    per_coord = 2.0 if W["kernel"] == "polynomial" else 3.0
+    gemm = prof["eval_flops"] / per_coord * 2.0 / max(steps, 1)
+    tflops = gemm / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    tensor = precision_name == "mixed" and W["kernel"] != "laplace" and W["d"] >= 64
+    if tensor:
+        # timed inside a long step: the sustained figure
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1710.8))
+        return {"kernel": "eval_tc_kernel (split-BF16 mma.sync, FP32 accumulate)", "bound": "tensor",
+                "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                "tensor_work_tflops": 6.0 * tflops, "tensor_work_frac": 6.0 * tflops / peak,
+                "peak_source": f"{peak_src} dense BF16, sustained (MEASURED_PEAKS.json bf16_tflops_sustained, "
+                               "tcgen05 cuBLAS)",
+                "gemm_flops_per_step": gemm, "ms_per_step": ms}
+    peak = FP32_PEAK_TFLOPS if precision_name == "mixed" else FP64_PEAK_TFLOPS
+    return {"kernel": "eval_kernel (SIMT)", "bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": tflops / peak, "gemm_flops_per_step": gemm, "ms_per_step": ms,
+            "peak_source": "nominal FP32 rate of GB300" if precision_name == "mixed" else "nominal FP64 rate of GB300"}
+
+
 def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned"):
     """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing.
 
@@ -477,6 +502,7 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned")
         "qr_ms_per_step_by_round": [round(v / steps, 3) for v in prof.get("qr_ms_round", [])],
         "nodes_per_step_by_round": [int(v // steps) for v in prof.get("items_round", [])],
         "qr_flops_per_step": prof["qr_flops"] / steps, "qr_bytes_per_step": prof["qr_bytes"] / steps,
+        "eval": eval_roofline(prof, steps, precision_name, peaks, peak_src),
     }
 
 
