@@ -645,7 +645,9 @@ __device__ __forceinline__ void update_column_vec_chunked(T* __restrict__ A, int
   }
 }
 
-template <typename T>
+// BIG: the launch has the register budget (2 CTAs per SM) to hold FP32 columns of up to
+// 512 W rows in registers, so the longest columns (s = 2,048) are read once per step
+template <typename T, bool BIG>
 __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
                             double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
                             int16_t* __restrict__ rcl, QrShared& sh) {
@@ -837,6 +839,9 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
       else if (vrows <= 256 * W)
         update_columns_vec<T, 1, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
                                     key, psum, emax);
+      else if (BIG && vrows <= 512 * W)
+        update_columns_vec<T, 1, 16>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s,
+                                     vn2s, key, psum, emax);
       else
         update_column_vec_chunked<T>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
                                      key, psum, emax);
@@ -886,8 +891,8 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
   for (int j = tid; j < ncols; j += QR_THREADS) it.selected[c0 + j] = sels[j];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(QR_THREADS, FFC_QR_MIN_BLOCKS)
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
 cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
             const int32_t* __restrict__ cta_off) {
   // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries
@@ -908,7 +913,7 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
     const CpqrItem it = items[a.item];
     if (threadIdx.x == 0) sh.status = FFC_OK;
     __syncthreads();
-    factor_item<T>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh);
+    factor_item<T, BIG>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh);
     __syncthreads();
   }
 }
@@ -1051,6 +1056,10 @@ trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
   }
 }
 
+// FP32 blocks of more than 256 W rows: the register-resident variant (2 CTAs per SM)
+template <typename T>
+bool qr_big(int s_max) { return sizeof(T) == 4 && s_max > 256 * Vec<T>::W; }
+
 template <typename T>
 size_t cpqr_smem_bytes(int s_max) {
   // the Householder vector is last; 8 spare elements keep the vector loads of
@@ -1067,7 +1076,7 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
     return FFC_E_INVALID;
   }
   const size_t smem = cpqr_smem_bytes<T>(s_max);
-  auto kfn = cpqr_kernel<T>;
+  auto kfn = qr_big<T>(s_max) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
   FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1087,8 +1096,9 @@ template <typename T>
 int max_ctas_t(int s_max) {
   int per_sm = 0;
   const size_t smem = cpqr_smem_bytes<T>(s_max);
-  cudaFuncSetAttribute(cpqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_kernel<T>, QR_THREADS, smem);
+  auto kfn = qr_big<T>(s_max) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, QR_THREADS, smem);
   return per_sm * sm_count();
 }
 
