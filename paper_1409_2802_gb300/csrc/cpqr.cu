@@ -646,7 +646,8 @@ __device__ __forceinline__ void update_column_vec_chunked(T* __restrict__ A, int
 }
 
 // BIG: the launch has the register budget (2 CTAs per SM) to hold FP32 columns of up to
-// 512 W rows in registers, so the longest columns (s = 2,048) are read once per step
+// 512 W rows in registers, so the longest columns (s = 2,048) are read once per step, and
+// to take columns of up to 256 W rows two at a time
 template <typename T, bool BIG>
 __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
                             double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
@@ -835,6 +836,9 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
                                     key, psum, emax);
       else if (vrows <= 128 * W)
         update_columns_vec<T, 2, 4>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
+                                    key, psum, emax);
+      else if (BIG && vrows <= 256 * W)
+        update_columns_vec<T, 2, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
                                     key, psum, emax);
       else if (vrows <= 256 * W)
         update_columns_vec<T, 1, 8>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
@@ -1056,9 +1060,13 @@ trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
   }
 }
 
-// FP32 blocks of more than 256 W rows: the register-resident variant (2 CTAs per SM)
+// FP32 blocks of more than 512 rows: the register-resident variant (2 CTAs per SM); measured
+// faster from s = 1,024 on (at s = 512 the third CTA per SM is worth more)
+#ifndef FFC_QR_BIG_MIN_ROWS
+#define FFC_QR_BIG_MIN_ROWS 512
+#endif
 template <typename T>
-bool qr_big(int s_max) { return sizeof(T) == 4 && s_max > 256 * Vec<T>::W; }
+bool qr_big(int s_max) { return sizeof(T) == 4 && s_max > FFC_QR_BIG_MIN_ROWS; }
 
 template <typename T>
 size_t cpqr_smem_bytes(int s_max) {
