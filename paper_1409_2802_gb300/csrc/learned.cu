@@ -318,11 +318,22 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
       S.X[e] = r < R ? F[row0 * NF + e] : 0.0f;
     }
     __syncthreads();
-    for (int r = r_first; r < TC_ROWS; r += 2) {
-      float z = b1j;
+    // two rows per pass (rows r and r + 2): 16-byte loads of the feature rows and two
+    // independent GELUs in flight; the sums keep the order b1 + w1[0] x[0] + ... + w1[11] x[11]
+    for (int r = r_first; r < TC_ROWS; r += 4) {
+      const float4* xa = reinterpret_cast<const float4*>(&S.X[r * NF]);
+      const float4* xb = reinterpret_cast<const float4*>(&S.X[(r + 2) * NF]);
+      float za = b1j, zb = b1j;
 #pragma unroll
-      for (int kk = 0; kk < NF; ++kk) z = fmaf(w1[kk], S.X[r * NF + kk], z);
-      S.H1[r * HS + j] = __float2half_rn(gelu_f(z));
+      for (int q = 0; q < NF / 4; ++q) {
+        const float4 a = xa[q], b = xb[q];
+        za = fmaf(w1[4 * q], a.x, za); zb = fmaf(w1[4 * q], b.x, zb);
+        za = fmaf(w1[4 * q + 1], a.y, za); zb = fmaf(w1[4 * q + 1], b.y, zb);
+        za = fmaf(w1[4 * q + 2], a.z, za); zb = fmaf(w1[4 * q + 2], b.z, zb);
+        za = fmaf(w1[4 * q + 3], a.w, za); zb = fmaf(w1[4 * q + 3], b.w, zb);
+      }
+      S.H1[r * HS + j] = __float2half_rn(gelu_f(za));
+      S.H1[(r + 2) * HS + j] = __float2half_rn(gelu_f(zb));
     }
     __syncthreads();
     // layer 2: warp w, rows 16 w .. 16 w + 15, all 128 units (16 n-tiles of 8)
