@@ -99,6 +99,26 @@ def test_mixed_id_single_block_error_within_1e6_of_oracle():
             assert r == r_max
 
 
+@pytest.mark.parametrize("s,n,r_max", [(1100, 1300, 550), (600, 900, 300)])
+def test_mixed_id_long_columns_within_1e6_of_oracle(s, n, r_max):
+    """Blocks of more than 512 rows in mixed precision take the register-resident QR variant
+    (2 CTAs per SM): columns longer than 1,024 rows held whole in registers, shorter ones two
+    per warp pass. The ID's full-block error stays within 1e-6 of the oracle's on the same
+    block (a geometrically decaying spectrum), with the rank within its FP32 rounding."""
+    K = workloads.random_matrix(s, n, seed=s + n, decay=(1e-8) ** (1.0 / 250))
+    ref = o_interp.interpolative_decomposition(K, r_max, 1e-6)
+    Kc = torch.tensor(np.ascontiguousarray(K.T), dtype=torch.float32, device=DEV)
+    skel, T, r, r22, st = ffc.ffc_id(Kc, r_max, 1e-6, precision=ffc.MIXED)
+    skel = skel.cpu().numpy().astype(np.int64)
+    P_g = o_interp.assemble_P(skel, T.cpu().numpy(), n)
+    assert np.array_equal(P_g[:, skel[:r]], np.eye(r))
+    e_g = np.linalg.norm(K - K[:, skel[:r]] @ P_g) / np.linalg.norm(K)
+    J_o = ref["skel_perm"][:ref["rank"]]
+    e_o = np.linalg.norm(K - K[:, J_o] @ o_interp.assemble_P(ref["skel_perm"], ref["T"], n)) / np.linalg.norm(K)
+    assert abs(r - ref["rank"]) <= max(3, ref["rank"] // 50), (r, ref["rank"])
+    assert abs(e_g - e_o) <= 1e-6, (e_g, e_o)
+
+
 def test_mixed_tree_nodes_within_1e6_of_oracle():
     P = workloads.gaussian_mixture(N=8192, d=8, k=4, seed=5)
     t_o = o_tree.build_tree(P, 256)
