@@ -34,6 +34,22 @@ __device__ __forceinline__ float half_round(float w) { return __half2float(__flo
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
+// Inference GELU, z Phi(z) = z erfc(-z / sqrt 2) / 2, with erfc from the rational
+// approximation of Abramowitz & Stegun 7.1.26 (Hastings): for x >= 0,
+// erfc(x) ~ (a1 t + a2 t^2 + ... + a5 t^5) e^{-x^2}, t = 1 / (1 + p x), |error| <= 1.5e-7.
+// Negative z take erfc directly (no cancellation in 1 + erf). The first layer rounds the
+// result to FP16 and the second feeds it to the FP32 logit, both far coarser than 1.5e-7.
+__device__ __forceinline__ float gelu_inf(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  float p = fmaf(1.061405429f, t, -1.453152027f);
+  p = fmaf(p, t, 1.421413741f);
+  p = fmaf(p, t, -0.284496736f);
+  p = fmaf(p, t, 0.254829592f);
+  const float q = p * t * __expf(-x * x);   // erfc(|z| / sqrt 2)
+  return 0.5f * z * (z >= 0.0f ? 2.0f - q : q);
+}
+
 // d/dz z Phi(z) = Phi(z) + z phi(z)
 __device__ __forceinline__ float gelu_prime_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
@@ -332,8 +348,8 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
         za = fmaf(w1[4 * q + 2], a.z, za); zb = fmaf(w1[4 * q + 2], b.z, zb);
         za = fmaf(w1[4 * q + 3], a.w, za); zb = fmaf(w1[4 * q + 3], b.w, zb);
       }
-      S.H1[r * HS + j] = __float2half_rn(gelu_f(za));
-      S.H1[(r + 2) * HS + j] = __float2half_rn(gelu_f(zb));
+      S.H1[r * HS + j] = __float2half_rn(gelu_inf(za));
+      S.H1[(r + 2) * HS + j] = __float2half_rn(gelu_inf(zb));
     }
     __syncthreads();
     // layer 2: warp w, rows 16 w .. 16 w + 15, all 128 units (16 n-tiles of 8)
@@ -359,10 +375,10 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
 #pragma unroll
     for (int nt = 0; nt < 16; ++nt) {
       const int c = nt * 8 + 2 * (lane & 3);
-      po0 = fmaf(S.w3[c], gelu_f(acc[nt][0] + S.b2[c]), po0);
-      po0 = fmaf(S.w3[c + 1], gelu_f(acc[nt][1] + S.b2[c + 1]), po0);
-      po1 = fmaf(S.w3[c], gelu_f(acc[nt][2] + S.b2[c]), po1);
-      po1 = fmaf(S.w3[c + 1], gelu_f(acc[nt][3] + S.b2[c + 1]), po1);
+      po0 = fmaf(S.w3[c], gelu_inf(acc[nt][0] + S.b2[c]), po0);
+      po0 = fmaf(S.w3[c + 1], gelu_inf(acc[nt][1] + S.b2[c + 1]), po0);
+      po1 = fmaf(S.w3[c], gelu_inf(acc[nt][2] + S.b2[c]), po1);
+      po1 = fmaf(S.w3[c + 1], gelu_inf(acc[nt][3] + S.b2[c + 1]), po1);
     }
     po0 += __shfl_xor_sync(0xffffffffu, po0, 1);
     po0 += __shfl_xor_sync(0xffffffffu, po0, 2);
