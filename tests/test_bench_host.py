@@ -1,0 +1,61 @@
+"""Host-side pieces of the benchmark on CPU: the reference arm's JSON line (the
+FP64 oracle timed on the host cores), the QR traffic record and the rooflines."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["metric"] == bench.METRIC and line["unit"] == "nodes/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == bench.WORKLOADS["c2"]["workload"]
+
+
+def test_traffic_record_applies_only_to_its_kernel_source_and_workload(tmp_path, monkeypatch):
+    bench.select_workload("c2")
+    t, src = bench.qr_traffic("mixed", "learned")
+    if t is not None:                         # the committed record matches the current source
+        assert t > 0 and src.startswith("profiles/")
+    assert bench.qr_traffic("fp64", "uniform") == (None, None)
+    bench.select_workload("c4")
+    assert bench.qr_traffic("mixed", "learned") == (None, None)
+    bench.select_workload("c2")
+    # a record for another kernel source is ignored
+    fake = tmp_path / "profiles"
+    fake.mkdir()
+    (fake / "cpqr_traffic_x.md").write_text("traffic_bytes_per_step: 5\ncpqr_sha256: 00\n"
+                                            f"workload: {bench.WORKLOAD['workload']}\nprecision: mixed\n"
+                                            "sampler: learned\n")
+    csrc = tmp_path / "paper_1409_2802_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "cpqr.cu").write_text("// another source\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.qr_traffic("mixed", "learned") == (None, None)
+
+
+def test_eval_roofline_bound_by_path():
+    prof = {"ms": {"eval": 30.0}, "eval_flops": 3.0 * 1e12}
+    bench.select_workload("c4")
+    r = bench.eval_roofline(prof, 1, "mixed", {"bf16_tflops_sustained": 1710.8}, "measured")
+    assert r["bound"] == "tensor" and abs(r["achieved"] - 2e12 / 0.030 / 1e12) < 1e-9
+    assert abs(r["tensor_work_tflops"] - 6 * r["achieved"]) < 1e-9 and r["peak"] == 1710.8
+    bench.select_workload("c2")                       # d = 16: the SIMT path
+    r = bench.eval_roofline(prof, 1, "mixed", {}, "measured")
+    assert r["bound"] == "alu" and r["peak"] == bench.FP32_PEAK_TFLOPS
+    bench.select_workload("c3-laplace")               # Laplace stays SIMT at any d
+    assert bench.eval_roofline(prof, 1, "mixed", {}, "measured")["bound"] == "alu"
+    bench.select_workload("c2")
