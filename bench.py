@@ -208,13 +208,15 @@ def precision_code(ffc, name):
     return ffc.FP64 if name == "fp64" else ffc.MIXED
 
 
-def run_gpu_steps(torch, ffc, Pp, tree, k, precision, steps, warmup, flush_buf, stream, result=None, proposal=None):
+def run_gpu_steps(torch, ffc, Pp, tree, k, precision, steps, warmup, flush_buf, stream, result=None, proposal=None,
+                  qr_kw=None):
     W = WORKLOAD
+    qr_kw = qr_kw or {}
 
     def step(res):
         return ffc.ffc_compress_tree(Pp, tree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
                                      s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
-                                     stream=stream, proposal=proposal)
+                                     stream=stream, proposal=proposal, **qr_kw)
 
     res = result
     for _ in range(warmup):
@@ -236,7 +238,7 @@ def run_gpu_steps(torch, ffc, Pp, tree, k, precision, steps, warmup, flush_buf, 
     return res, times, prof
 
 
-def run_e2e(torch, ffc, P_host_perm, tree, k, precision, steps, warmup, stream, proposal=None):
+def run_e2e(torch, ffc, P_host_perm, tree, k, precision, steps, warmup, stream, proposal=None, qr_kw=None):
     """Same metric through host buffers: pinned H2D inputs, compress, D2H results, every step."""
     W = WORKLOAD
     dev = P_host_perm.device if P_host_perm.is_cuda else torch.device("cuda")
@@ -256,7 +258,7 @@ def run_e2e(torch, ffc, P_host_perm, tree, k, precision, steps, warmup, stream, 
                 dT[n].copy_(tree_host[n], non_blocking=True)
         res = ffc.ffc_compress_tree(dP, dtree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
                                     s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
-                                    stream=stream, proposal=proposal)
+                                    stream=stream, proposal=proposal, **(qr_kw or {}))
         with torch.cuda.stream(stream):
             v = ffc.tree_result_views(res)
             out = {kk: v[kk].to("cpu", non_blocking=False) for kk in ("rank", "s", "status", "r22_rel", "skel", "T_off",
@@ -423,9 +425,10 @@ FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nomin
 
 
 
-def qr_traffic(precision_name, sampler):
+def qr_traffic(precision_name, sampler, shape=None):
     """DRAM bytes per step of the QR launches from the committed ncu record, while the kernel source
-    still matches the one the counters were taken on; else None."""
+    and the QR launch shape (``shape``: qr_big_min_s / qr_l2_budget_mb, None = the library defaults)
+    still match the ones the counters were taken on; else None."""
     import glob
     import hashlib
     src = os.path.join(ROOT, "paper_1409_2802_gb300", "csrc", "cpqr.cu")
@@ -438,8 +441,10 @@ def qr_traffic(precision_name, sampler):
                 if ":" in line and not line.startswith(("#", "|", "*", " ")):
                     k, v = line.split(":", 1)
                     rec[k.strip()] = v.strip()
+        want = dict(shape or {"qr_big_min_s": 1024, "qr_l2_budget_mb": 96})
+        same_shape = all(str(want.get(k_)) == rec.get(k_) for k_ in ("qr_big_min_s", "qr_l2_budget_mb"))
         if (rec.get("cpqr_sha256") == h and rec.get("workload") == WORKLOAD["workload"]
-                and rec.get("precision") == precision_name and rec.get("sampler") == sampler):
+                and rec.get("precision") == precision_name and rec.get("sampler") == sampler and same_shape):
             return float(rec["traffic_bytes_per_step"]), os.path.relpath(path, ROOT)
     return None, None
 
@@ -469,7 +474,7 @@ def eval_roofline(prof, steps, precision_name, peaks, peak_src):
             "peak_source": "nominal FP32 rate of GB300" if precision_name == "mixed" else "nominal FP64 rate of GB300"}
 
 
-def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned"):
+def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned", shape=None):
     """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing.
 
     Algorithmic bytes: one read and one write of every sampled block K' (s x n)
@@ -489,7 +494,7 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned")
     else:
         alu_peak, kern, src = FP32_PEAK_TFLOPS, "cpqr_kernel<float> (pivoted QR, FP32 updates, FP64 norms)", \
             "nominal FP32 rate of GB300 (152 SMs x 128 lanes x 2.07 GHz)"
-    traffic, traffic_src = qr_traffic(precision_name, sampler)
+    traffic, traffic_src = qr_traffic(precision_name, sampler, shape)
     return {
         "kernel": kern, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
         "traffic": traffic, "traffic_unit": "bytes per step (all QR launches of one call)",
@@ -569,6 +574,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the QR launch-shape autotuner (untimed, before the timed form's steps)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the headline): d=16 mixture; c3-laplace / c3-poly: d=128; c4: d=1000 FP32")
     ap.add_argument("--_cpu-leg", type=float, default=None, help=argparse.SUPPRESS)
@@ -605,12 +612,21 @@ def main():
     prec = precision_code(ffc, args.precision)
     peaks, peak_src = load_peaks()
 
-    def timed(prec_code, steps, warmup, prop):
+    tuned = None
+    if not args.no_autotune:
+        from paper_1409_2802_gb300 import autotune
+        W = WORKLOAD
+        tuned = autotune.tune_tree(Pp, tree, kern, precision=prec, stream=stream, tol=W["tol"],
+                                   min_level=W["min_level"], s0=W["s0"], s_max=W["s_max"], xi=W["xi"],
+                                   seed=W["sample_seed"], proposal=proposal)
+    qr_kw = {k_: tuned[k_] for k_ in ("qr_big_min_s", "qr_l2_budget_mb")} if tuned else {}
+
+    def timed(prec_code, steps, warmup, prop, kw=None):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, kern, prec_code, steps, warmup, flush, stream,
-                                         proposal=prop)
+                                         proposal=prop, qr_kw=kw)
         torch.cuda.synchronize()
         total = max_over_ranks(sum(times), world, dev)
         if world > 1:
@@ -619,7 +635,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    res, total_ms, prof = timed(prec, args.steps, args.warmup, proposal)
+    res, total_ms, prof = timed(prec, args.steps, args.warmup, proposal, qr_kw)
     clk = clocks.stop()
     n_nodes = int(ffc.tree_result_views(res)["n_out"])
     value = job_throughput(n_nodes, args.steps, world, total_ms)
@@ -634,10 +650,12 @@ def main():
                    "s": "128 doubling to 2048", "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk, "gpu_launches": int(prof["launches"]),
-        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src, args.sampler),
+        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src, args.sampler, qr_kw or None),
     }
     if train_info is not None:
         line["config"]["proposal_training"] = train_info
+    line["config"]["qr_launch_shape"] = (dict(tuned, source="autotune (timed form; other arms: defaults)")
+                                         if tuned else {"source": "library defaults"})
     # each arm's sampled errors are taken as soon as it has run and its result is released, so
     # that only one arm's workspace is resident at a time
     errors = {}
@@ -671,7 +689,8 @@ def main():
     if errors:
         line["accuracy"] = accuracy_summary(errors)
     if not args.no_e2e:
-        line["e2e"] = run_e2e(torch, ffc, Pp, tree, kern, prec, max(3, args.steps // 2), 2, stream, proposal=proposal)
+        line["e2e"] = run_e2e(torch, ffc, Pp, tree, kern, prec, max(3, args.steps // 2), 2, stream, proposal=proposal,
+                              qr_kw=qr_kw)
     if oracle is not None:
         line["cpu_baseline"] = finish_cpu_baseline(oracle, args.cpu_seconds)
     if rank == 0:

@@ -251,6 +251,13 @@ typedef struct {
                           uniform pool of pool_rows >= s_max rows */
   const double* proj_dev;   /* learned: 8 x d random directions of the projection features */
   const float* mlp_dev;     /* learned: FFC_MLP_PARAMS network parameters (FP32 master copy) */
+  /* launch shape of the pivoted QR (no effect on what is computed beyond FP32 summation order;
+   * 0 = the library's defaults, which the project's autotuner measures against):
+   * qr_big_min_s: mixed precision, rounds with s >= this use the register-resident variant
+   *   (2 CTAs per SM, 128 registers; default 1024); > s_max disables it;
+   * qr_l2_budget_mb: bytes of sampled blocks per cooperative QR launch, in MB (default 96) */
+  int32_t qr_big_min_s;
+  int32_t qr_l2_budget_mb;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2) or the learned proposal

@@ -1060,13 +1060,13 @@ trsm_kernel(const TrsmItem* __restrict__ items, int n_items) {
   }
 }
 
-// FP32 blocks of more than 512 rows: the register-resident variant (2 CTAs per SM); measured
-// faster from s = 1,024 on (at s = 512 the third CTA per SM is worth more)
-#ifndef FFC_QR_BIG_MIN_ROWS
-#define FFC_QR_BIG_MIN_ROWS 512
-#endif
+// FP32 blocks: the register-resident variant (2 CTAs per SM) when the caller asks for it, by
+// default from s = 1,024 on (measured faster there; at s = 512 the third CTA per SM is worth more)
 template <typename T>
-bool qr_big(int s_max) { return sizeof(T) == 4 && s_max > FFC_QR_BIG_MIN_ROWS; }
+bool qr_big(int s_max, int big) {
+  if (sizeof(T) != 4) return false;
+  return big < 0 ? s_max >= QR_BIG_MIN_S_DEFAULT : big != 0;
+}
 
 template <typename T>
 size_t cpqr_smem_bytes(int s_max) {
@@ -1078,13 +1078,13 @@ size_t cpqr_smem_bytes(int s_max) {
 
 template <typename T>
 ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const int32_t* cta_off, int grid,
-                         int s_max, cudaStream_t st) {
+                         int s_max, cudaStream_t st, int big) {
   if (s_max > 2048) {
     set_error("cpqr: s = %d exceeds the supported 2048 rows", s_max);
     return FFC_E_INVALID;
   }
   const size_t smem = cpqr_smem_bytes<T>(s_max);
-  auto kfn = qr_big<T>(s_max) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+  auto kfn = qr_big<T>(s_max, big) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
   FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1101,10 +1101,10 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
 }
 
 template <typename T>
-int max_ctas_t(int s_max) {
+int max_ctas_t(int s_max, int big) {
   int per_sm = 0;
   const size_t smem = cpqr_smem_bytes<T>(s_max);
-  auto kfn = qr_big<T>(s_max) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+  auto kfn = qr_big<T>(s_max, big) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, QR_THREADS, smem);
   return per_sm * sm_count();
@@ -1133,15 +1133,15 @@ int64_t trsm_tiles(int64_t n) { return (n + TS_COLS - 1) / TS_COLS; }
 
 int cpqr_min_group(int64_t n) { return (int)std::max<int64_t>(1, (n + QR_NCOL_MAX - 1) / QR_NCOL_MAX); }
 
-int cpqr_max_ctas(int precision, int s_max) {
-  return precision == FFC_MIXED ? max_ctas_t<float>(s_max) : max_ctas_t<double>(s_max);
+int cpqr_max_ctas(int precision, int s_max, int big) {
+  return precision == FFC_MIXED ? max_ctas_t<float>(s_max, big) : max_ctas_t<double>(s_max, 0);
 }
 
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid, int s_max,
-                       cudaStream_t st, const int32_t* cta_off) {
+                       cudaStream_t st, const int32_t* cta_off, int big) {
   if (grid <= 0) return FFC_OK;
-  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st);
-  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st);
+  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st, big);
+  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st, 0);
 }
 
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,

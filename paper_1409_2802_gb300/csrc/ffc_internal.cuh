@@ -241,9 +241,12 @@ ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, in
                        int32_t* status /* n_items */, cudaStream_t st);
 // entries: per-CTA work lists (CTA b runs entries[cta_off[b] .. cta_off[b+1]) in order), or with
 // cta_off == NULL one entry per CTA.
+// big: the register-resident variant (mixed precision only; -1 = the default rule s_max >= 1024)
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
-                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr);
-int cpqr_max_ctas(int precision, int s_max);
+                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr, int big = -1);
+int cpqr_max_ctas(int precision, int s_max, int big = -1);
+constexpr int QR_BIG_MIN_S_DEFAULT = 1024;
+constexpr int QR_L2_BUDGET_MB_DEFAULT = 96;
 int cpqr_min_group(int64_t n);   // fewest CTAs a group of n columns may have (per-CTA column cap)
 int64_t trsm_tiles(int64_t n);   // CTAs of the triangular solve for n columns
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,

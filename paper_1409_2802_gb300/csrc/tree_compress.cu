@@ -213,11 +213,8 @@ ffc_status grow(char** buf, size_t* have, size_t want, cudaStream_t st) {
   return FFC_OK;
 }
 
-// Bytes of sampled blocks one QR launch may hold: below the 129 MB L2.
-#ifndef FFC_QR_L2_BUDGET_MB
-#define FFC_QR_L2_BUDGET_MB 96
-#endif
-constexpr size_t QR_L2_BUDGET = (size_t)FFC_QR_L2_BUDGET_MB << 20;
+// Bytes of sampled blocks one QR launch may hold: below the 129 MB L2 (ffc_params.qr_l2_budget_mb,
+// default QR_L2_BUDGET_MB_DEFAULT).
 
 // Learned sampler: for every output node, the candidate pool (whole far field
 // or a uniform pool), features, network logits and the weighted draw of its
@@ -375,7 +372,9 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     tiles_tot += eval_tiles(s_nom, n, eval_shape(P.kernel, d, P.precision));
     n_max = std::max(n_max, n);
   }
-  const int cap = cpqr_max_ctas(P.precision, (int)s_nom);
+  const int big_min = P.qr_big_min_s > 0 ? P.qr_big_min_s : QR_BIG_MIN_S_DEFAULT;
+  const int big = (P.precision == FFC_MIXED && s_nom >= big_min) ? 1 : 0;
+  const int cap = cpqr_max_ctas(P.precision, (int)s_nom, big);
   if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
   // The round's QR runs as one cooperative launch per sub-batch of
   // consecutive items whose blocks together fit in QR_L2_BUDGET bytes: the
@@ -387,6 +386,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   // increasing order).
   std::vector<int> sb;   // sub-batch starts, then W
   {
+    const size_t QR_L2_BUDGET = (size_t)(P.qr_l2_budget_mb > 0 ? P.qr_l2_budget_mb : QR_L2_BUDGET_MB_DEFAULT) << 20;
     size_t acc = 0;
     for (int q = 0; q < W; ++q) {
       const size_t bq = esz * (size_t)s_nom * (size_t)R->count_h[items[q]];
@@ -566,7 +566,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
   // one cooperative QR launch per L2-sized sub-batch of the round
   for (int bb = 0; bb < n_sb; ++bb) {
-    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb]);
+    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb], big);
     if (rc != FFC_OK) return rc;
   }
   const int qr_launches = n_sb;

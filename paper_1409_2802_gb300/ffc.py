@@ -63,7 +63,8 @@ class c_params(ctypes.Structure):
     _fields_ = [("kernel", c_kernel), ("precision", ctypes.c_int32), ("min_level", ctypes.c_int32),
                 ("s0", ctypes.c_int32), ("s_max", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
-                ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p)]
+                ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
+                ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -320,8 +321,11 @@ class TreeResult:
 
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
-                      proposal: tuple | None = None, pool_rows=0) -> TreeResult:
-    """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler."""
+                      proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
+                      qr_l2_budget_mb=0) -> TreeResult:
+    """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler.
+    ``qr_big_min_s``, ``qr_l2_budget_mb``: the QR's launch shape (0 = the library's defaults; see
+    ``autotune``)."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
@@ -331,7 +335,8 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
         _dev(mlp, "proposal params"), _dev(proj, "proposal proj")
         sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
-                 ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p)
+                 ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
+                 int(qr_l2_budget_mb))
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))

@@ -101,10 +101,11 @@ def test_mixed_id_single_block_error_within_1e6_of_oracle():
 
 @pytest.mark.parametrize("s,n,r_max", [(1100, 1300, 550), (600, 900, 300)])
 def test_mixed_id_long_columns_within_1e6_of_oracle(s, n, r_max):
-    """Blocks of more than 512 rows in mixed precision take the register-resident QR variant
-    (2 CTAs per SM): columns longer than 1,024 rows held whole in registers, shorter ones two
-    per warp pass. The ID's full-block error stays within 1e-6 of the oracle's on the same
-    block (a geometrically decaying spectrum), with the rank within its FP32 rounding."""
+    """Mixed-precision ID of blocks of 1,100 rows (the register-resident QR variant, 2 CTAs per
+    SM: columns longer than 1,024 rows held whole in registers, shorter ones two per warp pass)
+    and 600 rows (the general variant, columns streamed in chunks beyond 512 rows). The ID's
+    full-block error stays within 1e-6 of the oracle's on the same block (a geometrically
+    decaying spectrum), with the rank within its FP32 rounding."""
     K = workloads.random_matrix(s, n, seed=s + n, decay=(1e-8) ** (1.0 / 250))
     ref = o_interp.interpolative_decomposition(K, r_max, 1e-6)
     Kc = torch.tensor(np.ascontiguousarray(K.T), dtype=torch.float32, device=DEV)

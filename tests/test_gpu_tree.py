@@ -157,3 +157,32 @@ def test_compress_tree_learned_sampler_matches_oracle():
         assert int(out["status"][i]) == ref.status and int(out["rank"][i]) == ref.rank, node
         assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
     assert same >= 0.8 * len(nodes), (same, len(nodes))
+
+
+def test_qr_launch_shape_and_autotuner():
+    """The QR's launch shape (sub-batch budget, register-resident variant threshold) does not change
+    what is computed: across budgets the FP64 ranks, samples, statuses and skeletons are identical
+    (integer pivot keys, the same per-column arithmetic) and T and the residual agree to rounding
+    (the per-CTA partial sums of ||K'||^2 depend on the column slicing); the tuner returns one of its
+    candidates and times every one it tried."""
+    from paper_1409_2802_gb300 import autotune
+    P = workloads.gaussian_mixture(N=8192, d=8, k=4, seed=11)
+    t_g = ffc.ffc_build_tree(cu(P), 256)
+    Pp = cu(P)[t_g.perm].contiguous()
+    k = ffc.Kernel(ffc.GAUSSIAN, h=1.5)
+    outs = [ffc.tree_result_to_host(ffc.ffc_compress_tree(Pp, t_g, k, tol=1e-6, s0=64, s_max=1024,
+                                                          qr_l2_budget_mb=b)) for b in (1, 64, 128)]
+    for o in outs[1:]:
+        for key in ("rank", "s", "status", "skel"):
+            assert np.array_equal(outs[0][key], o[key]), key
+        assert np.allclose(o["r22_rel"], outs[0]["r22_rel"], rtol=1e-12, atol=1e-300)
+        assert np.allclose(o["T"], outs[0]["T"], rtol=1e-9, atol=1e-12 * np.max(np.abs(outs[0]["T"])))
+    mixed = [ffc.tree_result_to_host(ffc.ffc_compress_tree(Pp, t_g, k, tol=1e-6, s0=64, s_max=1024,
+                                                           precision=ffc.MIXED, qr_big_min_s=b)) for b in (64, 4096)]
+    same = mixed[0]["s"] == mixed[1]["s"]          # a tolerance decision at the margin may flip
+    assert np.mean(same) >= 0.98
+    assert np.max(np.abs(mixed[0]["r22_rel"][same] - mixed[1]["r22_rel"][same])) <= 1e-6
+    best = autotune.tune_tree(Pp, t_g, k, precision=ffc.MIXED, tol=1e-6, s0=64, s_max=1024)
+    assert best["qr_big_min_s"] in autotune.BIG_MIN_S and best["qr_l2_budget_mb"] in autotune.L2_BUDGET_MB
+    assert len(best["table"]) == len(autotune.BIG_MIN_S) + len(autotune.L2_BUDGET_MB) - 1
+    assert best["ms"] == min(r["ms"] for r in best["table"] if r["qr_big_min_s"] == best["qr_big_min_s"])
