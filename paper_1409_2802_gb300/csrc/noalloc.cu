@@ -108,7 +108,7 @@ extern "C" ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t 
   FFC_REQUIRE(kcap <= NA_MAX_RANK, "ffc_id_noalloc: min(r_max, s, n) = %lld exceeds the fixed scratch limit of %lld",
               (long long)kcap, (long long)NA_MAX_RANK);
   FFC_REQUIRE(ldt >= std::max<int64_t>(r_max, 1), "ffc_id_noalloc: ldt must be >= max(r_max, 1)");
-  FFC_REQUIRE(precision == FFC_FP64, "ffc_id_noalloc: only FFC_FP64 is available in this build");
+  FFC_REQUIRE(precision == FFC_FP64, "ffc_id_noalloc: only FFC_FP64 is supported");
   FFC_REQUIRE(rank_host && r22_rel_host, "ffc_id_noalloc: null output pointer");
   FFC_REQUIRE(n == 0 || (K_dev && skel_perm_dev && T_dev), "ffc_id_noalloc: null pointer");
   if (n == 0) { *rank_host = 0; *r22_rel_host = 0.0; return FFC_OK; }
