@@ -99,6 +99,30 @@ def test_mixed_id_single_block_error_within_1e6_of_oracle():
             assert r == r_max
 
 
+@pytest.mark.parametrize("d", [64, 128])
+def test_mixed_laplace_high_d_matches_oracle_up_to_the_scale(d):
+    """Mixed-precision Laplace |x - y|^-(d-2) at d = 64 and 128: FP32 distances, with FP64 for pairs
+    that cancel and for every entry at or above 1e-6 of the largest. The block may differ from the
+    oracle's by a constant factor (its scale comes from the FP32 minimum distance), so both are
+    compared normalised by their largest entry: entries from 1e-6 up carry FP64 distances (FP32
+    rounding of the stored value), smaller ones the FP32 distance's error times (d - 2) / 2."""
+    g = np.random.default_rng(d)
+    X = g.standard_normal((500, d)) / np.sqrt(d)
+    Y = g.standard_normal((700, d)) / np.sqrt(d) + 2.0 / np.sqrt(d)
+    rows = g.choice(700, 256, replace=False).astype(np.int64)
+    ko = o_kernels.Kernel(o_kernels.LAPLACE)
+    Ko, _ = o_kernels.kernel_block(ko, Y[rows], X)
+    Kg, _ = ffc.ffc_eval_block(ffc.Kernel(ffc.LAPLACE), cu(Y), cu(rows), cu(X), precision=ffc.MIXED,
+                               center=cu(X.mean(axis=0)))
+    Kg = Kg.double().cpu().numpy()
+    kg, kr = Kg / Kg.max(), Ko / Ko.max()
+    u = 2.0 ** -24
+    big = kr >= 2e-6
+    assert np.all(np.abs(kg[big] - kr[big]) <= 4 * u * kr[big] + 1e-12)
+    small_bound = kr[~big] * (d - 2) / 2 * (d + 16) * 4 * u * 20 + 1e-12
+    assert np.all(np.abs(kg[~big] - kr[~big]) <= small_bound)
+
+
 @pytest.mark.parametrize("s,n,r_max", [(1100, 1300, 550), (600, 900, 300)])
 def test_mixed_id_long_columns_within_1e6_of_oracle(s, n, r_max):
     """Mixed-precision ID of blocks of 1,100 rows (the register-resident QR variant, 2 CTAs per
