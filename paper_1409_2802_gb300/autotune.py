@@ -54,8 +54,13 @@ def tune_tree(points_perm, tree: ffc.DeviceTree, kernel: ffc.Kernel, precision=f
     table = []
 
     def run(big, budget):
-        ms = _time_call(points_perm, tree, kernel, stream, reps, precision=precision, qr_big_min_s=big,
-                        qr_l2_budget_mb=budget, **compress_kw)
+        # a candidate the device cannot run (e.g. out of memory) is skipped, not fatal
+        try:
+            ms = _time_call(points_perm, tree, kernel, stream, reps, precision=precision, qr_big_min_s=big,
+                            qr_l2_budget_mb=budget, **compress_kw)
+        except ffc.FFCError as e:
+            table.append({"qr_big_min_s": big, "qr_l2_budget_mb": budget, "error": str(e)[:120]})
+            return float("inf")
         table.append({"qr_big_min_s": big, "qr_l2_budget_mb": budget, "ms": round(ms, 3)})
         return ms
 
@@ -71,5 +76,7 @@ def tune_tree(points_perm, tree: ffc.DeviceTree, kernel: ffc.Kernel, precision=f
         if b not in budgets:
             budgets[b] = run(big, b)
     budget = min(budgets, key=budgets.get)
+    if budgets[budget] == float("inf"):
+        raise ffc.FFCError(ffc.FFC_E_CUDA, "autotune: no candidate launch shape ran")
     return {"qr_big_min_s": big, "qr_l2_budget_mb": budget, "ms": round(budgets[budget], 3), "table": table,
             "seconds": round(time.perf_counter() - t0, 1)}
