@@ -14,8 +14,11 @@
 // D2 is recomputed from direct FP32 differences.
 //
 // Tiles: 128 targets x 128 sources per CTA (8 warps of 64 x 32), 32
-// coordinates per stage; every thread stages one target or source row
-// (centred, rounded to FP32, split) and its squared norm.
+// coordinates per stage. Eight threads stage a target or source row, four
+// coordinates each, with coalesced 16-byte loads: centred (FP32 points
+// against the FP32-rounded centre, FP64 points in FP64), rounded to FP32 and
+// split; their partial squared norms are summed in a fixed order at the end
+// of the tile.
 #include <cuda_bf16.h>
 
 #include <algorithm>
