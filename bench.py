@@ -306,33 +306,69 @@ def oracle_compress(Pp, t, kernel, node):
                                     W["xi"])
 
 
-def cpu_leg() -> int:
-    """Child process: compress nodes in a seeded random order, one JSON line per finished node."""
-    Pp, t, kernel = oracle_setup()
-    order = oracle_nodes_in_order(t)
-    print(json.dumps({"ready": True, "of": len(order)}), flush=True)
-    t0 = time.perf_counter()
-    for i, node in enumerate(order):
-        oracle_compress(Pp, t, kernel, node)
-        print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
+_WORKER = {}
+
+
+def _worker_init(name, barrier):
+    """Pool worker: the oracle's inputs (points, tree, kernel), then wait for every other worker."""
+    select_workload(name)
+    _WORKER["state"] = oracle_setup()
+    barrier.wait()
+
+
+def _worker_compress(node):
+    Pp, t, kernel = _WORKER["state"]
+    oracle_compress(Pp, t, kernel, node)
+    return int(node)
+
+
+def cpu_leg(workers: int = 1) -> int:
+    """Child process: compress nodes in a seeded random order, one JSON line per finished node.
+    With workers > 1 the nodes go to a pool of single-threaded processes (spawned), each with its own
+    copy of the oracle's inputs; the stream reports ready once every worker holds them."""
+    if workers <= 1:
+        Pp, t, kernel = oracle_setup()
+        order = oracle_nodes_in_order(t)
+        print(json.dumps({"ready": True, "of": len(order), "workers": 1}), flush=True)
+        t0 = time.perf_counter()
+        for i, node in enumerate(order):
+            oracle_compress(Pp, t, kernel, node)
+            print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
+        return 0
+    import multiprocessing as mp
+    from oracle import tree as o_tree
+    P = workload_points()
+    order = oracle_nodes_in_order(o_tree.build_tree(P, WORKLOAD["leaf_size"]))
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(workers + 1)
+        with ctx.Pool(workers, initializer=_worker_init, initargs=(WORKLOAD.get("name", "c2"), barrier)) as pool:
+            barrier.wait()
+            print(json.dumps({"ready": True, "of": len(order), "workers": workers}), flush=True)
+            t0 = time.perf_counter()
+            for i, _ in enumerate(pool.imap_unordered(_worker_compress, order, chunksize=1)):
+                print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
     return 0
 
 
 class OracleStream:
-    """The FP64 oracle compressing nodes in a seeded random order in a single-threaded child process.
+    """The FP64 oracle compressing nodes in a seeded random order in a child process: one
+    single-threaded process, or a pool of `workers` of them over the host cores.
 
     The child prints one line per finished node; the parent reads the count of
-    finished nodes at any time. The node in progress when a window closes
-    counts as time spent, so a window's throughput is finished nodes / window.
+    finished nodes at any time. The nodes in progress when a window closes
+    count as time spent, so a window's throughput is finished nodes / window.
     """
 
-    def __init__(self):
+    def __init__(self, workers: int = 1):
+        self.workers = max(1, int(workers))
         env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
         for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
             env.pop(k, None)
-        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", "1",
+        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", str(self.workers),
                                       "--workload", WORKLOAD.get("name", "c2")], env=env,
-                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                                     start_new_session=True)
         self.of, self.ready_t, self.done = None, None, 0
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
@@ -364,15 +400,20 @@ class OracleStream:
         return self.done - d0, time.perf_counter() - t0
 
     def close(self):
-        self.proc.kill()
+        # the child's own process group holds its pool workers
+        try:
+            os.killpg(self.proc.pid, 9)
+        except (ProcessLookupError, PermissionError):
+            self.proc.kill()
         self.proc.wait()
 
 
-def finish_cpu_baseline(o: "OracleStream", min_seconds: float) -> dict:
-    """Close the oracle stream started at the beginning of the run (one core, concurrent with the GPU work)."""
+def finish_cpu_baseline(o: "OracleStream", min_seconds: float, when: str) -> dict:
+    """Close an oracle stream after at least `min_seconds` of it; nodes finished / window."""
     try:
         if not o.wait_ready():
-            return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "oracle setup failed"}
+            return {"value": None, "unit": UNIT, "cores": o.workers, "kind": "oracle",
+                    "sample": "oracle setup failed"}
         remaining = o.ready_t + min_seconds - time.perf_counter()
         if remaining > 0:
             o.window(remaining)
@@ -380,10 +421,18 @@ def finish_cpu_baseline(o: "OracleStream", min_seconds: float) -> dict:
         done = o.done
     finally:
         o.close()
-    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    procs = "one thread" if o.workers == 1 else f"{o.workers} single-threaded processes, one node each at a time"
+    return {"value": done / el, "unit": UNIT, "cores": o.workers, "kind": "oracle",
             "sample": (f"{done} of {o.of} nodes finished in a {el:.1f} s window (seeded random node order; the "
-                       f"node still running at the end counts as time spent), uniform sampler, one thread "
-                       f"(OMP/OpenBLAS = 1), running on a host core while the GPU steps ran")}
+                       f"nodes still running at the end count as time spent), uniform sampler, {procs} "
+                       f"(OMP/OpenBLAS = 1), {when}")}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def reference_arm(args, rank, world):
@@ -391,7 +440,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     win = min(20.0, max(2.0, 150.0 / (args.steps + args.warmup)))
-    o = OracleStream()
+    o = OracleStream(args.cpu_workers or host_cores())
     try:
         if not o.wait_ready():
             print(json.dumps({"impl": "reference", "unavailable": "oracle setup failed"}))
@@ -412,9 +461,9 @@ def reference_arm(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD["workload"], "step": f"{win:.1f} s window of the oracle's node stream",
                    "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": o.workers,
                          "sample": f"{done} nodes finished over {args.steps} windows of {win:.1f} s "
-                                   f"(seeded random node order), one thread"},
+                                   f"(seeded random node order), {o.workers} single-threaded processes"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -572,18 +621,20 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 uniform arm and the others")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=30.0)
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="oracle processes for the all-cores CPU baseline and the reference arm (0 = every host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the QR launch-shape autotuner (untimed, before the timed form's steps)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the headline): d=16 mixture; c3-laplace / c3-poly: d=128; c4: d=1000 FP32")
-    ap.add_argument("--_cpu-leg", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--_cpu-leg", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     select_workload(args.workload)
 
     if args._cpu_leg is not None:
-        return cpu_leg()
+        return cpu_leg(args._cpu_leg)
 
     rank, world, local = _env_rank()
     oracle = OracleStream() if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.impl == "ours") else None
@@ -696,7 +747,15 @@ def main():
         line["e2e"] = run_e2e(torch, ffc, Pp, tree, kern, prec, max(3, args.steps // 2), 2, stream, proposal=proposal,
                               qr_kw=qr_kw)
     if oracle is not None:
-        line["cpu_baseline"] = finish_cpu_baseline(oracle, args.cpu_seconds)
+        single = finish_cpu_baseline(oracle, args.cpu_seconds, "on a host core while the GPU steps ran")
+        # every host core, after the GPU work (so that it does not compete with the GPU process's host thread)
+        try:
+            multi = finish_cpu_baseline(OracleStream(args.cpu_workers or host_cores()),
+                                        min(20.0, args.cpu_seconds), "on the host cores after the GPU work")
+        except (OSError, RuntimeError) as e:
+            multi = {"value": None, "sample": f"all-cores oracle failed: {e}"}
+        line["cpu_baseline"] = multi if multi["value"] is not None else single
+        line["cpu_baseline_single_core"] = single
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

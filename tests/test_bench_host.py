@@ -11,8 +11,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_the_contract_line():
+    """The oracle over a pool of two processes (the arm's default is every host core)."""
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "0", "--cpu-workers", "2"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
@@ -20,9 +22,10 @@ def test_reference_arm_prints_the_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["metric"] == bench.METRIC and line["unit"] == "nodes/s" and line["higher_is_better"] is True
-    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"] == bench.WORKLOADS["c2"]["workload"]
+    assert line["cpu_baseline"]["cores"] == 2
 
 
 def test_traffic_record_applies_only_to_its_kernel_source_and_workload(tmp_path, monkeypatch):
@@ -59,3 +62,10 @@ def test_eval_roofline_bound_by_path():
     bench.select_workload("c3-laplace")               # Laplace stays SIMT at any d
     assert bench.eval_roofline(prof, 1, "mixed", {}, "measured")["bound"] == "alu"
     bench.select_workload("c2")
+
+
+def test_oracle_stream_over_worker_processes():
+    """The all-cores CPU baseline: a pool of single-threaded oracle processes, closed with its group."""
+    bench.select_workload("c2")
+    cb = bench.finish_cpu_baseline(bench.OracleStream(2), 4.0, "test")
+    assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] is not None and cb["value"] > 0
