@@ -26,6 +26,8 @@ checks it against the paper by eye: no blocking, no fusion, no reordering.
                 leverage-score training targets (§3, §4.1.3).
 * ``apply``     the outgoing representation: skeleton charges q~ = P q and the
                 far-field potential C q~ (§2.1.3).
+* ``samplers``  the paper's other row samplers: distance, leverage and nearest
+                neighbours (§4.1.3, §3).
 
 Parity pins live in ``tests/test_oracle_*.py``. Parts without an independent
 pin are marked "parity unpinned" in their module docstring.

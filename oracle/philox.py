@@ -31,6 +31,7 @@ _MASK = (1 << 64) - 1
 DOMAIN_UNIFORM_ROWS = 0      # uniform far-field row sampling
 DOMAIN_WEIGHTED_POOL = 1     # candidate pool of the learned proposal
 DOMAIN_WEIGHTED_KEYS = 2     # Efraimidis-Spirakis keys of the weighted sampler
+DOMAIN_PAPER_SAMPLERS = 3    # keys of the paper's distance and leverage samplers (oracle/samplers.py)
 
 
 def philox4x64_10(counter, key):
