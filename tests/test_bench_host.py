@@ -69,3 +69,29 @@ def test_oracle_stream_over_worker_processes():
     bench.select_workload("c2")
     cb = bench.finish_cpu_baseline(bench.OracleStream(2), 4.0, "test")
     assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] is not None and cb["value"] > 0
+
+
+def test_autotuner_search_order_and_fallback(monkeypatch):
+    """The tuner's coordinate search with the timing mocked: the threshold first (at 96 MB), then the
+    budget at the best threshold; a candidate that fails is recorded and skipped."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    from paper_1409_2802_gb300 import autotune, ffc
+    cost = {(512, 96): 5.0, (1024, 96): 3.0, (2048, 96): 4.0, (1 << 30, 96): 9.0, (1024, 64): 3.5,
+            (1024, 128): 2.5}
+    calls = []
+
+    def fake(points_perm, tree, kernel, stream, reps, precision, qr_big_min_s, qr_l2_budget_mb, **kw):
+        calls.append((qr_big_min_s, qr_l2_budget_mb))
+        if (qr_big_min_s, qr_l2_budget_mb) == (2048, 96):
+            raise ffc.FFCError(ffc.FFC_E_NOMEM, "out of memory")
+        return cost.get((qr_big_min_s, qr_l2_budget_mb), 6.0)
+
+    monkeypatch.setattr(autotune, "_time_call", fake)
+    best = autotune.tune_tree(None, None, None, precision=ffc.MIXED, stream=object())
+    assert calls == [(512, 96), (1024, 96), (2048, 96), (1 << 30, 96), (1024, 64), (1024, 128)]
+    assert (best["qr_big_min_s"], best["qr_l2_budget_mb"], best["ms"]) == (1024, 128, 2.5)
+    assert any("error" in row for row in best["table"])
+    calls.clear()
+    best = autotune.tune_tree(None, None, None, precision=ffc.FP64, stream=object())
+    assert calls == [(1 << 30, 96), (1 << 30, 64), (1 << 30, 128)]
