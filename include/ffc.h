@@ -75,6 +75,18 @@ const char* ffc_last_error(void);
 const char* ffc_version(void);
 
 /*
+ * ffc_set_wait_limit - how many times a bounded device wait polls before it
+ * gives up (the pivoted QR's group barrier of ffc_id, ffc_id_noalloc and
+ * ffc_compress_tree). The paper has no counterpart: this is the control of the
+ * library's failure detection. A wait that runs out ends its QR with
+ * FFC_E_TIMEOUT (returned by ffc_id, per node in ffc_compress_tree) and leaves
+ * the device usable. polls < 0 restores the default (2e7 polls, a second or
+ * more); 0 makes every wait that is not already satisfied give up at once.
+ * Applies to launches enqueued after the call, process-wide. Always FFC_OK.
+ */
+ffc_status ffc_set_wait_limit(int64_t polls);
+
+/*
  * ffc_far_field - list the far field of a source set (§4.1, setup step 3):
  *   T = { j in [0, M) \ [ex_begin, ex_end) : ||Y_j - x_c|| >= xi * radius }.
  * Y_dev: M x d points (dtype). x_c_dev: d doubles, or NULL for "no distance
@@ -200,6 +212,39 @@ ffc_status ffc_id_error(ffc_kernel kernel, const void* Y_dev, int32_t dtype,
                         const int32_t* skel_perm_dev, const double* T_dev, int64_t ldt, int64_t r,
                         double* err_host, void* stream);
 
+/* ---------------- the outgoing representation (§2.1.3) ------------------ */
+
+/*
+ * ffc_skeleton_charges - the skeleton charges of an ID, q~ = P q (§2.1.3,
+ * after eq. e:id-error: the n source charges q of a node become r charges on
+ * its skeleton points, u = K q ~ C P q = C q~). With P = [I_r T] Pi^T as
+ * ffc_id returns it: q~ = q[skel_perm[0:r]] + T q[skel_perm[r:n]].
+ * skel_perm_dev: n int32; T_dev: r x (n - r) doubles, column c at T + c ldt
+ * (ldt >= max(r, 1); may be NULL when r = n); q_dev: n x nrhs doubles, column
+ * j at q + j ldq (ldq >= n); qt_dev: r x nrhs, column j at qt + j ldqt
+ * (ldqt >= r). FP64. Asynchronous.
+ */
+ffc_status ffc_skeleton_charges(const int32_t* skel_perm_dev, const double* T_dev, int64_t ldt, int64_t r, int64_t n,
+                                const double* q_dev, int64_t ldq, int64_t nrhs, double* qt_dev, int64_t ldqt,
+                                void* stream);
+
+/*
+ * ffc_potential - u_i = exp(-log_scale) sum_c K(Y[rows_i], X[cols_c]) w_c:
+ * the kernel sum of §1 (eq. e:sum) over a subset of the sources. With cols =
+ * the skeleton skel_perm[0:r] and w = q~ it is the potential of the outgoing
+ * representation, u ~ C q~ (§2.1.3); with cols_dev = NULL (nc = n) and w = q
+ * it is the direct sum u = K q it approximates. Y_dev: targets (M x d, dtype),
+ * rows_dev: m int64 indices into Y or NULL (rows 0..m-1); X_dev: n x d sources
+ * (dtype); cols_dev: nc int32 indices into X or NULL; w_dev: nc doubles;
+ * u_dev: m doubles. log_scale shifts every kernel value by exp(-log_scale)
+ * (the Laplace kernel's range; 0 for none). FP64 arithmetic. A Laplace
+ * target that coincides with a source gives an infinite value.
+ * Asynchronous.
+ */
+ffc_status ffc_potential(ffc_kernel kernel, const void* Y_dev, int32_t dtype, const int64_t* rows_dev, int64_t m,
+                         const void* X_dev, int64_t n, int32_t d, const int32_t* cols_dev, int64_t nc,
+                         const double* w_dev, double log_scale, double* u_dev, void* stream);
+
 /* ----------------------------- trees ---------------------------------- */
 
 /*
@@ -312,6 +357,33 @@ ffc_status ffc_tree_result_view(const ffc_tree_result* result, ffc_tree_view* vi
 void ffc_tree_result_free(ffc_tree_result* result);
 
 /*
+ * ffc_tree_apply - the potential at every point of a compressed tree from the
+ * nodes' outgoing representations (§2.1.3; the far-field criterion of the
+ * §4.1 setup, per node). Charges q_dev: N doubles in tree order (the same
+ * order as points_perm_dev). For every target y (every point, tree order):
+ *   u(y) = sum over b in IL(y) of sum_j K(y, x~_j) q~_j   (far field)
+ *        + sum over the near leaves of y of K(y, x) q(x), x != y  (near field,
+ *          only with near_field != 0)
+ * where IL(y) holds each node b at level >= min_level whose far field
+ * contains y while no ancestor at level >= min_level has y in its far field;
+ * a leaf reached with no such node on its path is a near leaf. Every source
+ * other than y is counted once. mode FFC_APPLY_SKELETON uses each node's ID
+ * (q~ = P q, x~ its skeleton points; a node whose status is neither FFC_OK
+ * nor FFC_E_TOL_NOT_REACHED is summed from its sources); FFC_APPLY_DIRECT sums
+ * every far node from its sources: the exact value the representation
+ * approximates. The kernel, xi, min_level and s_max are those of the
+ * compression that produced `result` (same tree, same points). qt_dev:
+ * skeleton charges, output node i's r_i values at qt + i (s_max / 2)
+ * (capacity n_out (s_max / 2) doubles; written in skeleton mode, may be NULL
+ * in direct mode). u_dev: N doubles. log_scale as in ffc_potential. FP64
+ * arithmetic. Requires 2^min_level + 2 depth + 2 <= 96. Asynchronous.
+ */
+typedef enum { FFC_APPLY_SKELETON = 0, FFC_APPLY_DIRECT = 1 } ffc_apply_mode;
+ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N, int32_t d, const ffc_tree* tree,
+                          const ffc_tree_result* result, const double* q_dev, int32_t mode, int32_t near_field,
+                          double log_scale, double* qt_dev, double* u_dev, void* stream);
+
+/*
  * Phase timing of ffc_compress_tree (tracing). When enabled on a result,
  * each later ffc_compress_tree call records CUDA events on its stream around
  * every phase of every round and adds the elapsed times (milliseconds) into
@@ -378,9 +450,10 @@ ffc_status ffc_features(ffc_kernel k, const void* Y_dev, int32_t dtype, int64_t 
                         const double* proj_dev, float* feats_dev, void* stream);
 
 /* ffc_mlp_forward - logits_dev[i] (R floats) of the feature rows feats_dev
- * (R x 12 FP32): the proposal's inference pass, whose 128 x 128 product takes
- * FP16 operands (first-layer activations rounded to FP16) and accumulates in
- * FP32 on the tensor cores. Asynchronous. */
+ * (R x 12 FP32): the proposal's inference pass. Its 128 x 128 product runs on
+ * the tensor cores with FP32 accumulation: the FP16 weights times the FP32
+ * first-layer activations, each split into two FP16 parts (hi + lo), so the
+ * activations keep about 2^-22 relative precision. Asynchronous. */
 ffc_status ffc_mlp_forward(const float* params_dev, const float* feats_dev, int64_t R, float* logits_dev,
                            void* stream);
 

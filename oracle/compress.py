@@ -20,6 +20,9 @@ With a learned ``Proposal`` the s rows of each attempt come from
 ``proposal.propose_from_mask`` (network weights over the candidate pool,
 weighted draw without replacement) instead of the uniform sampler; its keys
 do not depend on s, so a larger attempt extends the smaller one as well.
+With ``ranked_rows`` the rows of each attempt are the first s of that list
+instead (a draw made elsewhere and checked on its own, passed in like any
+other random input); everything after the draw is the same.
 """
 from __future__ import annotations
 
@@ -64,7 +67,7 @@ def rank_cap(s_eff: int, n: int, all_rows: bool, r_cap: int) -> int:
 
 
 def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048, xi=1.0,
-                  proposal: Proposal | None = None):
+                  proposal: Proposal | None = None, ranked_rows=None):
     b, c = int(tree.begin[node]), int(tree.count[node])
     far = far_field_mask(Xp, tree.centroid[node], tree.radius[node], xi, b, b + c)
     far_count = int(far.sum())
@@ -74,7 +77,9 @@ def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048,
     tried = []
     while True:
         tried.append(s)
-        if proposal is None:
+        if ranked_rows is not None:
+            rows = np.asarray(ranked_rows, dtype=np.int64)[:s]
+        elif proposal is None:
             rows = sample_uniform_from_mask(far, s, seed, node)
         else:
             rows = propose_from_mask(far, Xp, s, seed, node, tree.centroid[node], tree.radius[node],

@@ -24,10 +24,8 @@ Adam: Kingma & Ba (ICLR 2015), Algorithm 1, with bias-corrected moments.
 Precision reading: the network's weights are stored as an FP32 master copy
 and used in the forward and backward passes rounded to FP16 (round to
 nearest even); ``half_weights`` gives those FP16 values as exact float64
-numbers, and everything after that is FP64 here. The proposal's inference
-pass (``forward(..., h1_half=True)``) also rounds the first hidden layer's
-activations to FP16, the operand precision of its 128 x 128 product; training
-keeps them at full precision.
+numbers, and everything after that is FP64 here: the activations are not
+rounded, in inference or in training.
 """
 from __future__ import annotations
 
@@ -82,18 +80,12 @@ def gelu_prime(z):
     return 0.5 * (1.0 + erf(z / _SQRT2)) + z * _INV_SQRT_2PI * np.exp(-0.5 * z * z)
 
 
-def forward(theta, X, h1_half: bool = False):
-    """Logits o (R,) of the R x 12 feature rows X, and the cache for backward.
-
-    With ``h1_half`` the first hidden layer's activations are rounded to FP16
-    (round to nearest even) before the second layer.
-    """
+def forward(theta, X):
+    """Logits o (R,) of the R x 12 feature rows X, and the cache for backward."""
     p = unpack(theta)
     X = np.asarray(X, dtype=np.float64)
     z1 = X @ p["W1"].T + p["b1"]
     h1 = gelu(z1)
-    if h1_half:
-        h1 = h1.astype(np.float16).astype(np.float64)
     z2 = h1 @ p["W2"].T + p["b2"]
     h2 = gelu(z2)
     o = h2 @ p["w3"] + p["b3"][0]

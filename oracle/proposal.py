@@ -25,8 +25,8 @@ Readings used here (the paper has no learned part):
   that carry it are few: a uniform pool of a few times s rows misses them).
   Optionally a uniform pool of a fixed number P of rows (the uniform sampler
   with s = P, same stream) bounds the cost. The pool does not depend on s.
-* The network gives a logit o_i per pool row (FP16 weights and FP16 first-layer
-  activations, the inference precision); weights w_i = exp(o_i - max o);
+* The network gives a logit o_i per pool row (FP16 weights, FP64 arithmetic
+  here); weights w_i = exp(o_i - max o);
   mixed weights w'_i = 0.9 w_i / mean(w) + 0.1, so every row keeps at least
   a tenth of its uniform weight. s rows are drawn without replacement with
   probabilities proportional to w' by Efraimidis & Spirakis' keys (Inf. Proc.
@@ -124,7 +124,7 @@ def propose_from_mask(far, Y, s, seed, stream_id, x_c, rho, kernel: Kernel, proj
     if pool.size == 0:
         return pool
     F = features(Y, pool, x_c, rho, kernel, proj)
-    o, _ = forward(half_weights(theta32), F, h1_half=True)
+    o, _ = forward(half_weights(theta32), F)
     rows, _ = weighted_select(pool, o, s, seed, stream_id)
     return rows
 

@@ -1,5 +1,6 @@
 // C ABI of libffc (declarations and contracts in include/ffc.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -78,6 +79,10 @@ static int group_size(int64_t s, int64_t n, int64_t elems_per_cta) {
   return (int)std::max<int64_t>(1, g);
 }
 
+static std::atomic<long long> g_wait_limit{SPIN_LIMIT_DEFAULT};
+
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 }  // namespace ffc
 
 using namespace ffc;
@@ -85,6 +90,11 @@ using namespace ffc;
 extern "C" {
 
 const char* ffc_last_error(void) { return g_err; }
+
+ffc_status ffc_set_wait_limit(int64_t polls) {
+  g_wait_limit.store(polls < 0 ? SPIN_LIMIT_DEFAULT : (long long)polls, std::memory_order_relaxed);
+  return FFC_OK;
+}
 
 const char* ffc_version(void) { return "ffc 0.1 (sm_103a)"; }
 

@@ -89,13 +89,14 @@ __device__ __forceinline__ unsigned long long pivot_key(double nrm2, int col) {
   return (b & ~0xFFFFFull) | (unsigned long long)(0xFFFFF - col);
 }
 
-// Thread 0 only: arrive and wait until `target` arrivals. false on timeout.
-__device__ bool group_barrier(unsigned* ctr, unsigned target) {
+// Thread 0 only: arrive and wait until `target` arrivals, polling at most `limit` times.
+// false on timeout.
+__device__ bool group_barrier(unsigned* ctr, unsigned target, long long limit) {
   __threadfence();
   atomicAdd(ctr, 1u);
   long long spins = 0;
   while (ld_acquire_u32(ctr) < target) {
-    if (++spins > SPIN_LIMIT) return false;
+    if (++spins > limit) return false;
     __nanosleep(40);
   }
   __threadfence();
@@ -651,7 +652,7 @@ __device__ __forceinline__ void update_column_vec_chunked(T* __restrict__ A, int
 template <typename T, bool BIG>
 __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
                             double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
-                            int16_t* __restrict__ rcl, QrShared& sh) {
+                            int16_t* __restrict__ rcl, QrShared& sh, long long spin_limit) {
   const int s = it.s, n = it.n;
   T* __restrict__ A = reinterpret_cast<T*>(it.A);
   const int64_t lda = it.lda;
@@ -698,7 +699,7 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
         } else {
           red_publish(it.red + 4 * (k % 3), sh.key, sh.fsum);
         }
-        if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1))) {
+        if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1), spin_limit)) {
           sh.stop = 1;
           sh.status = FFC_E_TIMEOUT;
         } else if (k > 0) {
@@ -898,7 +899,7 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
 template <typename T, bool BIG>
 __global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
 cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
-            const int32_t* __restrict__ cta_off) {
+            const int32_t* __restrict__ cta_off, long long spin_limit) {
   // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries
   // (QR_NCOL_MAX T), recompute list (QR_NCOL_MAX int16), selected flags
   // (QR_NCOL_MAX bytes), Householder vector (s_max T)
@@ -917,7 +918,7 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
     const CpqrItem it = items[a.item];
     if (threadIdx.x == 0) sh.status = FFC_OK;
     __syncthreads();
-    factor_item<T, BIG>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh);
+    factor_item<T, BIG>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh, spin_limit);
     __syncthreads();
   }
 }
@@ -1096,7 +1097,7 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off));
+  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off, wait_limit()));
   return FFC_OK;
 }
 

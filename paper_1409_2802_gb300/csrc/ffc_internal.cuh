@@ -68,8 +68,10 @@ constexpr int SAMPLE_MAX_GRID = 2048;   // sampler CTAs; one scratch slice of M_
 template <typename TP>
 __device__ __forceinline__ double ld_point(const TP* p) { return (double)__ldg(p); }
 
-// Bounded spin limit for waits on other CTAs (about a second or more).
-constexpr long long SPIN_LIMIT = 20000000ll;
+// Bounded spin limit for waits on other CTAs (about a second or more); ffc_set_wait_limit
+// changes it for later launches, wait_limit() reads the current value on the host.
+constexpr long long SPIN_LIMIT_DEFAULT = 20000000ll;
+long long wait_limit();
 
 // ----------------------------------------------------------------------------
 // work items (host-built tables, copied to the device)

@@ -37,8 +37,8 @@ __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erf
 // Inference GELU, z Phi(z) = z erfc(-z / sqrt 2) / 2, with erfc from the rational
 // approximation of Abramowitz & Stegun 7.1.26 (Hastings): for x >= 0,
 // erfc(x) ~ (a1 t + a2 t^2 + ... + a5 t^5) e^{-x^2}, t = 1 / (1 + p x), |error| <= 1.5e-7.
-// Negative z take erfc directly (no cancellation in 1 + erf). The first layer rounds the
-// result to FP16 and the second feeds it to the FP32 logit, both far coarser than 1.5e-7.
+// Negative z take erfc directly (no cancellation in 1 + erf). The GELU's error is then
+// at most 0.75e-7 |z|, about one FP32 rounding of h for |z| near 1.
 __device__ __forceinline__ float gelu_inf(float z) {
   const float x = fabsf(z) * 0.70710678118654752f;
   const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
@@ -274,19 +274,24 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_kernel(const float* _
 // ----------------------------------------------------------------------------
 // inference forward on the tensor cores: the 128 x 128 layer as FP16 x FP16
 // products with FP32 accumulation (mma.sync m16n8k16); the first layer (K = 12)
-// on the FP32 pipes, its activations rounded to FP16 as the product's operand
+// on the FP32 pipes. The FP32 activations h1 enter the product as two FP16
+// planes, hi = fp16(h1) and lo = fp16(h1 - hi), so W2 h1 = W2 hi + W2 lo keeps
+// h1 to about 2^-22 relative (the FP16 weights are exact in both products):
+// the logits are those of FP32 activations, not of FP16-rounded ones.
 
-constexpr int TC_ROWS = 128;       // rows per tile: 8 warps x 16
+constexpr int TC_ROWS = 64;        // rows per tile: 4 row groups of 16, each split over two warps by units
 constexpr int HS = NH + 8;         // FP16 row stride in shared memory (272 B: ldmatrix rows hit distinct banks)
 
 struct TcSmem {
   alignas(16) __half W2[NH * HS];        // W2[j][k]: the B operand (k x n, "col")
-  alignas(16) __half H1[TC_ROWS * HS];   // h1[r][k]: the A operand (row-major)
+  alignas(16) __half H1[TC_ROWS * HS];   // hi plane of h1[r][k]: the A operand (row-major)
+  alignas(16) __half H1L[TC_ROWS * HS];  // lo plane
   alignas(16) float W1T[NF * NH];
   alignas(16) float X[TC_ROWS * NF];
   alignas(16) float b1[NH];
   alignas(16) float b2[NH];
   alignas(16) float w3[NH];
+  alignas(16) float part[2][TC_ROWS];    // partial logits over units [0, 64) and [64, 128)
   float b3;
 };
 
@@ -325,6 +330,8 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
 #pragma unroll
   for (int kk = 0; kk < NF; ++kk) w1[kk] = S.W1T[kk * NH + j];
   const float b1j = S.b1[j];
+  // layer 2: warp w takes rows 16 (w & 3) .. + 15 and units 64 (w >> 2) .. + 63 (8 n-tiles of 8)
+  const int mrow = 16 * (warp & 3), nhalf = warp >> 2, nbase = 64 * nhalf;
   const int64_t tiles = (R + TC_ROWS - 1) / TC_ROWS;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t row0 = t * TC_ROWS;
@@ -348,33 +355,40 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
         za = fmaf(w1[4 * q + 2], a.z, za); zb = fmaf(w1[4 * q + 2], b.z, zb);
         za = fmaf(w1[4 * q + 3], a.w, za); zb = fmaf(w1[4 * q + 3], b.w, zb);
       }
-      S.H1[r * HS + j] = __float2half_rn(gelu_inf(za));
-      S.H1[(r + 2) * HS + j] = __float2half_rn(gelu_inf(zb));
+      const float ga = gelu_inf(za), gb = gelu_inf(zb);
+      const __half ha = __float2half_rn(ga), hb = __float2half_rn(gb);
+      S.H1[r * HS + j] = ha;
+      S.H1[(r + 2) * HS + j] = hb;
+      S.H1L[r * HS + j] = __float2half_rn(ga - __half2float(ha));
+      S.H1L[(r + 2) * HS + j] = __float2half_rn(gb - __half2float(hb));
     }
     __syncthreads();
-    // layer 2: warp w, rows 16 w .. 16 w + 15, all 128 units (16 n-tiles of 8)
-    float acc[16][4];
+    float acc[8][4];
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) { acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f; }
+    for (int nt = 0; nt < 8; ++nt) { acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f; }
     const int q = lane >> 3;   // ldmatrix: the matrix this lane addresses a row of
 #pragma unroll
     for (int ks = 0; ks < NH / 16; ++ks) {
-      unsigned a0, a1, a2, a3;
-      ldsm_x4(&S.H1[(16 * warp + (lane & 15)) * HS + ks * 16 + (lane >> 4) * 8], a0, a1, a2, a3);
+      const int aoff = (mrow + (lane & 15)) * HS + ks * 16 + (lane >> 4) * 8;
+      unsigned a0, a1, a2, a3, l0, l1, l2, l3;
+      ldsm_x4(&S.H1[aoff], a0, a1, a2, a3);
+      ldsm_x4(&S.H1L[aoff], l0, l1, l2, l3);
 #pragma unroll
-      for (int np = 0; np < 8; ++np) {
+      for (int np = 0; np < 4; ++np) {
         unsigned b0, b1, b2, b3;
-        ldsm_x4(&S.W2[(np * 16 + (q >> 1) * 8 + (lane & 7)) * HS + ks * 16 + (q & 1) * 8], b0, b1, b2, b3);
+        ldsm_x4(&S.W2[(nbase + np * 16 + (q >> 1) * 8 + (lane & 7)) * HS + ks * 16 + (q & 1) * 8], b0, b1, b2, b3);
+        mma_16816(acc[2 * np], l0, l1, l2, l3, b0, b1);
+        mma_16816(acc[2 * np + 1], l0, l1, l2, l3, b2, b3);
         mma_16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
         mma_16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
       }
     }
-    // epilogue: h2 = GELU(z2 + b2), o = w3 . h2 + b3; lane holds rows lane/4 and lane/4 + 8,
-    // columns 8 nt + 2 (lane % 4) + {0, 1}
+    // epilogue: h2 = GELU(z2 + b2), the warp's share of w3 . h2; lane holds rows lane/4 and
+    // lane/4 + 8 of its row group, columns nbase + 8 nt + 2 (lane % 4) + {0, 1}
     float po0 = 0.0f, po1 = 0.0f;
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const int c = nt * 8 + 2 * (lane & 3);
+    for (int nt = 0; nt < 8; ++nt) {
+      const int c = nbase + nt * 8 + 2 * (lane & 3);
       po0 = fmaf(S.w3[c], gelu_inf(acc[nt][0] + S.b2[c]), po0);
       po0 = fmaf(S.w3[c + 1], gelu_inf(acc[nt][1] + S.b2[c + 1]), po0);
       po1 = fmaf(S.w3[c], gelu_inf(acc[nt][2] + S.b2[c]), po1);
@@ -385,10 +399,11 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
     po1 += __shfl_xor_sync(0xffffffffu, po1, 1);
     po1 += __shfl_xor_sync(0xffffffffu, po1, 2);
     if ((lane & 3) == 0) {
-      const int64_t ra = row0 + 16 * warp + (lane >> 2), rb = ra + 8;
-      if (ra < R) logits[ra] = po0 + S.b3;
-      if (rb < R) logits[rb] = po1 + S.b3;
+      S.part[nhalf][mrow + (lane >> 2)] = po0;
+      S.part[nhalf][mrow + (lane >> 2) + 8] = po1;
     }
+    __syncthreads();
+    if (tid < TC_ROWS && row0 + tid < R) logits[row0 + tid] = (S.part[0][tid] + S.part[1][tid]) + S.b3;
   }
 }
 
@@ -874,7 +889,7 @@ static ffc_status launch_mlp_forward_f32(const float* params, const float* feats
   return FFC_OK;
 }
 
-// inference forward: the 128 x 128 layer on the tensor cores (FP16 operands)
+// inference forward: the 128 x 128 layer on the tensor cores (FP16 weights, two FP16 planes of h1)
 ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R, float* logits, cudaStream_t st) {
   if (R <= 0) return FFC_OK;
   const size_t smem = sizeof(TcSmem);

@@ -3,6 +3,7 @@
 // launches; their scratch lives in one file-scope device array instead of
 // memory obtained from cudaMallocAsync.
 #include <algorithm>
+#include <atomic>
 
 #include "ffc_internal.cuh"
 
@@ -39,8 +40,9 @@ static_assert(SCRATCH_BYTES <= (size_t)1 << 20, "no-allocation scratch must stay
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device, taken once per device.
-static char* g_scratch_addr[64] = {nullptr};
+// Device address of g_noalloc_scratch per device, taken once per device. Host threads making
+// their first call on a device at the same time may both look it up; they store the same value.
+static std::atomic<char*> g_scratch_addr[64];
 
 struct Scalars {
   unsigned barrier;
@@ -78,13 +80,15 @@ ffc_status scratch_base(char** out) {
     set_error("ffc_id_noalloc: device ordinal %d out of range", dev);
     return FFC_E_INVALID;
   }
-  if (!g_scratch_addr[dev]) {
+  char* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_scratch_addr[dev] = static_cast<char*>(p);
+    addr = static_cast<char*>(p);
+    g_scratch_addr[dev].store(addr, std::memory_order_release);
   }
-  *out = g_scratch_addr[dev];
+  *out = addr;
   return FFC_OK;
 }
 
@@ -119,6 +123,10 @@ extern "C" ffc_status ffc_id_noalloc(void* K_dev, int64_t s, int64_t n, int64_t 
   const int s_launch = (int)std::max<int64_t>(s, 1);
   const int cap = cpqr_max_ctas(precision, s_launch);
   FFC_REQUIRE(cap > 0, "ffc_id_noalloc: the QR kernel cannot be resident on this device");
+  // each CTA of the group owns at most a fixed number of columns (their norms live in its shared memory)
+  FFC_REQUIRE(cpqr_min_group(n) <= std::min<int>(cap, (int)NA_MAX_GROUP),
+              "ffc_id_noalloc: n = %lld needs %d resident QR blocks, this device holds %d", (long long)n,
+              cpqr_min_group(n), std::min<int>(cap, (int)NA_MAX_GROUP));
   const int g = std::min<int>({cap, (int)NA_MAX_GROUP, std::max(cpqr_min_group(n), group_size_noalloc(s, n))});
   const int rc_cap = (int)std::max<int64_t>(kcap, 1);
 

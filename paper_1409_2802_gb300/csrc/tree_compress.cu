@@ -622,6 +622,12 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
 
 }  // namespace
 
+namespace ffc {
+// The parameters the result was computed with, and the heap id of its first compressed node.
+const ffc_params* tree_result_params(const ffc_tree_result* r) { return &r->p; }
+int64_t tree_result_first_node(const ffc_tree_result* r) { return r->node_h.empty() ? 0 : r->node_h[0]; }
+}  // namespace ffc
+
 extern "C" {
 
 ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t N, int32_t d, const ffc_tree* tree,

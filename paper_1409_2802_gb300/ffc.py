@@ -36,7 +36,8 @@ EXPORTS = (
     "ffc_id_error", "ffc_tree_depth", "ffc_build_tree", "ffc_compress_tree", "ffc_tree_result_view",
     "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
     "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
-    "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched",
+    "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched", "ffc_set_wait_limit",
+    "ffc_skeleton_charges", "ffc_potential", "ffc_tree_apply",
 )
 MLP_PARAMS = 18305
 N_FEATURES = 12
@@ -134,6 +135,10 @@ def lib() -> ctypes.CDLL:
     L.ffc_adam_step.argtypes = [vp, vp, vp, vp, i64, i64, dbl, dbl, dbl, dbl, vp]
     L.ffc_leverage.argtypes = [vp, i64, i64, i64, dbl, i64, vp, vp, pi64, vp]
     L.ffc_leverage_batched.argtypes = [i32, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]
+    L.ffc_set_wait_limit.argtypes = [i64]
+    L.ffc_skeleton_charges.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
+    L.ffc_potential.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i64, vp, dbl, vp, vp]
+    L.ffc_tree_apply.argtypes = [vp, i32, i64, i32, ctypes.POINTER(c_tree), vp, vp, i32, i32, dbl, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
             getattr(L, name).restype = ctypes.c_int
@@ -173,6 +178,11 @@ def _dev(t: torch.Tensor, name: str):
 
 def version() -> str:
     return lib().ffc_version().decode()
+
+
+def ffc_set_wait_limit(polls: int) -> None:
+    """Polls of a bounded device wait before it gives up (< 0: the library's default)."""
+    _check(lib().ffc_set_wait_limit(int(polls)))
 
 
 def ffc_far_field(Y, x_c=None, radius=0.0, xi=1.0, ex_begin=0, ex_end=0, stream=None):
@@ -341,6 +351,53 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
     return res
+
+
+APPLY_SKELETON, APPLY_DIRECT = 0, 1
+
+
+def ffc_skeleton_charges(skel, T, q, stream=None):
+    """q~ = P q for an ID (skel int32[n], T (r x (n - r)) float64 as ffc_id returns it); q: (n,) or (n, nrhs)."""
+    _dev(skel, "skel"), _dev(q, "q")
+    n = skel.numel()
+    r = T.shape[0]
+    Tc = T.t().contiguous()                       # column c of T at Tc + c r
+    qc = q.reshape(n, -1).t().contiguous()        # column j of q at qc + j n
+    nrhs = qc.shape[0]
+    qt = torch.empty((nrhs, max(r, 1)), dtype=torch.float64, device=q.device)
+    _check(lib().ffc_skeleton_charges(_ptr(skel), _ptr(Tc) if r < n else None, max(r, 1), r, n, _ptr(qc), max(n, 1),
+                                      nrhs, _ptr(qt), max(r, 1), _stream(stream)))
+    out = qt[:, :r].t()
+    return out.reshape(r) if q.dim() == 1 else out
+
+
+def ffc_potential(kernel: Kernel, Y, X, w, rows=None, cols=None, log_scale=0.0, stream=None):
+    """u_i = exp(-log_scale) sum_c K(Y[rows_i], X[cols_c]) w_c (cols None: all of X)."""
+    _dev(Y, "Y"), _dev(X, "X"), _dev(w, "w")
+    M, d = Y.shape
+    n = X.shape[0]
+    m = rows.numel() if rows is not None else M
+    nc = cols.numel() if cols is not None else n
+    u = torch.empty(max(m, 1), dtype=torch.float64, device=Y.device)
+    _check(lib().ffc_potential(kernel.c_struct(), _ptr(Y), _dtype_code(Y), _ptr(rows), m, _ptr(X), n, d, _ptr(cols),
+                               nc, _ptr(w), float(log_scale), _ptr(u), _stream(stream)))
+    return u[:m]
+
+
+def ffc_tree_apply(points_perm, tree: "DeviceTree", result: "TreeResult", q, mode=APPLY_SKELETON, near_field=True,
+                   log_scale=0.0, s_max=2048, stream=None):
+    """Potential at every point (tree order) from the compressed tree's representations; returns (u, qt) with
+    qt the skeleton charges (n_out x s_max/2, node i's first r_i entries), None in direct mode."""
+    _dev(points_perm, "points_perm"), _dev(q, "q")
+    N, d = points_perm.shape
+    n_out = int(result.view().n_out)
+    qt = torch.zeros((n_out, s_max // 2), dtype=torch.float64, device=q.device) if mode == APPLY_SKELETON else None
+    u = torch.empty(N, dtype=torch.float64, device=q.device)
+    tr = tree.c_struct()
+    _check(lib().ffc_tree_apply(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr), result.handle,
+                                _ptr(q), int(mode), 1 if near_field else 0, float(log_scale), _ptr(qt), _ptr(u),
+                                _stream(stream)))
+    return u, qt
 
 
 _TORCH_DTYPES = {"int32": torch.int32, "int64": torch.int64, "float64": torch.float64}

@@ -18,6 +18,7 @@ from oracle import interp as o_interp
 from oracle import kernels as o_kernels
 from oracle import sampling as o_sampling
 from oracle.cpqr import cpqr as o_cpqr
+from parity import fp64_error_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -177,7 +178,7 @@ def _check_id(Ko, r_max, tol, ok=None, Y=None, X=None, gk=None):
     if ok is not None:
         e_g = ffc.ffc_id_error(gk, cu(Y), cu(X), cu(skel.astype(np.int32)), cu(T), r)
         e_o = o_interp.full_block_error(ok, Y, X, ref["skel_perm"], ref["T"])
-        assert abs(e_g - e_o) <= 1e-10, (e_g, e_o)
+        assert fp64_error_ok(e_g, e_o), (e_g, e_o, abs(e_g - e_o))
     return r, st
 
 

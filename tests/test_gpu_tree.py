@@ -14,6 +14,7 @@ from oracle import compress as o_compress
 from oracle import interp as o_interp
 from oracle import kernels as o_kernels
 from oracle import tree as o_tree
+from parity import check_learned_node, far_rows_subset, fp64_error_ok, node_id
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +48,7 @@ def test_build_tree_matches_oracle(N, d, leaf):
     np.testing.assert_allclose(t_g.radius.cpu().numpy(), t_o.radius, rtol=1e-13)
 
 
-def _compare_nodes(out, t_o, Pp, kernel_o, tol, nodes, s0, s_max, seed=0, check_error=True):
+def _compare_nodes(out, t_o, Pp, kernel_o, tol, nodes, s0, s_max, seed=0, check_error=True, subset=False):
     index = {int(nd): i for i, nd in enumerate(out["node"])}
     for node in nodes:
         i = index[node]
@@ -62,17 +63,25 @@ def _compare_nodes(out, t_o, Pp, kernel_o, tol, nodes, s0, s_max, seed=0, check_
         assert r == ref.rank, (node, r, ref.rank)
         assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
         n = int(t_o.count[node])
-        skel = out["skel"][out["skel_off"][i]: out["skel_off"][i] + n].astype(np.int64)
-        T = out["T"][out["T_off"][i]: out["T_off"][i] + r * (n - r)].reshape(n - r, r).T if r else np.zeros((0, n))
+        skel, T, r = node_id(out, i, n)
         P_g = o_interp.assemble_P(skel, T, n)
         assert np.array_equal(P_g[:, skel[:r]], np.eye(r))      # P contains I_r
         if check_error and r > 0:
             b = int(t_o.begin[node])
-            from oracle.sampling import far_field_mask
-            far = far_field_mask(Pp, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n)
+            if subset:
+                far = far_rows_subset(Pp, t_o, node)
+            else:
+                from oracle.sampling import far_field_mask
+                far = far_field_mask(Pp, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n)
             e_g = o_interp.full_block_error(kernel_o, Pp[far], Pp[b:b + n], skel, T)
             e_o = o_interp.full_block_error(kernel_o, Pp[far], Pp[b:b + n], ref.skel_perm, ref.T)
-            assert abs(e_g - e_o) <= 1e-10 + 1e-6 * e_o, (node, e_g, e_o)
+            assert fp64_error_ok(e_g, e_o), (node, e_g, e_o, abs(e_g - e_o))
+            # the two interpolation operators themselves: ||K'(:,J)(P_g - P_o)|| small against ||K'||
+            Kn, _ = o_kernels.kernel_block(kernel_o, Pp[rows], Pp[b:b + n])
+            P_o = o_interp.assemble_P(ref.skel_perm, ref.T, n)
+            if np.array_equal(skel[:r], ref.skel_perm[:r]):
+                dP = np.linalg.norm(Kn[:, skel[:r]] @ (P_g - P_o)) / np.linalg.norm(Kn)
+                assert dP <= 1e-12, (node, dP)
 
 
 def test_compress_small_tree_every_node():
@@ -120,15 +129,14 @@ def test_compress_full_size_gaussian_d16():
     assert np.all(out["rank"] <= np.maximum(cap, out["s"]))
     g = np.random.default_rng(0)
     nodes = sorted(g.choice(out["node"], 12, replace=False).tolist())
+    # full-block errors on a far-field subset of about 4,096 rows per node, for both IDs
     _compare_nodes(out, t_o, Pp, o_kernels.Kernel(o_kernels.GAUSSIAN, h=2.0), 1e-6, nodes, 128, 2048,
-                   check_error=False)
+                   subset=True)
 
 
 def test_compress_tree_learned_sampler_matches_oracle():
-    """Learned sampler, FP64: nodes whose drawn rows equal the oracle's (the FP32
-    logits may swap rows whose keys tie within their rounding) must have the
-    oracle's ID; every node's rows are distinct far-field rows."""
-    from oracle.sampling import far_field_mask
+    """Learned sampler, FP64, every node: the drawn rows are the oracle's best keys up to the
+    rounding of the FP32 logits, and the ID on those rows is the oracle's."""
     P = workloads.gaussian_mixture(N=4096, d=4, k=4, seed=3)
     t_o, t_g = _build_both(P, 256)
     Pp = P[t_o.perm]
@@ -142,21 +150,9 @@ def test_compress_tree_learned_sampler_matches_oracle():
     out = ffc.tree_result_to_host(res)
     prop = o_compress.Proposal(theta, proj)
     nodes = [i for i in range(t_o.n_nodes) if t_o.level[i] >= 2]
-    same = 0
-    for i, node in enumerate(out["node"]):
-        node = int(node)
-        b, n = int(t_o.begin[node]), int(t_o.count[node])
-        s = int(out["s"][i])
-        rows = out["rows"][out["rows_off"][i]: out["rows_off"][i] + s]
-        far = far_field_mask(Pp, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n)
-        assert np.unique(rows).size == s and np.all(far[rows])
-        ref = o_compress.compress_node(Pp, t_o, node, ko, 1e-6, 0, 32, 512, proposal=prop)
-        if ref.s != s or not np.array_equal(rows, ref.rows):
-            continue
-        same += 1
-        assert int(out["status"][i]) == ref.status and int(out["rank"][i]) == ref.rank, node
-        assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
-    assert same >= 0.8 * len(nodes), (same, len(nodes))
+    assert list(out["node"]) == nodes
+    swapped = sum(check_learned_node(out, i, Pp, t_o, ko, prop, 1e-6, 32, 512) for i in range(len(nodes)))
+    print(f"{len(nodes)} nodes checked, {swapped} rows swapped inside the key margin")
 
 
 def test_qr_launch_shape_and_autotuner():

@@ -26,6 +26,7 @@ from oracle import interp as o_interp
 from oracle import kernels as o_kernels
 from oracle import tree as o_tree
 from oracle.sampling import far_field_mask
+from parity import check_learned_node, far_rows_subset, fp64_error_ok, node_id
 
 pytestmark = pytest.mark.gpu
 
@@ -94,24 +95,12 @@ def _invariants(out, t_o):
         assert np.array_equal(np.sort(skel), np.arange(n[i])), nodes[i]
 
 
-def _rows_subset(Pp64, t_o, node, k_near=2048, k_uniform=2048, seed=0):
-    """Far-field rows nearest to the node centroid plus a seeded uniform pick of the rest."""
-    b, n = int(t_o.begin[node]), int(t_o.count[node])
-    far = np.flatnonzero(far_field_mask(Pp64, t_o.centroid[node], t_o.radius[node], 1.0, b, b + n))
-    dist = np.sum((Pp64[far] - t_o.centroid[node]) ** 2, axis=1)
-    order = np.argsort(dist, kind="stable")
-    near = far[order[:k_near]]
-    rest = far[order[k_near:]]
-    pick = np.random.default_rng(seed + node).choice(rest, min(k_uniform, rest.size), replace=False) \
-        if rest.size else rest
-    return np.sort(np.concatenate([near, pick]))
+def _rows_subset(Pp64, t_o, node):
+    return far_rows_subset(Pp64, t_o, node)
 
 
 def _id_of(out, i, n):
-    r = int(out["rank"][i])
-    skel = out["skel"][out["skel_off"][i]: out["skel_off"][i] + n].astype(np.int64)
-    T = out["T"][out["T_off"][i]: out["T_off"][i] + r * (n - r)].reshape(n - r, r).T if r else np.zeros((0, n))
-    return skel, T, r
+    return node_id(out, i, n)
 
 
 def _compare(w, out, ko, nodes, precision):
@@ -135,7 +124,7 @@ def _compare(w, out, ko, nodes, precision):
             assert int(out["status"][i]) == ref.status, node
             assert r == ref.rank, (node, r, ref.rank)
             assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10, node
-            assert abs(e_g - e_o) <= 1e-10 + 1e-6 * e_o, (node, e_g, e_o)
+            assert fp64_error_ok(e_g, e_o), (node, e_g, e_o, abs(e_g - e_o))
         else:
             assert abs(e_g - e_o) <= max(1e-6, 1e-4 * e_o), (node, e_g, e_o)
 
@@ -178,10 +167,8 @@ def test_compress_d1000_fp32_full_size(d1000, precision):
 @pytest.mark.parametrize("which", ["d128_laplace", "d1000"])
 def test_compress_learned_sampler_full_size(d128, d1000, which):
     """Learned sampler with a seeded (untrained) network: every node's rows are
-    distinct far-field rows; sampled leaves whose drawn rows equal the oracle's
-    have the oracle's rank and residual. The draw is compared as a set: rows whose
-    keys differ by less than the rounding of the FP32 logits may come in either
-    order, and a row permutation of the block leaves its pivoted QR unchanged."""
+    distinct far-field rows; on sampled leaves the draw is the oracle's best keys up
+    to the FP32 logits' rounding, and the ID on the drawn rows is the oracle's."""
     if which == "d128_laplace":
         w, kg, ko = d128, ffc.Kernel(ffc.LAPLACE), o_kernels.Kernel(o_kernels.LAPLACE)
     else:
@@ -206,16 +193,10 @@ def test_compress_learned_sampler_full_size(d128, d1000, which):
         far = far_field_mask(w.Pp64, w.t_o.centroid[node], w.t_o.radius[node], 1.0, b, b + n)
         assert np.unique(rows).size == s and np.all(far[rows]), node
     prop = o_compress.Proposal(theta, proj)
-    same = 0
-    leaves = _deep_nodes(w.t_o, 4, (w.t_o.depth,), seed=31)
-    for node in leaves:
+    swapped = 0
+    for node in _deep_nodes(w.t_o, 4, (w.t_o.depth,), seed=31):
         i = index[node]
-        ref = o_compress.compress_node(w.Pp64, w.t_o, node, ko, TOL, 0, S0, S_MAX, proposal=prop)
-        s = int(out["s"][i])
-        rows = out["rows"][out["rows_off"][i]: out["rows_off"][i] + s]
-        if ref.s != s or not np.array_equal(np.sort(rows), np.sort(ref.rows)):
-            continue
-        same += 1
-        assert int(out["status"][i]) == ref.status and int(out["rank"][i]) == ref.rank, node
-        assert abs(out["r22_rel"][i] - ref.r22_rel) <= 1e-10
-    assert same >= 2, (same, leaves)
+        swapped += check_learned_node(out, i, w.Pp64, w.t_o, ko, prop, TOL, S0, S_MAX,
+                                      err_rows=_rows_subset(w.Pp64, w.t_o, node))
+    print(f"4 leaves checked, {swapped} rows swapped inside the key margin")
+

@@ -192,16 +192,3 @@ def test_leverage_targets_of_exact_low_rank_block():
     lev = np.sum(Q * Q, axis=1)
     assert abs(t.sum() - 1.0) < 1e-12
     assert np.max(np.abs(t - lev / 5)) < 1e-12
-
-
-def test_half_activations_round_only_the_hidden_layer():
-    theta, X, _, _ = _small_problem(seed=8, R=50)
-    o_full, cache = mlp.forward(theta, X)
-    o_half, cache_h = mlp.forward(theta, X, h1_half=True)
-    h1 = cache[2]
-    assert np.array_equal(cache_h[2], h1.astype(np.float16).astype(np.float64))
-    # FP16 rounding of h1 moves o by at most sum_k |w3 . W2[:, k]| |dh1_k|, dh1 <= 2^-11 |h1|
-    p = mlp.unpack(theta)
-    dz2 = np.abs(h1) * 2.0 ** -11 @ np.abs(p["W2"]).T
-    bound = (np.abs(p["w3"]) * 1.13) @ dz2.T      # |GELU'| <= 1.13
-    assert np.all(np.abs(o_half - o_full) <= bound + 1e-12)

@@ -78,6 +78,23 @@ def test_noalloc_matches_ffc_id_on_two_calls_in_a_row():
     assert first[0][1] == 64 and first[0][0] == ffc.FFC_OK
 
 
+def test_noalloc_at_its_stated_limits():
+    """The largest problem the fixed scratch holds, n = FFC_NOALLOC_MAX_COLS columns, rank cap
+    FFC_NOALLOC_MAX_RANK and s = 2048 rows (every region of the scratch at its full size), and the
+    same width with a single row, against ffc_id, twice in a row."""
+    n, r_max = 16384, 256
+    K = workloads.random_matrix(2048, n, seed=12, decay=0.97)
+    ref = _run("ffc_id", K, r_max, 0.0)
+    assert ref[1] == r_max
+    for _ in range(2):
+        _same(ref, _run("ffc_id_noalloc", K, r_max, 0.0), K)
+    K1 = workloads.random_matrix(1, n, seed=13)
+    ref1 = _run("ffc_id", K1, 4, 0.0)
+    assert ref1[1] == 1
+    for _ in range(2):
+        _same(ref1, _run("ffc_id_noalloc", K1, 4, 0.0), K1)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     rank, r22 = ctypes.c_int64(0), ctypes.c_double(0.0)
     n = 16385                                                        # one column past FFC_NOALLOC_MAX_COLS
