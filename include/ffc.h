@@ -291,7 +291,7 @@ typedef struct {
   double tol;          /* relative tolerance on ||R22||_F / ||K'||_F (1e-6) */
   double xi;           /* far-field separation (1.0) */
   uint64_t seed;       /* sampling seed; the stream id of a node is its heap id */
-  int32_t sampler;     /* ffc_sampler: FFC_SAMPLE_UNIFORM (0) or FFC_SAMPLE_LEARNED (1) */
+  int32_t sampler;     /* ffc_sampler */
   int32_t pool_rows;   /* learned: 0 = the whole far field is the candidate pool, else a
                           uniform pool of pool_rows >= s_max rows */
   const double* proj_dev;   /* learned: 8 x d random directions of the projection features */
@@ -305,9 +305,18 @@ typedef struct {
   int32_t qr_l2_budget_mb;
 } ffc_params;
 
-/* Row sampler of a tree compression: uniform (§2.2) or the learned proposal
- * (ffc_propose_rows, same seed and stream id). */
-typedef enum { FFC_SAMPLE_UNIFORM = 0, FFC_SAMPLE_LEARNED = 1 } ffc_sampler;
+/* Row sampler of a tree compression: uniform (§2.2), the learned proposal
+ * (ffc_propose_rows, same seed and stream id), or one of the paper's samplers
+ * of §4.1.3 over the node's whole far field (ffc_sample_paper with the far
+ * field in ascending order as the candidates, same seed, stream id = node):
+ * distance, inverse distance, nearest neighbours. */
+typedef enum {
+  FFC_SAMPLE_UNIFORM = 0,
+  FFC_SAMPLE_LEARNED = 1,
+  FFC_SAMPLE_DISTANCE = 2,
+  FFC_SAMPLE_INV_DISTANCE = 3,
+  FFC_SAMPLE_NEAREST = 4
+} ffc_sampler;
 
 /*
  * Compression of every node at level >= min_level. For a node with
@@ -486,6 +495,50 @@ ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int6
                             const double* proj_dev, const float* params_dev, int64_t pool_rows, int64_t s,
                             uint64_t seed, uint64_t stream_id, int64_t* rows_dev, int64_t* s_out_host,
                             int64_t* far_count_host, void* stream);
+
+/*
+ * The paper's other row samplers (§4.1.3, compared there with uniform
+ * sampling; the heuristics of §3), for comparison with the learned proposal.
+ *   FFC_DRAW_DISTANCE      probability proportional to ||y - x_c||
+ *   FFC_DRAW_INV_DISTANCE  probability proportional to 1 / ||y - x_c|| (rows
+ *                          near the sources carry the block, §3)
+ *   FFC_DRAW_NEAREST       deterministic: the candidates closest to the
+ *                          node's sources (squared distance to the nearest
+ *                          source, FP64; ties to the lower position)
+ * The weighted draws are without replacement by Efraimidis & Spirakis' keys
+ * ln(u_i) / w_i, u_i the unit double (top 53 bits + 1/2) 2^-53 of draw i
+ * (i = candidate position) of stream (seed, stream_id, domain 3), Philox
+ * layout as in ffc_sample_rows; the min(s, P) largest keys win, in key order,
+ * ties to the lower position (a size-s draw is a prefix of the size-2s draw).
+ */
+typedef enum { FFC_DRAW_DISTANCE = 0, FFC_DRAW_INV_DISTANCE = 1, FFC_DRAW_NEAREST = 2 } ffc_paper_sampler;
+
+/*
+ * ffc_sample_paper - s of the P candidates cand_dev (int64 rows of Y_dev,
+ * M x d, dtype) by one of the samplers above. x_c_dev: d doubles (distance
+ * samplers); X_dev: the node's n sources (n x d, dtype; nearest neighbours).
+ * rows_dev: capacity min(s, P). min(s, P) <= FFC_MAX_DRAW when P > 16384.
+ * Distances in FP64. Asynchronous.
+ */
+ffc_status ffc_sample_paper(int32_t sampler, const void* Y_dev, int32_t dtype, int32_t d, const int64_t* cand_dev,
+                            int64_t P, const double* x_c_dev, const void* X_dev, int64_t n, int64_t s, uint64_t seed,
+                            uint64_t stream_id, int64_t* rows_dev, void* stream);
+
+/*
+ * ffc_sample_leverage - leverage sampling (§4.1.3 "Leverage sampling"; §3,
+ * Def. "Statistical Leverage"): s rows of the full far-field block K (m x n
+ * FP64, column-major, ld ldk; row i stands for candidate cand_dev[i], or i
+ * when cand_dev is NULL) drawn with probabilities proportional to their
+ * leverage scores at the eps-rank of K (ffc_leverage), over the rows with a
+ * positive score; Efraimidis-Spirakis keys as above, i = the row's position
+ * among the rows with a positive score. n <= 1024. rows_dev: capacity
+ * min(s, m). s_out_host: rows drawn; rank_host: the eps-rank.
+ * FFC_E_TOL_NOT_REACHED (soft) if the eigen-solver did not converge.
+ * Synchronises.
+ */
+ffc_status ffc_sample_leverage(const double* K_dev, int64_t m, int64_t n, int64_t ldk, const int64_t* cand_dev,
+                               double eps, int64_t s, uint64_t seed, uint64_t stream_id, int64_t* rows_dev,
+                               int64_t* s_out_host, int64_t* rank_host, void* stream);
 
 /*
  * ffc_mlp_loss_grad - loss and gradient of the proposal on a batch of nodes:

@@ -65,7 +65,7 @@ ffc_status ffc_sample_weighted(const int64_t* pool_dev, const float* logits_dev,
   cudaStream_t st = as_stream(stream);
   SelectItem* item = nullptr;
   FFC_CUDA(cudaMallocAsync((void**)&item, sizeof(SelectItem), st));
-  SelectItem h;
+  SelectItem h{};
   h.pool = pool_dev; h.count = nullptr; h.P = P; h.logits = logits_dev; h.s = s; h.stream_id = stream_id;
   h.rows_out = rows_dev; h.s_out = nullptr; h.keys = nullptr;
   FFC_CUDA(cudaMemcpyAsync(item, &h, sizeof(h), cudaMemcpyHostToDevice, st));
@@ -116,7 +116,7 @@ ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int6
   FeatItem hf;
   hf.rows = pool; hf.count = p_count; hf.cap = cap; hf.out_begin = 0; hf.x_c = x_c_dev;
   hf.radius = nullptr; hf.radius_host = radius;
-  SelectItem hp;
+  SelectItem hp{};
   hp.pool = pool; hp.count = p_count; hp.P = cap; hp.logits = logits; hp.s = s; hp.stream_id = stream_id;
   hp.rows_out = rows_dev; hp.s_out = s_sel; hp.keys = nullptr;
   FFC_CUDA(cudaMemcpyAsync(fitem, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));

@@ -170,6 +170,19 @@ struct SelectItem {
   int64_t* rows_out;     // capacity s
   int64_t* s_out;        // device: rows written (may be NULL)
   uint64_t* keys;        // capacity P: sort keys kept between passes, or NULL (recomputed)
+  const uint64_t* given; // or: ascending sort keys per pool position, computed elsewhere (logits unused)
+};
+
+// A candidate pool whose sort keys the paper's samplers compute (csrc/samplers.cu).
+struct KeyItem {
+  const int64_t* pool;   // candidate rows
+  const int64_t* count;  // device pool size, or NULL: cap
+  int64_t cap;
+  const double* x_c;     // distance samplers: the node centre (d doubles)
+  int64_t src_begin;     // nearest neighbours: the node's sources are rows [src_begin, src_begin + src_n) of X
+  int64_t src_n;
+  uint64_t stream_id;
+  uint64_t* keys;        // capacity cap: ascending sort keys
 };
 
 // ----------------------------------------------------------------------------
@@ -280,6 +293,9 @@ ffc_status launch_far_features_tiled(ffc_kernel k, const void* Y, int dtype, int
                                      const FarItem* items_dev, const FeatItem* fitems_dev, int n_items,
                                      const double* proj, const float* yy, const float* yg, void* node_ws,
                                      int64_t* tile_cnt, uint32_t* mask, float* feats, cudaStream_t st);
+// Sort keys of the paper's samplers (FFC_DRAW_*) for n_items pools; cap_max: largest pool.
+ffc_status launch_paper_keys(int sampler, const void* Y, const void* X, int dtype, int d, const KeyItem* items_dev,
+                             int n_items, int64_t cap_max, uint64_t seed, cudaStream_t st);
 ffc_status launch_mlp_loss_grad(const float* params, const float* feats, const double* targets,
                                 const int64_t* node_off_dev, int n_nodes, int64_t R, float* logits, float* g_o,
                                 double* loss_part, float* part, int n_part, float* grad, cudaStream_t st);

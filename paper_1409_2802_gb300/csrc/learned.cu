@@ -695,6 +695,109 @@ constexpr int SEL_BITS = 12, SEL_BINS = 1 << SEL_BITS;
 
 size_t select_smem_bytes() { return (size_t)SEL_CAP * (sizeof(uint64_t) + sizeof(uint32_t)) + SEL_BINS * sizeof(int); }
 
+// The selection with the ascending sort keys given (it.given): the n_keep smallest keys, in key order,
+// ties to the lower pool position (radix narrowing and a shared-memory sort as in select_kernel).
+__device__ void select_given(const SelectItem& it, int64_t P, int64_t n_keep, uint64_t* key, uint32_t* pos,
+                             int* hist) {
+  __shared__ int s_bin, s_fill;
+  __shared__ long long s_lt, s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t* gk = it.given;
+  int m = 0;
+  if (P <= SEL_CAP) {
+    m = (int)P;
+    for (int e = tid; e < m; e += blockDim.x) {
+      key[e] = gk[e];
+      pos[e] = (uint32_t)e;
+    }
+    __syncthreads();
+  } else {
+    uint64_t pv = 0;
+    int pl = 0;
+    long long c_lt = 0, c_in = P;
+    while (pl < 64 && c_lt + c_in > SEL_CAP) {
+      const int nb = min(SEL_BITS, 64 - pl);
+      const int sh = 64 - pl - nb;
+      const int bins = 1 << nb;
+      for (int b = tid; b < bins; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for (int64_t i = tid; i < P; i += blockDim.x) {
+        const uint64_t k = gk[i];
+        if (pl == 0 || (k >> (64 - pl)) == pv) atomicAdd(&hist[(int)((k >> sh) & (uint64_t)(bins - 1))], 1);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int per = (bins + 31) / 32;
+        const int b0 = lane * per;
+        long long own = 0;
+        for (int b = b0; b < b0 + per && b < bins; ++b) own += hist[b];
+        long long inc = own;
+        for (int off = 1; off < 32; off <<= 1) {
+          const long long v = __shfl_up_sync(0xffffffffu, inc, off);
+          if (lane >= off) inc += v;
+        }
+        const long long excl = inc - own;
+        if (c_lt + excl < n_keep && c_lt + inc >= n_keep) {
+          long long run = c_lt + excl;
+          for (int b = b0; b < b0 + per && b < bins; ++b) {
+            if (run + hist[b] >= n_keep) {
+              s_bin = b;
+              s_lt = run;
+              s_cnt = hist[b];
+              break;
+            }
+            run += hist[b];
+          }
+        }
+      }
+      __syncthreads();
+      pv = (pv << nb) | (uint64_t)s_bin;
+      pl += nb;
+      c_lt = s_lt;
+      c_in = s_cnt;
+      __syncthreads();
+    }
+    if (tid == 0) s_fill = 0;
+    __syncthreads();
+    const bool ties = c_lt + c_in > SEL_CAP;
+    for (int64_t i = tid; i < P; i += blockDim.x) {
+      const uint64_t k = gk[i];
+      if (ties ? k < pv : (k >> (64 - pl)) <= pv) {
+        const int slot = atomicAdd(&s_fill, 1);
+        key[slot] = k;
+        pos[slot] = (uint32_t)i;
+      }
+    }
+    __syncthreads();
+    if (ties && warp == 0) {
+      int fill = s_fill;
+      for (int64_t base = 0; base < P && fill < n_keep; base += 32) {
+        const int64_t i = base + lane;
+        const bool eq = i < P && gk[i] == pv;
+        const unsigned bal = __ballot_sync(0xffffffffu, eq);
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        if (eq && fill + rank < n_keep) {
+          key[fill + rank] = pv;
+          pos[fill + rank] = (uint32_t)i;
+        }
+        fill = min((int)n_keep, fill + __popc(bal));
+      }
+      if (lane == 0) s_fill = fill;
+    }
+    __syncthreads();
+    m = s_fill;
+  }
+  int Pp = 1;
+  while (Pp < m) Pp <<= 1;
+  for (int e = m + tid; e < Pp; e += blockDim.x) {
+    key[e] = ~0ull;
+    pos[e] = 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  bitonic_sort(key, pos, Pp);
+  for (int64_t i = tid; i < n_keep; i += blockDim.x) it.rows_out[i] = it.pool[pos[i]];
+}
+
 __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* items, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SelectItem& it = items[blockIdx.x];
@@ -711,6 +814,10 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
   __shared__ int s_bin, s_fill;
   __shared__ long long s_lt, s_cnt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (it.given) {
+    select_given(it, P, n_keep, key, pos, hist);
+    return;
+  }
   float mx = -INFINITY;
   for (int64_t i = tid; i < P; i += blockDim.x) mx = fmaxf(mx, it.logits[i]);
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));

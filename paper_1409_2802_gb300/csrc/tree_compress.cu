@@ -227,18 +227,29 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
   const ffc_params& P = R->p;
   const int d = R->d;
   const int64_t n_out = R->n_out;
-  const bool whole = P.pool_rows == 0;
+  // the paper's samplers (distance, nearest neighbours) draw from the whole far field by their own keys
+  const bool paper = P.sampler >= FFC_SAMPLE_DISTANCE;
+  const bool whole = paper || P.pool_rows == 0;
   if (!R->lcount) {
     FFC_CUDA(cudaMalloc((void**)&R->lcount, sizeof(int64_t) * 2 * n_out));
     R->lfar = R->lcount + n_out;
   }
   float *pyy = nullptr, *pyg = nullptr;
+  const double* proj = P.proj_dev;
   if (whole) {
-    ffc_status rc = grow(&R->pst, &R->pst_bytes, (size_t)R->N * 9 * sizeof(float), st);
+    // per-point sums (N x 9 floats), then room for 8 x d zero directions (the far-field kernels form the
+    // learned features as they go; the paper's samplers ignore them)
+    const size_t pts = ((size_t)R->N * 9 * sizeof(float) + 255) & ~size_t(255);
+    ffc_status rc = grow(&R->pst, &R->pst_bytes, pts + (size_t)8 * d * sizeof(double), st);
     if (rc != FFC_OK) return rc;
     pyy = (float*)R->pst;
     pyg = pyy + R->N;
-    rc = launch_point_stats(X, R->dtype, R->N, d, P.proj_dev, pyy, pyg, st);
+    if (!proj) {
+      double* z = (double*)(R->pst + pts);
+      FFC_CUDA(cudaMemsetAsync(z, 0, (size_t)8 * d * sizeof(double), st));
+      proj = z;
+    }
+    rc = launch_point_stats(X, R->dtype, R->N, d, proj, pyy, pyg, st);
     if (rc != FFC_OK) return rc;
   }
   int64_t o0 = 0;
@@ -261,7 +272,7 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     const int64_t tiles = far_tiles_count(R->N);
     Layout L;
     const size_t o_far = L.add<FarItem>(g), o_smp = L.add<SampleItem>(g), o_fi = L.add<FeatItem>(g),
-                 o_si = L.add<SelectItem>(g), o_pool = L.add<int64_t>(tot),
+                 o_si = L.add<SelectItem>(g), o_ki = L.add<KeyItem>(paper ? g : 0), o_pool = L.add<int64_t>(tot),
                  o_feat = L.add<float>((size_t)tot * FFC_N_FEATURES), o_lg = L.add<float>(tot),
                  o_key = L.add<uint64_t>(tot),
                  o_cnt = L.add<int64_t>(g), o_fc = L.add<int64_t>(g), o_st = L.add<int32_t>(g),
@@ -276,6 +287,7 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     SampleItem* d_smp = (SampleItem*)(b + o_smp);
     FeatItem* d_fi = (FeatItem*)(b + o_fi);
     SelectItem* d_si = (SelectItem*)(b + o_si);
+    KeyItem* d_ki = (KeyItem*)(b + o_ki);
     int64_t* pool = (int64_t*)(b + o_pool);
     float* feats = (float*)(b + o_feat);
     float* logits = (float*)(b + o_lg);
@@ -291,6 +303,7 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
     std::vector<SampleItem> hsmp(whole ? 0 : g);
     std::vector<FeatItem> hfi(g);
     std::vector<SelectItem> hsi(g);
+    std::vector<KeyItem> hki(paper ? g : 0);
     for (int i = 0; i < g; ++i) {
       const int64_t o = o0 + i, node = R->node_h[o], bgn = R->begin_h[o], n = R->count_h[o];
       const double* xc = tree->centroid_dev + node * d;
@@ -311,14 +324,22 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
       se.pool = pool + base[i]; se.count = cnt + i; se.P = cap[i]; se.logits = logits + base[i]; se.s = P.s_max;
       se.stream_id = (uint64_t)node; se.rows_out = R->rows + R->rows_off_h[o]; se.s_out = R->lcount + o;
       se.keys = skeys + base[i];
+      if (paper) {
+        KeyItem& ki = hki[i];
+        ki.pool = pool + base[i]; ki.count = cnt + i; ki.cap = cap[i]; ki.x_c = xc; ki.src_begin = bgn; ki.src_n = n;
+        ki.stream_id = (uint64_t)node; ki.keys = skeys + base[i];
+        se.given = skeys + base[i];
+        se.keys = nullptr;
+      }
     }
     if (whole) FFC_CUDA(cudaMemcpyAsync(d_far, hfar.data(), sizeof(FarItem) * g, cudaMemcpyHostToDevice, st));
     else FFC_CUDA(cudaMemcpyAsync(d_smp, hsmp.data(), sizeof(SampleItem) * g, cudaMemcpyHostToDevice, st));
     FFC_CUDA(cudaMemcpyAsync(d_fi, hfi.data(), sizeof(FeatItem) * g, cudaMemcpyHostToDevice, st));
     FFC_CUDA(cudaMemcpyAsync(d_si, hsi.data(), sizeof(SelectItem) * g, cudaMemcpyHostToDevice, st));
+    if (paper) FFC_CUDA(cudaMemcpyAsync(d_ki, hki.data(), sizeof(KeyItem) * g, cudaMemcpyHostToDevice, st));
     if (whole) {
       // far-field lists and features together, tiled over (points x nodes)
-      rc = launch_far_features_tiled(P.kernel, X, R->dtype, R->N, d, d_far, d_fi, g, P.proj_dev, pyy, pyg, nst,
+      rc = launch_far_features_tiled(P.kernel, X, R->dtype, R->N, d, d_far, d_fi, g, proj, pyy, pyg, nst,
                                      tcnt, fmask, feats, st);
       if (rc == FFC_OK) {
         copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, cnt, fc);
@@ -329,7 +350,14 @@ ffc_status propose_tree(ffc_tree_result* R, const void* X, const ffc_tree* tree,
       const int64_t cap_max = *std::max_element(cap.begin(), cap.end());
       if (rc == FFC_OK) rc = launch_features(P.kernel, X, R->dtype, d, d_fi, g, cap_max, P.proj_dev, feats, st);
     }
-    if (rc == FFC_OK) rc = launch_mlp_forward(P.mlp_dev, feats, tot, logits, st);
+    if (paper) {
+      const int draw = P.sampler == FFC_SAMPLE_DISTANCE ? FFC_DRAW_DISTANCE
+                     : P.sampler == FFC_SAMPLE_INV_DISTANCE ? FFC_DRAW_INV_DISTANCE : FFC_DRAW_NEAREST;
+      const int64_t cap_max = *std::max_element(cap.begin(), cap.end());
+      if (rc == FFC_OK) rc = launch_paper_keys(draw, X, X, R->dtype, d, d_ki, g, cap_max, P.seed, st);
+    } else if (rc == FFC_OK) {
+      rc = launch_mlp_forward(P.mlp_dev, feats, tot, logits, st);
+    }
     if (rc == FFC_OK) rc = launch_select(d_si, g, P.s_max, P.seed, st);
     if (rc != FFC_OK) return rc;
     copy_counts_kernel<<<(g + 127) / 128, 128, 0, st>>>(g, fc, R->lfar + o0);
@@ -447,7 +475,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += trsm_tiles(R->count_h[items[q]]); }
 
   const int64_t scratch_ctas = std::min<int64_t>(W, 2048);
-  const bool learned = P.sampler == FFC_SAMPLE_LEARNED;
+  const bool learned = P.sampler != FFC_SAMPLE_UNIFORM;   // learned or paper sampler: rows drawn once per call
   Layout L;
   const size_t o_si = L.add<SampleItem>(W), o_ei = L.add<EvalItem>(W), o_qi = L.add<CpqrItem>(W),
                o_ti = L.add<TrsmItem>(W), o_as = L.add<CtaAssign>(ha.size()), o_coff = L.add<int32_t>(hoff.size()),
@@ -645,7 +673,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");
   FFC_REQUIRE(P.min_level >= 0 && P.min_level <= tree->depth, "ffc_compress_tree: min_level out of range");
   if (!kernel_ok(P.kernel, d)) return FFC_E_INVALID;
-  FFC_REQUIRE(P.sampler == FFC_SAMPLE_UNIFORM || P.sampler == FFC_SAMPLE_LEARNED, "ffc_compress_tree: bad sampler");
+  FFC_REQUIRE(P.sampler >= FFC_SAMPLE_UNIFORM && P.sampler <= FFC_SAMPLE_NEAREST, "ffc_compress_tree: bad sampler");
   if (P.sampler == FFC_SAMPLE_LEARNED) {
     FFC_REQUIRE(P.pool_rows == 0 || P.pool_rows >= P.s_max,
                 "ffc_compress_tree: pool_rows must be 0 (whole far field) or >= s_max");
@@ -688,7 +716,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   int64_t s_nom = P.s0;
   R->rounds = 0;
   if (R->prof.enabled) R->prof.calls += 1;
-  if (P.sampler == FFC_SAMPLE_LEARNED) {
+  if (P.sampler != FFC_SAMPLE_UNIFORM) {
     const bool prof = R->prof.enabled != 0;
     if (prof) FFC_CUDA(cudaEventRecord(R->ev[0], st));
     ffc_status rc = propose_tree(R, points_perm_dev, tree, st);

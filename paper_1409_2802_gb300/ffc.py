@@ -28,6 +28,7 @@ FFC_E_TOL_NOT_REACHED = 7
 SOFT_STATUSES = (FFC_OK, FFC_E_FARFIELD_TOO_SMALL, FFC_E_TOL_NOT_REACHED)
 
 GAUSSIAN, LAPLACE, POLYNOMIAL = 0, 1, 2
+SAMPLE_UNIFORM, SAMPLE_LEARNED, SAMPLE_DISTANCE, SAMPLE_INV_DISTANCE, SAMPLE_NEAREST = 0, 1, 2, 3, 4
 F64, F32 = 0, 1
 FP64, MIXED = 0, 1
 
@@ -37,7 +38,7 @@ EXPORTS = (
     "ffc_tree_result_free", "ffc_tree_profile_enable", "ffc_tree_profile_reset", "ffc_tree_profile_get",
     "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
     "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched", "ffc_set_wait_limit",
-    "ffc_skeleton_charges", "ffc_potential", "ffc_tree_apply",
+    "ffc_skeleton_charges", "ffc_potential", "ffc_tree_apply", "ffc_sample_paper", "ffc_sample_leverage",
 )
 MLP_PARAMS = 18305
 N_FEATURES = 12
@@ -138,6 +139,8 @@ def lib() -> ctypes.CDLL:
     L.ffc_set_wait_limit.argtypes = [i64]
     L.ffc_skeleton_charges.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
     L.ffc_potential.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i64, vp, dbl, vp, vp]
+    L.ffc_sample_paper.argtypes = [i32, vp, i32, i32, vp, i64, vp, vp, i64, i64, u64, u64, vp, vp]
+    L.ffc_sample_leverage.argtypes = [vp, i64, i64, i64, vp, dbl, i64, u64, u64, vp, pi64, pi64, vp]
     L.ffc_tree_apply.argtypes = [vp, i32, i64, i32, ctypes.POINTER(c_tree), vp, vp, i32, i32, dbl, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("ffc_last_error", "ffc_version", "ffc_tree_depth", "ffc_tree_result_free"):
@@ -332,14 +335,15 @@ class TreeResult:
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
-                      qr_l2_budget_mb=0) -> TreeResult:
-    """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler.
-    ``qr_big_min_s``, ``qr_l2_budget_mb``: the QR's launch shape (0 = the library's defaults; see
-    ``autotune``)."""
+                      qr_l2_budget_mb=0, sampler: int | None = None) -> TreeResult:
+    """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
+    ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``: the QR's
+    launch shape (0 = the library's defaults; see ``autotune``)."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
-    sampler, proj_p, mlp_p = 0, None, None
+    proj_p, mlp_p = None, None
+    sampler = SAMPLE_UNIFORM if sampler is None else int(sampler)
     if proposal is not None:
         mlp, proj = proposal
         _dev(mlp, "proposal params"), _dev(proj, "proposal proj")
@@ -354,6 +358,34 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
 
 
 APPLY_SKELETON, APPLY_DIRECT = 0, 1
+DRAW_DISTANCE, DRAW_INV_DISTANCE, DRAW_NEAREST = 0, 1, 2
+
+
+def ffc_sample_paper(sampler, Y, cand, s, seed, stream_id, x_c=None, X=None, stream=None):
+    """min(s, P) of the candidate rows cand of Y by a paper sampler (DRAW_*), in key order."""
+    _dev(Y, "Y"), _dev(cand, "cand")
+    M, d = Y.shape
+    P = cand.numel()
+    keep = min(int(s), P)
+    rows = torch.empty(max(keep, 1), dtype=torch.int64, device=Y.device)
+    n = X.shape[0] if X is not None else 0
+    _check(lib().ffc_sample_paper(int(sampler), _ptr(Y), _dtype_code(Y), d, _ptr(cand), P, _ptr(x_c), _ptr(X), n,
+                                  int(s), ctypes.c_uint64(int(seed)), ctypes.c_uint64(int(stream_id)), _ptr(rows),
+                                  _stream(stream)))
+    return rows[:keep]
+
+
+def ffc_sample_leverage(Kcm, s, seed, stream_id, eps=1e-6, cand=None, stream=None):
+    """Rows of the full block (given as its (n, m) column-major storage) drawn by leverage; returns
+    (rows, eps-rank, status)."""
+    _dev(Kcm, "K")
+    n, m = Kcm.shape
+    rows = torch.empty(max(min(int(s), m), 1), dtype=torch.int64, device=Kcm.device)
+    s_out, rank = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _check(lib().ffc_sample_leverage(_ptr(Kcm), m, n, m, _ptr(cand), float(eps), int(s),
+                                          ctypes.c_uint64(int(seed)), ctypes.c_uint64(int(stream_id)), _ptr(rows),
+                                          ctypes.byref(s_out), ctypes.byref(rank), _stream(stream)))
+    return rows[:s_out.value], rank.value, st
 
 
 def ffc_skeleton_charges(skel, T, q, stream=None):
