@@ -581,6 +581,18 @@ ffc_status ffc_leverage(const double* K_dev, int64_t m, int64_t n, int64_t ldk, 
                         double* lev_dev, double* sigma_dev, int64_t* rank_host, void* stream);
 
 /*
+ * ffc_spectrum - the singular values of K (m x n FP64, column-major, ld ldk;
+ * §4.2 "Singular values of K") and its eps-rank, the smallest r with
+ * sigma_{r+1} / sigma_1 < eps (§4.1.3 step 1): the route of ffc_leverage
+ * without the scores (G = K^T K, Jacobi eigenvalues, FP64), so singular
+ * values below about 1e-7 sigma_1 are not resolved. sigma_dev: n doubles,
+ * decreasing. n <= 1024. FFC_E_TOL_NOT_REACHED (soft) if Jacobi did not
+ * converge. Synchronises.
+ */
+ffc_status ffc_spectrum(const double* K_dev, int64_t m, int64_t n, int64_t ldk, double eps, double* sigma_dev,
+                        int64_t* rank_host, void* stream);
+
+/*
  * ffc_leverage_batched - ffc_leverage of B blocks at once (the eigen-
  * decompositions run concurrently, one CTA per block). Host arrays of B
  * entries: K_dev[b] (m[b] x n[b], ld ldk[b]), lev_dev[b] (m[b]),

@@ -318,7 +318,7 @@ ffc_status launch_leverage_batched(int B, const double* const* K, const int64_t*
   for (int b = 0; b < B; ++b) {
     FFC_REQUIRE(n[b] >= 1 && n[b] <= LEV_MAX_N, "leverage: need 1 <= n <= %d", LEV_MAX_N);
     FFC_REQUIRE(m[b] >= 1 && ldk[b] >= m[b], "leverage: need m >= 1 and ldk >= m");
-    FFC_REQUIRE(K[b] && lev[b] && sigma[b], "leverage: null pointer");
+    FFC_REQUIRE(K[b] && (!lev || lev[b]) && sigma[b], "leverage: null pointer");
   }
   // per block: G, V, W (n^2 each), perm (n), rank, sweeps; one Gram partial buffer shared in stream order
   size_t per = 0, gpart = 0;
@@ -367,7 +367,7 @@ ffc_status launch_leverage_batched(int B, const double* const* K, const int64_t*
   }
   jacobi_kernel<<<B, JAC_THREADS, 0, st>>>(d_jobs);
   eig_order_kernel<<<B, 1024, 0, st>>>(d_jobs, eps, r_fixed);
-  for (int b = 0; b < B; ++b)
+  for (int b = 0; lev && b < B; ++b)
     leverage_kernel<<<(unsigned)((m[b] + GT - 1) / GT), 256, 0, st>>>(K[b], m[b], (int)n[b], ldk[b], jobs[b].W,
                                                                     jobs[b].rank, lev[b]);
   cudaError_t e = cudaGetLastError();
@@ -389,3 +389,16 @@ ffc_status launch_leverage_batched(int B, const double* const* K, const int64_t*
 }
 
 }  // namespace ffc
+
+extern "C" ffc_status ffc_spectrum(const double* K_dev, int64_t m, int64_t n, int64_t ldk, double eps, double* sigma_dev,
+                                   int64_t* rank_host, void* stream) {
+  FFC_REQUIRE(m >= 1 && n >= 1 && ldk >= m, "ffc_spectrum: need m, n >= 1 and ldk >= m");
+  FFC_REQUIRE(n <= 1024, "ffc_spectrum: n = %lld exceeds 1024 columns", (long long)n);
+  FFC_REQUIRE(K_dev && sigma_dev && rank_host && eps >= 0.0, "ffc_spectrum: null pointer or eps < 0");
+  const double* Kp[1] = {K_dev};
+  const int64_t mm[1] = {m}, nn[1] = {n}, ll[1] = {ldk};
+  double* sp[1] = {sigma_dev};
+  int32_t sweeps = 0;
+  return ffc::launch_leverage_batched(1, Kp, mm, nn, ll, eps, 0, nullptr, sp, rank_host, &sweeps,
+                                      ffc::as_stream(stream));
+}

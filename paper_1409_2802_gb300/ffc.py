@@ -39,6 +39,7 @@ EXPORTS = (
     "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
     "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched", "ffc_set_wait_limit",
     "ffc_skeleton_charges", "ffc_potential", "ffc_tree_apply", "ffc_sample_paper", "ffc_sample_leverage",
+    "ffc_spectrum",
 )
 MLP_PARAMS = 18305
 N_FEATURES = 12
@@ -139,6 +140,7 @@ def lib() -> ctypes.CDLL:
     L.ffc_set_wait_limit.argtypes = [i64]
     L.ffc_skeleton_charges.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
     L.ffc_potential.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i64, vp, dbl, vp, vp]
+    L.ffc_spectrum.argtypes = [vp, i64, i64, i64, dbl, vp, pi64, vp]
     L.ffc_sample_paper.argtypes = [i32, vp, i32, i32, vp, i64, vp, vp, i64, i64, u64, u64, vp, vp]
     L.ffc_sample_leverage.argtypes = [vp, i64, i64, i64, vp, dbl, i64, u64, u64, vp, pi64, pi64, vp]
     L.ffc_tree_apply.argtypes = [vp, i32, i64, i32, ctypes.POINTER(c_tree), vp, vp, i32, i32, dbl, vp, vp, vp]
@@ -539,6 +541,16 @@ def ffc_adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8
         _dev(t, nm)
     _check(lib().ffc_adam_step(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step), float(lr),
                                float(beta1), float(beta2), float(eps), _stream(stream)))
+
+
+def ffc_spectrum(Kcm, eps=1e-2, stream=None):
+    """(singular values (decreasing), eps-rank, status) of a block given as its (n, m) column-major storage."""
+    _dev(Kcm, "K")
+    n, m = Kcm.shape
+    sigma = torch.empty(n, dtype=torch.float64, device=Kcm.device)
+    rank = ctypes.c_int64(0)
+    st = _check(lib().ffc_spectrum(_ptr(Kcm), m, n, m, float(eps), _ptr(sigma), ctypes.byref(rank), _stream(stream)))
+    return sigma, rank.value, st
 
 
 def ffc_leverage(Kcm, eps=1e-6, r_fixed=0, stream=None):
