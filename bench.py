@@ -1,30 +1,34 @@
 #!/usr/bin/env python
 """Benchmark: tree nodes compressed per second by sampled-row ID on one GB300.
 
-Workload (one "step" = one full ffc_compress_tree call over every node at
-level >= 2): N = 65,536 points in d = 16 from an 8-component Gaussian mixture
-(means uniform in [-5, 5]^16, sigma 1), PCA median-split tree with leaf size
-256 (levels 2..8, 508 nodes, n = 16,384 .. 256), Gaussian kernel h = 2,
-tolerance 1e-6 on ||R22||_F / ||K'||_F, s = 128 doubling to at most 2,048.
-Synthetic data; the tree is built once on the GPU before timing (support).
+Default configuration (the mixed-precision one): N = 262,144 points in d = 128
+from a 16-component Gaussian mixture whose coordinate k has variance 1/k,
+PCA median-split tree with leaf size 256 (levels 2..10, 2,044 nodes, n =
+65,536 .. 256); one "step" compresses every node twice, once per kernel of
+the configuration: Laplace |x - y|^-126 and the cubic polynomial
+(x.y / 128 + 1)^3 (4,088 node compressions). Tolerance 1e-6 on
+||R22||_F / ||K'||_F, s = 128 doubling to at most 2,048. Synthetic data; the
+tree is built once on the GPU before timing (support).
 
 Timing: W warm-up steps, then K timed steps, each bracketed by CUDA events
 on the launching stream; a 512 MB buffer is written between steps to flush
 the 129 MB L2 (outside the events). Clocks are sampled with nvidia-smi
 during the timed steps. `value` is nodes / second over the timed steps;
 `e2e` repeats the measurement through host buffers (pinned H2D of the
-permuted points and tree, compression, D2H of every node's rank, status,
-residual, skeleton and interpolation matrix). `cpu_baseline` times the FP64
-oracle on a seeded, time-bounded sample of the same nodes in a
-single-threaded subprocess; `--impl reference` times that oracle per step.
+points and tree, compression, D2H of every node's rank, status, residual,
+skeleton and interpolation matrix). `cpu_baseline` and `--impl reference`
+time the FP64 oracle over a pool of single-threaded processes on the host
+cores, each step one complete pass over a fixed seeded sample of nodes from
+the tree's two deepest levels (the oracle's time for the largest nodes is
+minutes each).
 
 The timed form (`value`) is mixed precision with the learned row proposal,
 whose network is first trained on the GPU (untimed) with the standard recipe
 (leaves of the d = 128 and d = 1000 generators). Beside it: plain FP64 with
-uniform sampling (`fp64_plain`, the reference point of the speedup) and the
-two other precision x sampler arms. The oracle baseline compresses with the
-uniform sampler (the network's weights come from the GPU path and are never
-fed to the oracle).
+uniform sampling (`fp64_plain`, the reference point of the speedup), and the
+other configurations (d = 16 and d = 1,000 trees) with their own plain FP64
+arms (`extra_configs`). The oracle compresses with the uniform sampler (the
+network's weights come from the GPU path and are never fed to the oracle).
 """
 from __future__ import annotations
 
@@ -41,6 +45,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# One tree and kernel each ("parts"); a configuration compresses one or more parts per step.
 WORKLOADS = {
     # N = 65,536 in d = 16, 8-component mixture, leaf 256 (levels 2..8, 508 nodes), Gaussian h = 2
     "c2": {"workload": "tree_compress_gaussian_mixture_N65536_d16", "gen": "gaussian_mixture", "N": 65536, "d": 16,
@@ -58,11 +63,21 @@ WORKLOADS = {
            "d": 1000, "d_i": 10, "data_seed": 1000, "leaf_size": 512, "kernel": "gaussian", "h": "median",
            "points": "f32"},
 }
+CONFIGS = {
+    "c3": {"workload": "tree_compress_decaying_mixture_N262144_d128_laplace_and_poly3",
+           "parts": ["c3-laplace", "c3-poly"]},
+    "c2": {"workload": WORKLOADS["c2"]["workload"], "parts": ["c2"]},
+    "c4": {"workload": WORKLOADS["c4"]["workload"], "parts": ["c4"]},
+    "c3-laplace": {"workload": WORKLOADS["c3-laplace"]["workload"], "parts": ["c3-laplace"]},
+    "c3-poly": {"workload": WORKLOADS["c3-poly"]["workload"], "parts": ["c3-poly"]},
+}
+DEFAULT_CONFIG = "c3"
 COMMON = {"tol": 1e-6, "s0": 128, "s_max": 2048, "min_level": 2, "xi": 1.0, "sample_seed": 0}
 WORKLOAD = dict(WORKLOADS["c2"], **COMMON)
 
 
 def select_workload(name: str):
+    """Make part `name` the one the per-part helpers below describe."""
     global WORKLOAD
     WORKLOAD = dict(WORKLOADS[name], **COMMON)
     WORKLOAD["name"] = name
@@ -99,6 +114,18 @@ def kernel_label(h_value=None):
     if W["kernel"] == "laplace":
         return f"laplace |x-y|^-{W['d'] - 2}"
     return f"polynomial (x.y/{W['h']:g} + {W['c']:g})^{W['p']}"
+
+
+def part_label(p):
+    """Kernel label of a part's inputs."""
+    select_workload(p.name)
+    return kernel_label(p.kern.h)
+
+
+def points_key(name):
+    """Parts with the same points and leaf size share one tree."""
+    W = WORKLOADS[name]
+    return (W["gen"], W["N"], W["d"], W["data_seed"], W["leaf_size"])
 
 
 METRIC = "nodes compressed/sec at ID rel. error <=1e-6; chosen form vs plain FP64 GPU"
@@ -178,14 +205,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_inputs(torch, dev):
+class PartInputs:
+    """One part's device inputs: points in tree order, the tree and the kernel (the points and tree are
+    shared by parts with the same generator)."""
+
+    def __init__(self, name, P, tree, Pp, kern):
+        self.name, self.P, self.tree, self.Pp, self.kern = name, P, tree, Pp, kern
+
+
+def build_config_inputs(torch, dev, cfg_name):
     from paper_1409_2802_gb300 import ffc
     rank, _, _ = _env_rank()
-    P = workload_points(rank)
-    Pd = torch.tensor(P, device=dev)
-    tree = ffc.ffc_build_tree(Pd, WORKLOAD["leaf_size"])
-    Pp = Pd[tree.perm].contiguous()
-    return P, tree, Pp, workload_kernel(ffc, P)
+    shared = {}
+    out = []
+    for part in CONFIGS[cfg_name]["parts"]:
+        select_workload(part)
+        key = points_key(part)
+        if key not in shared:
+            P = workload_points(rank)
+            Pd = torch.tensor(P, device=dev)
+            tree = ffc.ffc_build_tree(Pd, WORKLOAD["leaf_size"])
+            shared[key] = (P, tree, Pd[tree.perm].contiguous())
+            del Pd
+        P, tree, Pp = shared[key]
+        out.append(PartInputs(part, P, tree, Pp, workload_kernel(ffc, P)))
+    return out
 
 
 def max_over_ranks(value: float, world: int, device="cpu") -> float:
@@ -208,100 +252,129 @@ def precision_code(ffc, name):
     return ffc.FP64 if name == "fp64" else ffc.MIXED
 
 
-def run_gpu_steps(torch, ffc, Pp, tree, k, precision, steps, warmup, flush_buf, stream, result=None, proposal=None,
-                  qr_kw=None):
+def compress_kwargs():
     W = WORKLOAD
+    return dict(tol=W["tol"], min_level=W["min_level"], s0=W["s0"], s_max=W["s_max"], xi=W["xi"],
+                seed=W["sample_seed"])
+
+
+def run_gpu_steps(torch, ffc, parts, precision, steps, warmup, flush_buf, stream, proposal=None, qr_kw=None,
+                  sampler=None):
+    """W warm-up and K timed steps; a step compresses every part's tree. Returns (results, per-step ms,
+    profiles per part)."""
     qr_kw = qr_kw or {}
+    results = {p.name: None for p in parts}
 
-    def step(res):
-        return ffc.ffc_compress_tree(Pp, tree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
-                                     s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
-                                     stream=stream, proposal=proposal, **qr_kw)
+    def step():
+        for p in parts:
+            select_workload(p.name)
+            prop = proposal[p.name] if isinstance(proposal, dict) else proposal
+            results[p.name] = ffc.ffc_compress_tree(p.Pp, p.tree, p.kern, precision=precision, result=results[p.name],
+                                                    stream=stream, proposal=prop, sampler=sampler,
+                                                    **compress_kwargs(), **qr_kw.get(p.name, {}))
 
-    res = result
     for _ in range(warmup):
-        res = step(res)
-    res.profile_enable(True)
-    res.profile_reset()
+        step()
+    for r in results.values():
+        r.profile_enable(True)
+        r.profile_reset()
     times = []
     for _ in range(steps):
         flush_buf.fill_(1.0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step(res)
+        step()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    prof = res.profile()
-    res.profile_enable(False)
-    return res, times, prof
+    profs = {}
+    for name, r in results.items():
+        profs[name] = r.profile()
+        r.profile_enable(False)
+    return results, times, profs
 
 
-def run_e2e(torch, ffc, P_host_perm, tree, k, precision, steps, warmup, stream, proposal=None, qr_kw=None):
-    """Same metric through host buffers: pinned H2D inputs, compress, D2H results, every step."""
-    W = WORKLOAD
-    dev = P_host_perm.device if P_host_perm.is_cuda else torch.device("cuda")
-    hP = P_host_perm.cpu().pin_memory()
-    tree_host = {n: getattr(tree, n).cpu().pin_memory() for n in ("begin", "count", "centroid", "radius")}
-    dP = torch.empty_like(hP, device=dev)
-    dT = {n: torch.empty_like(v, device=dev) for n, v in tree_host.items()}
-    dtree = ffc.DeviceTree(tree.depth, tree.perm, dT["begin"], dT["count"], dT["centroid"], dT["radius"])
-    res = None
-    h2d = hP.numel() * hP.element_size() + sum(v.numel() * v.element_size() for v in tree_host.values())
+def run_e2e(torch, ffc, parts, precision, steps, warmup, stream, proposal=None, qr_kw=None):
+    """Same metric through host buffers: pinned H2D of the points and tree (once per step, shared by the
+    parts), every part compressed, D2H of every node's outputs, every step."""
+    dev = parts[0].Pp.device
+    trees = {}
+    for p in parts:
+        if id(p.tree) not in trees:
+            hP = p.Pp.cpu().pin_memory()
+            th = {n: getattr(p.tree, n).cpu().pin_memory() for n in ("begin", "count", "centroid", "radius")}
+            dP = torch.empty_like(hP, device=dev)
+            dT = {n: torch.empty_like(v, device=dev) for n, v in th.items()}
+            trees[id(p.tree)] = (hP, th, dP, dT, ffc.DeviceTree(p.tree.depth, p.tree.perm, dT["begin"], dT["count"],
+                                                                dT["centroid"], dT["radius"]))
+    h2d = sum(v[0].numel() * v[0].element_size() + sum(t.numel() * t.element_size() for t in v[1].values())
+              for v in trees.values())
+    results = {p.name: None for p in parts}
     d2h_bytes = []
+    qr_kw = qr_kw or {}
 
-    def step(res):
+    def step():
         with torch.cuda.stream(stream):
-            dP.copy_(hP, non_blocking=True)
-            for n in dT:
-                dT[n].copy_(tree_host[n], non_blocking=True)
-        res = ffc.ffc_compress_tree(dP, dtree, k, tol=W["tol"], precision=precision, min_level=W["min_level"],
-                                    s0=W["s0"], s_max=W["s_max"], xi=W["xi"], seed=W["sample_seed"], result=res,
-                                    stream=stream, proposal=proposal, **(qr_kw or {}))
-        with torch.cuda.stream(stream):
-            v = ffc.tree_result_views(res)
-            out = {kk: v[kk].to("cpu", non_blocking=False) for kk in ("rank", "s", "status", "r22_rel", "skel", "T_off",
-                                                                       "T")}
-        d2h_bytes.append(sum(t.numel() * t.element_size() for t in out.values()))
-        return res
+            for hP, th, dP, dT, _ in trees.values():
+                dP.copy_(hP, non_blocking=True)
+                for n in dT:
+                    dT[n].copy_(th[n], non_blocking=True)
+        nb = 0
+        for p in parts:
+            select_workload(p.name)
+            _, _, dP, _, dtree = trees[id(p.tree)]
+            prop = proposal[p.name] if isinstance(proposal, dict) else proposal
+            results[p.name] = ffc.ffc_compress_tree(dP, dtree, p.kern, precision=precision, result=results[p.name],
+                                                    stream=stream, proposal=prop, **compress_kwargs(),
+                                                    **qr_kw.get(p.name, {}))
+            with torch.cuda.stream(stream):
+                v = ffc.tree_result_views(results[p.name])
+                out = {kk: v[kk].to("cpu", non_blocking=False)
+                       for kk in ("rank", "s", "status", "r22_rel", "skel", "T_off", "T")}
+            nb += sum(t.numel() * t.element_size() for t in out.values())
+        d2h_bytes.append(nb)
 
     for _ in range(warmup):
-        res = step(res)
+        step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        res = step(res)
+        step()
     e1.record(stream)
     e1.synchronize()
     wall = time.perf_counter() - t0
     ms = e0.elapsed_time(e1)
-    n_nodes = ffc.tree_result_views(res)["n_out"]
+    n_nodes = sum(ffc.tree_result_views(r)["n_out"] for r in results.values())
+    for r in results.values():
+        r.close()
     return {"value": n_nodes * steps / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(statistics.mean(d2h_bytes[-steps:])), "wall_s": wall}
+            "d2h_bytes_per_step": int(statistics.mean(d2h_bytes[-steps:])), "wall_s": wall, "steps": steps}
 
 
 # --------------------------------------------------------------------------- oracle legs
 
-def oracle_setup():
-    from oracle import kernels as o_kernels
-    from oracle import tree as o_tree
-    P = workload_points()
-    t = o_tree.build_tree(P, WORKLOAD["leaf_size"])
-    return P[t.perm].astype("float64"), t, workload_kernel(o_kernels, P)
-
-
-def oracle_nodes_in_order(t, seed=12345):
+def oracle_sample(cfg_name, per_part=16, seed=12345):
+    """The fixed node sample of the oracle legs: per part, `per_part` seeded nodes of the tree's two deepest
+    levels (node ids depend only on N and the leaf size), largest first."""
     import numpy as np
-    nodes = np.array([i for i in range(t.n_nodes) if t.level[i] >= WORKLOAD["min_level"]])
-    return list(np.random.default_rng(seed).permutation(nodes))
+    from oracle import tree as o_tree
+    out = []
+    for part in CONFIGS[cfg_name]["parts"]:
+        W = WORKLOADS[part]
+        D = o_tree.tree_depth(W["N"], W["leaf_size"])
+        cand = np.arange((1 << (D - 1)) - 1, (1 << (D + 1)) - 1)
+        pick = np.random.default_rng(seed).choice(cand, min(per_part, cand.size), replace=False)
+        out += [(part, int(nd)) for nd in sorted(pick.tolist())]
+    return out
 
 
-def oracle_compress(Pp, t, kernel, node):
+def oracle_compress(state, part, node):
     from oracle import compress as o_compress
-    W = WORKLOAD
+    Pp, t, kernel = state[part]
+    W = dict(WORKLOADS[part], **COMMON)
     return o_compress.compress_node(Pp, t, int(node), kernel, W["tol"], W["sample_seed"], W["s0"], W["s_max"],
                                     W["xi"])
 
@@ -309,123 +382,57 @@ def oracle_compress(Pp, t, kernel, node):
 _WORKER = {}
 
 
-def _worker_init(name, barrier):
-    """Pool worker: the oracle's inputs (points, tree, kernel), then wait for every other worker."""
-    select_workload(name)
-    _WORKER["state"] = oracle_setup()
-    barrier.wait()
-
-
-def _worker_compress(node):
-    Pp, t, kernel = _WORKER["state"]
-    oracle_compress(Pp, t, kernel, node)
-    return int(node)
-
-
-def cpu_leg(workers: int = 1) -> int:
-    """Child process: compress nodes in a seeded random order, one JSON line per finished node.
-    With workers > 1 the nodes go to a pool of single-threaded processes (spawned), each with its own
-    copy of the oracle's inputs; the stream reports ready once every worker holds them."""
-    if workers <= 1:
-        Pp, t, kernel = oracle_setup()
-        order = oracle_nodes_in_order(t)
-        print(json.dumps({"ready": True, "of": len(order), "workers": 1}), flush=True)
-        t0 = time.perf_counter()
-        for i, node in enumerate(order):
-            oracle_compress(Pp, t, kernel, node)
-            print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
-        return 0
-    import multiprocessing as mp
+def _worker_init(cfg_name):
+    """Pool worker: the oracle's inputs of every part (parts with the same points share the tree)."""
+    from oracle import kernels as o_kernels
     from oracle import tree as o_tree
-    P = workload_points()
-    order = oracle_nodes_in_order(o_tree.build_tree(P, WORKLOAD["leaf_size"]))
-    ctx = mp.get_context("spawn")
-    with ctx.Manager() as mgr:
-        barrier = mgr.Barrier(workers + 1)
-        with ctx.Pool(workers, initializer=_worker_init, initargs=(WORKLOAD.get("name", "c2"), barrier)) as pool:
-            barrier.wait()
-            print(json.dumps({"ready": True, "of": len(order), "workers": workers}), flush=True)
-            t0 = time.perf_counter()
-            for i, _ in enumerate(pool.imap_unordered(_worker_compress, order, chunksize=1)):
-                print(json.dumps({"done": i + 1, "t": time.perf_counter() - t0}), flush=True)
-    return 0
+    state, trees = {}, {}
+    for part in CONFIGS[cfg_name]["parts"]:
+        select_workload(part)
+        key = points_key(part)
+        if key not in trees:
+            P = workload_points()
+            t = o_tree.build_tree(P, WORKLOAD["leaf_size"])
+            trees[key] = (P, P[t.perm].astype("float64"), t)
+        P, Pp, t = trees[key]
+        state[part] = (Pp, t, workload_kernel(o_kernels, P))
+    _WORKER["state"] = state
 
 
-class OracleStream:
-    """The FP64 oracle compressing nodes in a seeded random order in a child process: one
-    single-threaded process, or a pool of `workers` of them over the host cores.
+def _worker_compress(item):
+    part, node = item
+    oracle_compress(_WORKER["state"], part, node)
+    return item
 
-    The child prints one line per finished node; the parent reads the count of
-    finished nodes at any time. The nodes in progress when a window closes
-    count as time spent, so a window's throughput is finished nodes / window.
-    """
 
-    def __init__(self, workers: int = 1):
+class OraclePool:
+    """The FP64 oracle over a pool of single-threaded processes (spawned, so that no GPU state is
+    forked); each pass compresses a fixed list of (part, node) items completely."""
+
+    def __init__(self, cfg_name: str, workers: int):
+        import multiprocessing as mp
         self.workers = max(1, int(workers))
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
-            env.pop(k, None)
-        self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--_cpu-leg", str(self.workers),
-                                      "--workload", WORKLOAD.get("name", "c2")], env=env,
-                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
-                                     start_new_session=True)
-        self.of, self.ready_t, self.done = None, None, 0
-        self.thread = threading.Thread(target=self._read, daemon=True)
-        self.thread.start()
+        self.cfg = cfg_name
+        ctx = mp.get_context("spawn")
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.pool = ctx.Pool(self.workers, initializer=_worker_init, initargs=(cfg_name,))
+        # every worker holds its inputs before the first timed pass
+        self.pool.map(_noop, range(self.workers), chunksize=1)
 
-    def _read(self):
-        for line in self.proc.stdout:
-            try:
-                msg = json.loads(line)
-            except ValueError:
-                continue
-            if msg.get("ready"):
-                self.of = msg["of"]
-                self.ready_t = time.perf_counter()
-            elif "done" in msg:
-                self.done = msg["done"]
-
-    def wait_ready(self, timeout=900.0) -> bool:
-        end = time.perf_counter() + timeout
-        while self.ready_t is None and self.proc.poll() is None and time.perf_counter() < end:
-            time.sleep(0.05)
-        return self.ready_t is not None
-
-    def window(self, seconds: float):
-        """Sleep through one window; returns (nodes finished in it, its length)."""
-        d0, t0 = self.done, time.perf_counter()
-        end = t0 + seconds
-        while self.proc.poll() is None and time.perf_counter() < end:
-            time.sleep(0.05)
-        return self.done - d0, time.perf_counter() - t0
+    def run_pass(self, items) -> float:
+        t0 = time.perf_counter()
+        for _ in self.pool.imap_unordered(_worker_compress, items, chunksize=1):
+            pass
+        return time.perf_counter() - t0
 
     def close(self):
-        # the child's own process group holds its pool workers
-        try:
-            os.killpg(self.proc.pid, 9)
-        except (ProcessLookupError, PermissionError):
-            self.proc.kill()
-        self.proc.wait()
+        self.pool.terminate()
+        self.pool.join()
 
 
-def finish_cpu_baseline(o: "OracleStream", min_seconds: float, when: str) -> dict:
-    """Close an oracle stream after at least `min_seconds` of it; nodes finished / window."""
-    try:
-        if not o.wait_ready():
-            return {"value": None, "unit": UNIT, "cores": o.workers, "kind": "oracle",
-                    "sample": "oracle setup failed"}
-        remaining = o.ready_t + min_seconds - time.perf_counter()
-        if remaining > 0:
-            o.window(remaining)
-        el = time.perf_counter() - o.ready_t
-        done = o.done
-    finally:
-        o.close()
-    procs = "one thread" if o.workers == 1 else f"{o.workers} single-threaded processes, one node each at a time"
-    return {"value": done / el, "unit": UNIT, "cores": o.workers, "kind": "oracle",
-            "sample": (f"{done} of {o.of} nodes finished in a {el:.1f} s window (seeded random node order; the "
-                       f"nodes still running at the end count as time spent), uniform sampler, {procs} "
-                       f"(OMP/OpenBLAS = 1), {when}")}
+def _noop(i):
+    return i
 
 
 def host_cores() -> int:
@@ -435,46 +442,77 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def sample_label(items, workers):
+    parts = sorted({p for p, _ in items})
+    return (f"{len(items)} nodes ({', '.join(f'{sum(1 for q, _ in items if q == p)} of {p}' for p in parts)}), "
+            f"a seeded sample of the two deepest tree levels, each pass compressing all of them; "
+            f"{workers} single-threaded processes (OMP/OpenBLAS = 1), uniform sampler")
+
+
+def cpu_baseline_leg(cfg_name, workers, min_seconds=10.0) -> dict:
+    """The oracle on the host cores after the GPU work: complete passes over the fixed sample until at
+    least `min_seconds` have gone by; nodes / second."""
+    items = oracle_sample(cfg_name)
+    pool = OraclePool(cfg_name, workers)
+    try:
+        el, done, passes = 0.0, 0, 0
+        while el < min_seconds or passes == 0:
+            el += pool.run_pass(items)
+            done += len(items)
+            passes += 1
+    finally:
+        pool.close()
+    return {"value": done / el, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": sample_label(items, pool.workers) + f"; {passes} passes in {el:.1f} s"}
+
+
 def reference_arm(args, rank, world):
-    """--impl reference: the FP64 CPU oracle; each step is one fixed time window of its node stream."""
+    """--impl reference: the FP64 CPU oracle; each step is one complete pass over the fixed sample."""
     if rank != 0:
         return 0
-    win = min(20.0, max(2.0, 150.0 / (args.steps + args.warmup)))
-    o = OracleStream(args.cpu_workers or host_cores())
+    items = oracle_sample(args.workload)
     try:
-        if not o.wait_ready():
-            print(json.dumps({"impl": "reference", "unavailable": "oracle setup failed"}))
-            return 0
+        pool = OraclePool(args.workload, args.cpu_workers or host_cores())
+    except (OSError, RuntimeError) as e:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle pool failed: {e}"}))
+        return 0
+    try:
         for _ in range(args.warmup):
-            o.window(win)
-        done, el = 0, 0.0
-        for _ in range(args.steps):
-            dn, t = o.window(win)
-            done += dn
-            el += t
+            pool.run_pass(items)
+        times = [pool.run_pass(items) for _ in range(args.steps)]
     finally:
-        o.close()
-    value = done / el
+        pool.close()
+    el = sum(times)
+    value = len(items) * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["workload"], "step": f"{win:.1f} s window of the oracle's node stream",
-                   "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": o.workers,
-                         "sample": f"{done} nodes finished over {args.steps} windows of {win:.1f} s "
-                                   f"(seeded random node order), {o.workers} single-threaded processes"},
+        "config": config_block(args.workload, "fp64", "uniform"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": pool.workers,
+                         "sample": sample_label(items, pool.workers)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
+def config_block(cfg_name, precision, sampler, extra=None):
+    parts = CONFIGS[cfg_name]["parts"]
+    W0 = dict(WORKLOADS[parts[0]], **COMMON)
+    cfg = {"workload": CONFIGS[cfg_name]["workload"], "precision": precision, "sampler": sampler,
+           "parts": parts, "N": W0["N"], "d": W0["d"], "leaf_size": W0["leaf_size"], "points": W0["points"],
+           "tol": W0["tol"], "s": "128 doubling to 2048", "l2": "flushed between steps (512 MB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal)
 
 
 
-def qr_traffic(precision_name, sampler, shape=None):
+def qr_traffic(precision_name, sampler, shape=None, workload_name=None):
     """DRAM bytes per step of the QR launches from the committed ncu record, while the kernel source
     and the QR launch shape (``shape``: qr_big_min_s / qr_l2_budget_mb, None = the library defaults)
     still match the ones the counters were taken on; else None."""
@@ -492,7 +530,7 @@ def qr_traffic(precision_name, sampler, shape=None):
                     rec[k.strip()] = v.strip()
         want = dict(shape or {"qr_big_min_s": 1024, "qr_l2_budget_mb": 96})
         same_shape = all(str(want.get(k_)) == rec.get(k_) for k_ in ("qr_big_min_s", "qr_l2_budget_mb"))
-        if (rec.get("cpqr_sha256") == h and rec.get("workload") == WORKLOAD["workload"]
+        if (rec.get("cpqr_sha256") == h and rec.get("workload") == (workload_name or WORKLOAD["workload"])
                 and rec.get("precision") == precision_name and rec.get("sampler") == sampler and same_shape):
             return float(rec["traffic_bytes_per_step"]), os.path.relpath(path, ROOT)
     return None, None
@@ -517,19 +555,68 @@ def eval_roofline(prof, steps, precision_name, peaks, peak_src):
                 "peak_source": f"{peak_src} dense BF16, sustained (MEASURED_PEAKS.json bf16_tflops_sustained, "
                                "tcgen05 cuBLAS)",
                 "gemm_flops_per_step": gemm, "ms_per_step": ms}
-    peak = FP32_PEAK_TFLOPS if precision_name == "mixed" else FP64_PEAK_TFLOPS
+    peak, src = alu_peak(peaks, precision_name)
     return {"kernel": "eval_kernel (SIMT)", "bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-            "frac": tflops / peak, "gemm_flops_per_step": gemm, "ms_per_step": ms,
-            "peak_source": "nominal FP32 rate of GB300" if precision_name == "mixed" else "nominal FP64 rate of GB300"}
+            "frac": tflops / peak, "gemm_flops_per_step": gemm, "ms_per_step": ms, "peak_source": src}
 
 
-def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned", shape=None):
-    """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing.
+def alu_peak(peaks, precision_name):
+    """FP32 (mixed) or FP64 ALU peak: the one measured in this run when present, else nominal."""
+    key = "fp64_tflops" if precision_name == "fp64" else "fp32_tflops"
+    if peaks.get(key):
+        return peaks[key], f"measured in this run: {peaks.get(key + '_how', '')}"
+    if precision_name == "fp64":
+        return FP64_PEAK_TFLOPS, "nominal FP64 rate of GB300"
+    return FP32_PEAK_TFLOPS, "nominal FP32 rate of GB300 (152 SMs x 128 lanes x 2 flops x 2.07 GHz)"
+
+
+def measure_alu_peaks(torch, dev):
+    """FP64 and FP32 (TF32 off) GEMM throughput of this GPU (cuBLAS through torch.matmul, best of 3 after a
+    warm-up): the denominators of the ALU fractions of the FP64 and FP32 paths."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for key, dt, n in (("fp64_tflops", torch.float64, 8192), ("fp32_tflops", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            out[key + "_how"] = f"torch.matmul {str(dt).replace('torch.', '')} {n}^3, best of 3 (TF32 off)"
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+def combine_profiles(profs):
+    """Sum of the per-part profiles of one arm."""
+    keys = ("sample", "eval", "qr", "trsm", "bookkeeping")
+    out = {"ms": {k: sum(p["ms"][k] for p in profs) for k in keys},
+           "launches": sum(p["launches"] for p in profs), "qr_launches": sum(p["qr_launches"] for p in profs)}
+    for k in ("qr_flops", "eval_flops", "qr_bytes"):
+        out[k] = sum(p[k] for p in profs)
+    out["qr_ms_round"] = [sum(p["qr_ms_round"][i] for p in profs) for i in range(8)]
+    out["items_round"] = [sum(p["items_round"][i] for p in profs) for i in range(8)]
+    return out
+
+
+def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned", shape=None, workload_name=None):
+    """Roofline of the pivoted QR from the library's live per-phase CUDA-event timing (all parts of a step).
 
     Algorithmic bytes: one read and one write of every sampled block K' (s x n)
-    per QR launch. The unblocked Householder QR streams the trailing matrix
-    once per step, (s - k)(n - k) elements read and written at step k; that
-    volume is reported as `streamed_gbs`, and the FP32/FP64 ALU rate beside it.
+    per QR launch. The Householder QR streams the trailing matrix once per step,
+    (s - k)(n - k) elements at step k; that volume is reported as `streamed_gbs`,
+    and the FP32/FP64 ALU rate beside it.
     """
     phase_ms = prof["ms"]
     qr_ms = phase_ms["qr"] / max(steps, 1)
@@ -538,37 +625,37 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned",
     gbs = prof["qr_bytes"] / steps / (qr_ms / 1e3) / 1e9 if qr_ms > 0 else 0.0
     streamed = prof["qr_flops"] / 2.0 * esz / steps / (qr_ms / 1e3) / 1e9 if qr_ms > 0 else 0.0
     hbm = peaks.get("hbm_gbs", 6775.3)
-    if precision_name == "fp64":
-        alu_peak, kern, src = FP64_PEAK_TFLOPS, "cpqr_kernel<double> (pivoted QR, FP64)", "nominal FP64 rate of GB300"
-    else:
-        alu_peak, kern, src = FP32_PEAK_TFLOPS, "cpqr_kernel<float> (pivoted QR, FP32 updates, FP64 norms)", \
-            "nominal FP32 rate of GB300 (152 SMs x 128 lanes x 2.07 GHz)"
-    traffic, traffic_src = qr_traffic(precision_name, sampler, shape)
+    apk, src = alu_peak(peaks, precision_name)
+    kern = ("cpqr_kernel<double> (pivoted QR, FP64)" if precision_name == "fp64"
+            else "cpqr_kernel<float> (pivoted QR, FP32 updates, FP64 norms)")
+    traffic, traffic_src = qr_traffic(precision_name, sampler, shape, workload_name)
     return {
         "kernel": kern, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
         "traffic": traffic, "traffic_unit": "bytes per step (all QR launches of one call)",
         "traffic_source": traffic_src,
         "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
         "streamed_gbs": streamed, "streamed_frac": streamed / hbm,
-        "alu": {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak, "source": src},
+        "alu": {"achieved": tflops, "peak": apk, "unit": "TFLOP/s", "frac": tflops / apk, "source": src},
         "dominant_phase": max(phase_ms, key=phase_ms.get),
         "phase_ms_per_step": {k: v / steps for k, v in phase_ms.items()},
         "qr_ms_per_step_by_round": [round(v / steps, 3) for v in prof.get("qr_ms_round", [])],
         "nodes_per_step_by_round": [int(v // steps) for v in prof.get("items_round", [])],
         "qr_flops_per_step": prof["qr_flops"] / steps, "qr_bytes_per_step": prof["qr_bytes"] / steps,
-        "eval": eval_roofline(prof, steps, precision_name, peaks, peak_src),
     }
 
 
-def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7):
-    """Full-block ID error of a seeded sample of nodes of one arm's result (outside the timed region)."""
+def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7, max_n=4096):
+    """Full-block ID error of a seeded sample of nodes of one arm's result (outside the timed region): nodes
+    of at most max_n sources (the FP64 error of a 65,536-source node against its whole far field takes
+    seconds)."""
     import numpy as np
     W = WORKLOAD
     h = ffc.tree_result_to_host(res)
     v = ffc.tree_result_views(res)
     nodes = h["node"]
-    pick = sorted(np.random.default_rng(seed).choice(len(nodes), min(n_sample, len(nodes)), replace=False).tolist())
     begin, count = tree.begin.cpu().numpy(), tree.count.cpu().numpy()
+    cand = np.flatnonzero(count[nodes] <= max_n)
+    pick = sorted(np.random.default_rng(seed).choice(cand, min(n_sample, cand.size), replace=False).tolist())
     errs = []
     for i in pick:
         node = int(nodes[i])
@@ -582,7 +669,7 @@ def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7):
                                                                                       dtype=torch.float64)
         errs.append(ffc.ffc_id_error(k, Pp, Pp[b:b + n], skel, T, r, rows=far))
     return {"nodes": [int(nodes[i]) for i in pick], "errors": errs, "mean_rank": float(h["rank"].mean()),
-            "mean_s": float(h["s"].mean())}
+            "mean_s": float(h["s"].mean()), "max_sources": int(max_n)}
 
 
 def accuracy_summary(per_arm):
@@ -595,6 +682,8 @@ def accuracy_summary(per_arm):
     for p, a in per_arm.items():
         e = np.asarray(a["errors"])
         out[p] = {"median_full_block_error": float(np.median(e)), "max_full_block_error": float(e.max()),
+                  "nodes_checked": int(e.size), "nodes_at_or_below_1e-6": int(np.sum(e <= 1e-6)),
+                  "fraction_at_or_below_1e-6": float(np.mean(e <= 1e-6)),
                   "nodes_at_or_below_1e-5": int(np.sum(e <= 1e-5)), "mean_rank": a["mean_rank"],
                   "mean_s": a["mean_s"]}
     for samp in ("learned", "uniform"):
@@ -606,38 +695,64 @@ def accuracy_summary(per_arm):
     return out
 
 
+def tune_parts(ffc, parts, prec, stream, proposal, max_step_s=1.5):
+    """The QR launch shape per part from the project's autotuner (untimed); a part whose single call takes
+    longer than max_step_s keeps the library defaults (tuning would cost minutes)."""
+    from paper_1409_2802_gb300 import autotune
+    import torch
+    kw, info = {}, {}
+    for p in parts:
+        select_workload(p.name)
+        prop = proposal[p.name] if isinstance(proposal, dict) else proposal
+        t0 = time.perf_counter()
+        r = ffc.ffc_compress_tree(p.Pp, p.tree, p.kern, precision=prec, stream=stream, proposal=prop,
+                                  **compress_kwargs())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        r.close()
+        if dt > max_step_s:
+            info[p.name] = {"source": f"library defaults (one call takes {dt:.1f} s, too long to tune here)"}
+            continue
+        try:
+            t = autotune.tune_tree(p.Pp, p.tree, p.kern, precision=prec, stream=stream, proposal=prop,
+                                   **compress_kwargs())
+            kw[p.name] = {k_: t[k_] for k_ in ("qr_big_min_s", "qr_l2_budget_mb")}
+            info[p.name] = dict(t, source="autotune")
+        except ffc.FFCError as e:
+            info[p.name] = {"source": f"library defaults (autotune failed: {e})"}
+    return kw, info
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_CONFIG, choices=sorted(CONFIGS),
+                    help="c3 (default): d = 128, Laplace and polynomial; c2: d = 16; c4: d = 1000 FP32; "
+                         "c3-laplace / c3-poly: one kernel of c3")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="precision of the timed form (value)")
     ap.add_argument("--sampler", default="learned", choices=["learned", "uniform"],
                     help="row sampler of the timed form; learned trains the proposal first (untimed)")
     ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--train-nodes", type=int, default=100, help="training leaves per generator (d=128, d=1000)")
-    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 uniform arm and the others")
+    ap.add_argument("--arm-steps", type=int, default=2, help="timed steps of the plain FP64 arm and other arms")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the plain FP64 uniform arm")
+    ap.add_argument("--all-arms", action="store_true", help="also time mixed + uniform and FP64 + learned")
+    ap.add_argument("--no-extra-configs", action="store_true", help="skip the other configurations")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=30.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-workers", type=int, default=0,
-                    help="oracle processes for the all-cores CPU baseline and the reference arm (0 = every host core)")
+                    help="oracle processes of the CPU baseline and the reference arm (0 = every host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the QR launch-shape autotuner (untimed, before the timed form's steps)")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                    help="c2 (default, the headline): d=16 mixture; c3-laplace / c3-poly: d=128; c4: d=1000 FP32")
-    ap.add_argument("--_cpu-leg", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    select_workload(args.workload)
-
-    if args._cpu_leg is not None:
-        return cpu_leg(args._cpu_leg)
 
     rank, world, local = _env_rank()
-    oracle = OracleStream() if (rank == 0 and world == 1 and not args.no_cpu_baseline and args.impl == "ours") else None
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 
@@ -650,113 +765,146 @@ def main():
     import workloads
     from paper_1409_2802_gb300 import ffc, learned
     ffc.lib()
-    proposal, train_info = None, None
+    peaks, peak_src = load_peaks()
+    peaks = dict(peaks, **measure_alu_peaks(torch, dev))
+    params, train_info = None, None
     if args.sampler == "learned":
         params, train_info = learned.train_standard(seed=0, epochs=args.train_epochs,
                                                     nodes_per_generator=args.train_nodes, device=dev)
-        proj = torch.as_tensor(workloads.projections(WORKLOAD["d"], seed=7)).to(dev)
-        proposal = (params, proj)
         torch.cuda.empty_cache()
-    P, tree, Pp, kern = build_inputs(torch, dev)
+
+    def proposal_for(parts):
+        if params is None:
+            return None
+        return {p.name: (params, torch.as_tensor(workloads.projections(WORKLOADS[p.name]["d"], seed=7)).to(dev))
+                for p in parts}
+
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prec = precision_code(ffc, args.precision)
-    peaks, peak_src = load_peaks()
+    arm = f"{args.precision}_{args.sampler}"
 
-    tuned = None
-    if not args.no_autotune:
-        from paper_1409_2802_gb300 import autotune
-        W = WORKLOAD
-        try:
-            tuned = autotune.tune_tree(Pp, tree, kern, precision=prec, stream=stream, tol=W["tol"],
-                                       min_level=W["min_level"], s0=W["s0"], s_max=W["s_max"], xi=W["xi"],
-                                       seed=W["sample_seed"], proposal=proposal)
-        except ffc.FFCError as e:             # the library's defaults then
-            print(f"autotune skipped: {e}", file=sys.stderr)
-            tuned = None
-    qr_kw = {k_: tuned[k_] for k_ in ("qr_big_min_s", "qr_l2_budget_mb")} if tuned else {}
-
-    def timed(prec_code, steps, warmup, prop, kw=None):
+    def timed(parts, prec_code, steps, warmup, prop, kw=None):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        res, times, prof = run_gpu_steps(torch, ffc, Pp, tree, kern, prec_code, steps, warmup, flush, stream,
-                                         proposal=prop, qr_kw=kw)
+        res, times, profs = run_gpu_steps(torch, ffc, parts, prec_code, steps, warmup, flush, stream, proposal=prop,
+                                          qr_kw=kw)
         torch.cuda.synchronize()
         total = max_over_ranks(sum(times), world, dev)
         if world > 1:
             torch.distributed.barrier()
-        return res, total, prof
+        return res, total, profs
 
+    def n_nodes_of(res):
+        return sum(int(ffc.tree_result_views(r)["n_out"]) for r in res.values())
+
+    def close_all(res):
+        for r in res.values():
+            r.close()
+
+    # ------------------------------------------------------------------ the headline configuration
+    parts = build_config_inputs(torch, dev, args.workload)
+    prop = proposal_for(parts)
+    qr_kw, tune_info = ({}, {p.name: {"source": "library defaults"} for p in parts}) if args.no_autotune else \
+        tune_parts(ffc, parts, prec, stream, prop)
     clocks = ClockSampler(local)
     clocks.start()
-    res, total_ms, prof = timed(prec, args.steps, args.warmup, proposal, qr_kw)
+    res, total_ms, profs = timed(parts, prec, args.steps, args.warmup, prop, qr_kw)
     clk = clocks.stop()
-    n_nodes = int(ffc.tree_result_views(res)["n_out"])
+    n_nodes = n_nodes_of(res)
     value = job_throughput(n_nodes, args.steps, world, total_ms)
-    arm = f"{args.precision}_{args.sampler}"
+    prof = combine_profiles(list(profs.values()))
+    roof = qr_roofline(prof, args.steps, args.precision, peaks, peak_src, args.sampler, None,
+                       CONFIGS[args.workload]["workload"])
+    evals = {}
+    for p in parts:
+        select_workload(p.name)
+        evals[p.name] = eval_roofline(profs[p.name], args.steps, args.precision, peaks, peak_src)
+    roof["eval"] = evals
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == ffc.FP64 else "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["workload"], "precision": args.precision, "sampler": args.sampler,
-                   "nodes": n_nodes, "levels": f"2..{tree.depth}", "kernel": kernel_label(kern.h),
-                   "points": WORKLOAD["points"], "tol": WORKLOAD["tol"],
-                   "s": "128 doubling to 2048", "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas x{world}"},
-        "clocks": clk, "gpu_launches": int(prof["launches"]),
-        "roofline": qr_roofline(prof, args.steps, args.precision, peaks, peak_src, args.sampler, qr_kw or None),
+        "config": config_block(args.workload, args.precision, args.sampler,
+                               {"nodes_per_step": n_nodes, "parallelism": f"replicas x{world}",
+                                "kernels": {p.name: part_label(p) for p in parts}}),
+        "clocks": clk, "gpu_launches": int(prof["launches"]), "roofline": roof,
     }
     if train_info is not None:
         line["config"]["proposal_training"] = train_info
-    line["config"]["qr_launch_shape"] = (dict(tuned, source="autotune (timed form; other arms: defaults)")
-                                         if tuned else {"source": "library defaults"})
-    # each arm's sampled errors are taken as soon as it has run and its result is released, so
-    # that only one arm's workspace is resident at a time
-    errors = {}
+    line["config"]["qr_launch_shape"] = tune_info
+    errors = {p.name: {} for p in parts}
     if not args.no_accuracy and rank == 0:
-        errors[arm] = arm_errors(torch, ffc, Pp, tree, kern, res)
-    res.close()
+        for p in parts:
+            select_workload(p.name)
+            errors[p.name][arm] = arm_errors(torch, ffc, p.Pp, p.tree, p.kern, res[p.name])
+    close_all(res)
     del res
+    # the plain FP64 GPU path on the same configuration (the speedup's reference point), and the other arms
     if not args.no_fp64_compare:
-        fsteps = max(3, args.steps // 3)
         arms = [("fp64", "uniform")]
-        if args.sampler == "learned":
+        if args.all_arms and args.sampler == "learned":
             arms += [("mixed", "uniform"), ("fp64", "learned")]
         other = {}
         for pname, sname in arms:
             key = f"{pname}_{sname}"
             if key == arm:
                 continue
-            r_, ms_, pf_ = timed(precision_code(ffc, pname), fsteps, 1, proposal if sname == "learned" else None)
-            v_ = job_throughput(n_nodes, fsteps, world, ms_)
-            other[key] = {"value": v_, "unit": UNIT, "ms_per_step": ms_ / fsteps, "steps": fsteps,
-                          "roofline": qr_roofline(pf_, fsteps, pname, peaks, peak_src, sname)}
+            r_, ms_, pf_ = timed(parts, precision_code(ffc, pname), args.arm_steps, 1,
+                                 prop if sname == "learned" else None)
+            v_ = job_throughput(n_nodes, args.arm_steps, world, ms_)
+            cp = combine_profiles(list(pf_.values()))
+            other[key] = {"value": v_, "unit": UNIT, "ms_per_step": ms_ / args.arm_steps, "steps": args.arm_steps,
+                          "warmup": 1, "phase_ms_per_step": {k: v / args.arm_steps for k, v in cp["ms"].items()},
+                          "qr_roofline_frac": qr_roofline(cp, args.arm_steps, pname, peaks, peak_src, sname)["frac"]}
             if not args.no_accuracy and rank == 0:
-                errors[key] = arm_errors(torch, ffc, Pp, tree, kern, r_)
-            r_.close()
+                for p in parts:
+                    select_workload(p.name)
+                    errors[p.name][key] = arm_errors(torch, ffc, p.Pp, p.tree, p.kern, r_[p.name])
+            close_all(r_)
             del r_
         if "fp64_uniform" in other:
             line["fp64_plain"] = other.pop("fp64_uniform")
             line["speedup_vs_fp64"] = value / line["fp64_plain"]["value"]
         if other:
             line["arms"] = other
-    if errors:
-        line["accuracy"] = accuracy_summary(errors)
+    if not args.no_accuracy and rank == 0:
+        line["accuracy"] = {name: accuracy_summary(e) for name, e in errors.items() if e}
     if not args.no_e2e:
-        line["e2e"] = run_e2e(torch, ffc, Pp, tree, kern, prec, max(3, args.steps // 2), 2, stream, proposal=proposal,
+        line["e2e"] = run_e2e(torch, ffc, parts, prec, max(2, min(3, args.steps)), 1, stream, proposal=prop,
                               qr_kw=qr_kw)
-    if oracle is not None:
-        single = finish_cpu_baseline(oracle, args.cpu_seconds, "on a host core while the GPU steps ran")
-        # every host core, after the GPU work (so that it does not compete with the GPU process's host thread)
+    del parts
+    torch.cuda.empty_cache()
+    # ------------------------------------------------------------------ the other configurations
+    if not args.no_extra_configs and args.workload == DEFAULT_CONFIG:
+        extra = {}
+        for cname in ("c2", "c4"):
+            cparts = build_config_inputs(torch, dev, cname)
+            cprop = proposal_for(cparts)
+            r1, ms1, pf1 = timed(cparts, prec, args.arm_steps, 1, cprop)
+            nn = n_nodes_of(r1)
+            close_all(r1)
+            v1 = job_throughput(nn, args.arm_steps, world, ms1)
+            ent = {"workload": CONFIGS[cname]["workload"], "value": v1, "unit": UNIT, "steps": args.arm_steps,
+                   "warmup": 1, "ms_per_step": ms1 / args.arm_steps, "nodes_per_step": nn,
+                   "phase_ms_per_step": {k: v / args.arm_steps for k, v in combine_profiles(list(pf1.values()))["ms"].items()}}
+            if not args.no_fp64_compare:
+                r2, ms2, _ = timed(cparts, ffc.FP64, args.arm_steps, 1, None)
+                close_all(r2)
+                v2 = job_throughput(nn, args.arm_steps, world, ms2)
+                ent["fp64_plain"] = {"value": v2, "ms_per_step": ms2 / args.arm_steps, "steps": args.arm_steps}
+                ent["speedup_vs_fp64"] = v1 / v2
+            extra[cname] = ent
+            del cparts
+            torch.cuda.empty_cache()
+        line["extra_configs"] = extra
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            multi = finish_cpu_baseline(OracleStream(args.cpu_workers or host_cores()),
-                                        min(20.0, args.cpu_seconds), "on the host cores after the GPU work")
+            line["cpu_baseline"] = cpu_baseline_leg(args.workload, args.cpu_workers or host_cores(), args.cpu_seconds)
         except (OSError, RuntimeError) as e:
-            multi = {"value": None, "sample": f"all-cores oracle failed: {e}"}
-        # a window in which no node finished (large blocks) says nothing: keep the longer single-core one
-        line["cpu_baseline"] = multi if multi.get("value") else single
-        line["cpu_baseline_single_core"] = single
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "kind": "oracle", "cores": 0,
+                                    "sample": f"oracle pool failed: {e}"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

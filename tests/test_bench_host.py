@@ -12,9 +12,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_the_contract_line():
     """The oracle over a pool of two processes (the arm's default is every host core)."""
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0", "--cpu-workers", "2"], capture_output=True, text=True, timeout=600,
-                         cwd=ROOT)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--cpu-workers", "2", "--workload", "c2"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
@@ -24,8 +24,10 @@ def test_reference_arm_prints_the_contract_line():
     assert line["metric"] == bench.METRIC and line["unit"] == "nodes/s" and line["higher_is_better"] is True
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"] == bench.WORKLOADS["c2"]["workload"]
+    assert line["config"]["workload"] == bench.CONFIGS["c2"]["workload"]
     assert line["cpu_baseline"]["cores"] == 2
+    # each step is one complete pass over the same fixed sample
+    assert line["cpu_baseline"]["sample"].startswith("16 nodes (16 of c2)")
 
 
 def test_traffic_record_applies_only_to_its_kernel_source_and_workload(tmp_path, monkeypatch):
@@ -64,11 +66,28 @@ def test_eval_roofline_bound_by_path():
     bench.select_workload("c2")
 
 
-def test_oracle_stream_over_worker_processes():
-    """The all-cores CPU baseline: a pool of single-threaded oracle processes, closed with its group."""
-    bench.select_workload("c2")
-    cb = bench.finish_cpu_baseline(bench.OracleStream(2), 4.0, "test")
-    assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] is not None and cb["value"] > 0
+def test_oracle_sample_and_cpu_baseline_pool():
+    """The oracle legs' node sample (the two deepest levels, fixed by the seed) and the all-cores CPU
+    baseline: complete passes over it by a pool of single-threaded oracle processes."""
+    items = bench.oracle_sample("c3")
+    assert [p for p, _ in items] == ["c3-laplace"] * 16 + ["c3-poly"] * 16
+    assert all(510 <= nd <= 2046 for _, nd in items)                  # levels 9 and 10 of the depth-10 tree
+    assert items == bench.oracle_sample("c3")
+    cb = bench.cpu_baseline_leg("c2", 2, 0.5)
+    assert cb["cores"] == 2 and cb["kind"] == "oracle" and cb["value"] > 0 and "1 passes" in cb["sample"]
+
+
+def test_combined_profiles_and_measured_alu_peaks():
+    p1 = {"ms": {"sample": 1.0, "eval": 2.0, "qr": 3.0, "trsm": 4.0, "bookkeeping": 0.5}, "launches": 10,
+          "qr_launches": 2, "qr_flops": 1e9, "eval_flops": 2e9, "qr_bytes": 3e9, "qr_ms_round": [1.0] * 8,
+          "items_round": [2] * 8}
+    c = bench.combine_profiles([p1, p1])
+    assert c["ms"]["qr"] == 6.0 and c["launches"] == 20 and c["qr_bytes"] == 6e9 and c["items_round"][0] == 4
+    r = bench.qr_roofline(c, 2, "mixed", {"hbm_gbs": 6000.0, "fp32_tflops": 60.0, "fp32_tflops_how": "probe"},
+                          "measured")
+    assert abs(r["achieved"] - 3e9 / (3.0 / 1e3) / 1e9) < 1e-9 and r["alu"]["peak"] == 60.0
+    assert r["alu"]["source"].startswith("measured") and r["peak"] == 6000.0
+    assert bench.qr_roofline(c, 2, "fp64", {}, "measured")["alu"]["peak"] == bench.FP64_PEAK_TFLOPS
 
 
 def test_autotuner_search_order_and_fallback(monkeypatch):
