@@ -303,6 +303,12 @@ typedef struct {
    * qr_l2_budget_mb: bytes of sampled blocks per cooperative QR launch, in MB (default 96) */
   int32_t qr_big_min_s;
   int32_t qr_l2_budget_mb;
+  /* qr_panel: panel width of the pivoted QR. 0 or 1 = unblocked, the library's default (every step
+   *   updates the trailing matrix); 2..8 = the blocked form with that width (the trailing matrix is
+   *   only read at each step and updated once per panel; a panel also ends early once the pivot norm
+   *   falls below a quarter of the panel's first; rounds whose CTAs own more than 128 columns each
+   *   stay unblocked). Same pivots and outputs up to rounding. */
+  int32_t qr_panel;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2), the learned proposal

@@ -225,17 +225,23 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   const int kcap = (int)std::min<int64_t>(r_max, std::min(s, n));
   if (n == 0) { *rank_host = 0; *r22_rel_host = 0.0; return FFC_OK; }
   const int sm = std::max<int64_t>(s, 1) > 0 ? (int)std::max<int64_t>(s, 1) : 1;
-  const int cap = cpqr_max_ctas(precision, sm);
+  // the blocked QR (panel width nb) when the columns are 16-byte aligned
+  const size_t esz = precision == FFC_MIXED ? sizeof(float) : sizeof(double);
+  const bool aligned = (reinterpret_cast<uintptr_t>(K_dev) % 16 == 0) && ((size_t)ldk * esz) % 16 == 0;
+  const int nb = aligned ? qr_panel(precision, sm, -1) : 1;
+  const int cap = cpqr_max_ctas(precision, sm, -1, nb);
   FFC_REQUIRE(cap > 0, "ffc_id: the QR kernel cannot be resident on this device");
   FFC_REQUIRE(cpqr_min_group(n) <= cap, "ffc_id: n = %lld columns exceed what the QR can hold", (long long)n);
   const int g = std::min(cap, std::max(cpqr_min_group(n), group_size(s, n, 4096)));
+  const int nbl = (n + g - 1) / g <= QR_FS_COLS ? nb : 1;   // the blocked form keeps each CTA's F rows on chip
   const int rc_cap = std::max(kcap, 1);
   Arena ar;
   size_t bytes = 16 * 256 + round_up(sizeof(CpqrItem)) + round_up(sizeof(TrsmItem)) +
                  round_up(sizeof(CtaAssign) * g) + round_up(sizeof(int32_t) * rc_cap) +
                  round_up(sizeof(double) * rc_cap) + 2 * round_up(sizeof(double) * n) + round_up((size_t)n) +
                  round_up(sizeof(Slot) * 2 * g) + round_up((size_t)rc_cap * rc_cap * sizeof(double)) +
-                 round_up(12 * sizeof(unsigned long long));
+                 round_up(12 * sizeof(unsigned long long)) +
+                 (nbl > 1 ? round_up((size_t)n * QR_F_STRIDE * esz) : 0);
   FFC_CUDA(cudaMallocAsync((void**)&ar.base, bytes, st));
   CpqrItem* d_item = ar.take<CpqrItem>(1);
   TrsmItem* d_titem = ar.take<TrsmItem>(1);
@@ -252,10 +258,12 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   int32_t* rank = ar.take<int32_t>(1);
   double* r22 = ar.take<double>(1);
   int32_t* status = ar.take<int32_t>(1);
+  char* Fbuf = nbl > 1 ? ar.take<char>((size_t)n * QR_F_STRIDE * esz) : nullptr;
   CpqrItem hi = {};
   hi.A = K_dev; hi.lda = ldk; hi.s = (int32_t)s; hi.n = (int32_t)n; hi.r_max = kcap; hi.tol = tol;
   hi.piv = piv; hi.beta = beta; hi.vn1 = vn1; hi.vn2 = vn2; hi.selected = sel; hi.slots = slots;
   hi.barrier = barrier; hi.red = red; hi.rank_out = rank; hi.r22_out = r22; hi.status_out = status;
+  hi.F = Fbuf;
   std::vector<CtaAssign> asg(g);
   for (int c = 0; c < g; ++c) asg[c] = CtaAssign{0, c, g, 0};
   TrsmItem ti = {};
@@ -270,7 +278,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   FFC_CUDA(cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 12, st));
   FFC_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
   FFC_CUDA(cudaMemsetAsync(rank, 0, sizeof(int32_t), st));
-  ffc_status rc = launch_cpqr(precision, d_item, d_assign, g, (int)std::max<int64_t>(s, 1), st);
+  ffc_status rc = launch_cpqr(precision, d_item, d_assign, g, (int)std::max<int64_t>(s, 1), st, nullptr, -1, nbl);
   if (rc != FFC_OK) return rc;
   rc = launch_trsm_batched(precision, d_titem, 1, trsm_tiles(n), rc_cap, st);
   if (rc != FFC_OK) return rc;

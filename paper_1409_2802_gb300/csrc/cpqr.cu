@@ -896,10 +896,405 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
   for (int j = tid; j < ncols; j += QR_THREADS) it.selected[c0 + j] = sels[j];
 }
 
+// Shared-memory row stride of the blocked form's V (a multiple of 8 elements, 8 spare) and its offset
+// (after the unblocked form's arrays, 256-byte aligned).
+__host__ __device__ constexpr int qr_ldv(int s_max) { return ((s_max + 7) & ~7) + 8; }
+template <typename T>
+__host__ __device__ constexpr size_t qr_blocked_off(int s_max) {
+  return (QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) +
+          (size_t)((s_max > 1 ? s_max : 1) + 8) * sizeof(T) + 255) & ~size_t(255);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Blocked variant (the trailing matrix is read, not written, at every step).
+//
+// Within a panel of nb steps starting at step k0 the stored columns keep their
+// panel-start values in rows >= the current step (rows above are R, written as
+// each step's pivot row). With the panel's reflectors V (s x nb, shared memory,
+// every CTA its own copy) and F (n x nb, global, F(c, t) = tau_t (current
+// column c)^T v_t), the current column is A(:, c) - V F(c, :)^T, so step
+// k = k0 + j needs, for every free column, one dot product with the stored
+// column (read only): F(c, j) = tau (A(k:s, c)^T v - F(c, 0:j) w),
+// w = V(k:s, 0:j)^T v; then the pivot row A(k, c) -= V(k, 0:j+1) F(c, 0:j+1)^T
+// and the FP64 norm downdate. The pivot column itself is formed as
+// A(k:s, p) - V(k:s, 0:j) F(p, 0:j)^T. At the end of a panel every CTA applies
+// A(k_end:s, c) -= V F(c, :)^T to its columns once (skipped after the last
+// step: the trailing rows are never read again). Pivots, stopping rule and
+// outputs are those of the unblocked form (Businger-Golub order, LAPACK
+// reflectors); only rounding differs.
+constexpr int QR_NB_MAX = QR_F_STRIDE;   // panel width bound; F rows are padded to it
+constexpr int QR_BLOCKED_MIN_S = 1024;   // smallest round (rows) the library blocks by default
+
+// Blocked form, step k (panel step j): for NC owned columns per warp pass, the dot product of the
+// stored rows [kb, s) with v (M vectors per lane held in registers: one round of loads), then lane c
+// finishes column c: F(c, j) = tau (dot - F(c, 0:j) w), the pivot row A(k, c) -= V(k, 0:j+1) F(c, 0:j+1)^T,
+// the FP64 norm downdate (an unsafe one recomputes the current rows k+1..s-1 from the stored column and
+// the panel) and the pivot key. With CHUNK, columns longer than 32 W M rows stream in chunks.
+template <typename T, int NC, int M, bool CHUNK>
+__device__ __forceinline__ void blocked_columns(T* __restrict__ A, int64_t lda, T* __restrict__ F,
+                                                T* __restrict__ Fs, int nb, int c0, int ncols,
+                                                const uint8_t* __restrict__ sels, const T* __restrict__ vj,
+                                                const T* __restrict__ Vs, int ldv, const T* __restrict__ wsh, T ttau,
+                                                bool apply, int k, int j, int s, int warp, int lane, double tol3z,
+                                                double* __restrict__ vn1s, double* __restrict__ vn2s,
+                                                unsigned long long& key, Fix128& psum, int emax) {
+  using V4 = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int kb = k & ~(W - 1);
+  for (int jj0 = warp * NC; jj0 < ncols; jj0 += QR_WARPS * NC) {
+    bool va[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) va[c] = (jj0 + c < ncols) && !sels[jj0 + c];
+    T acc[NC], akr[NC];   // dot products; the stored A(k, c) from the first chunk's registers
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { acc[c] = (T)0; akr[c] = (T)0; }
+    if (apply) {
+      for (int cb = kb; cb < s; cb += 32 * W * M) {
+        V4 x[NC][M];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const int r0 = cb + W * (lane + 32 * m);
+            x[c][m] = (va[c] && r0 < s) ? *reinterpret_cast<const V4*>(A + (int64_t)(c0 + jj0 + c) * lda + r0)
+                                        : V4{};
+          }
+        if (cb == kb) {
+          // row k sits in lane 0's first vector, component k - kb
+#pragma unroll
+          for (int c = 0; c < NC; ++c) akr[c] = __shfl_sync(0xffffffffu, vget(x[c][0], k - kb), 0);
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int r0 = cb + W * (lane + 32 * m);
+          if (r0 < s) {
+            const V4 vv = *reinterpret_cast<const V4*>(vj + r0);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+              const T ve = r0 + e < s ? vget(vv, e) : (T)0;
+#pragma unroll
+              for (int c = 0; c < NC; ++c) acc[c] = fma(ve, vget(x[c][m], e), acc[c]);
+            }
+          }
+        }
+        if (!CHUNK) break;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
+    T dotc = acc[0], akc = akr[0];
+    bool mine = va[0] && lane == 0;
+#pragma unroll
+    for (int c = 1; c < NC; ++c)
+      if (lane == c) { dotc = acc[c]; akc = akr[c]; mine = va[c]; }
+    const int jc = jj0 + lane;
+    int unsafe = 0;
+    if (mine) {
+      T* col = A + (int64_t)(c0 + jc) * lda;
+      T* fs = Fs + jc * nb;
+      T corr = (T)0, rowc = (T)0;
+      for (int t = 0; t < j; ++t) {
+        const T ft = fs[t];
+        corr = fma(ft, wsh[t], corr);
+        rowc = fma(Vs[(int64_t)t * ldv + k], ft, rowc);
+      }
+      const T fcj = apply ? ttau * (dotc - corr) : (T)0;
+      fs[j] = fcj;
+      F[(int64_t)(c0 + jc) * QR_F_STRIDE + j] = fcj;   // for the CTAs that take this column as a pivot
+      const T ak = (apply ? akc : col[k]) - rowc - fcj;   // V(k, j) = 1 (and F(c, j) = 0 when H = I)
+      col[k] = ak;
+      const double akd = (double)ak;
+      const double rest = fma(-akd, akd, vn1s[jc]);
+      if (rest <= tol3z * vn2s[jc]) unsafe = 1;
+      else vn1s[jc] = rest;
+    }
+    unsigned um = __ballot_sync(0xffffffffu, unsafe);
+    while (um) {   // recompute the current norm of rows k+1..s-1 (rare)
+      const int src = __ffs(um) - 1;
+      um &= um - 1u;
+      const int jr = jj0 + src;
+      const T* col = A + (int64_t)(c0 + jr) * lda;
+      const T* fs = Fs + jr * nb;
+      double nr = 0.0;
+      for (int i = k + 1 + lane; i < s; i += 32) {
+        T x = col[i];
+        for (int t = 0; t <= j; ++t) x = fma(-Vs[(int64_t)t * ldv + i], fs[t], x);
+        nr = fma((double)x, (double)x, nr);
+      }
+      nr = warp_sum(nr);
+      if (lane == 0) { vn1s[jr] = nr; vn2s[jr] = nr; }
+    }
+    __syncwarp();
+    if (mine) {
+      const double v = vn1s[jc];
+      const unsigned long long kj = pivot_key(v, c0 + jc);
+      key = kj > key ? kj : key;
+      fix_add(psum, v, emax);
+    }
+  }
+}
+
+template <typename T, bool BIG>
+__device__ void factor_item_blocked(const CpqrItem& it, const CtaAssign a, double* __restrict__ vn1s,
+                                    double* __restrict__ vn2s, uint8_t* __restrict__ sels, T* __restrict__ Vs,
+                                    int ldv, T* __restrict__ wsh, T* __restrict__ fsh, T* __restrict__ Fs, int nb,
+                                    QrShared& sh, long long spin_limit) {
+  using V4 = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int s = it.s, n = it.n;
+  T* __restrict__ A = reinterpret_cast<T*>(it.A);
+  T* __restrict__ F = reinterpret_cast<T*>(it.F);
+  const int64_t lda = it.lda;
+  const int c0 = (int)((int64_t)n * a.rank / a.g), c1 = (int)((int64_t)n * (a.rank + 1) / a.g);
+  const int ncols = c1 - c0;
+  StepSlot* slots = reinterpret_cast<StepSlot*>(it.slots);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+  const int kmax = min(it.r_max, min(s, n));
+  const double TOL3Z = sizeof(T) == 4 ? 2.44140625e-04 : 1.0536712127723509e-08;
+
+  for (int j = warp; j < ncols; j += QR_WARPS) {
+    const double nr = column_norm2<T>(A + (int64_t)(c0 + j) * lda, 0, s, lane);
+    if (lane == 0) { vn1s[j] = nr; vn2s[j] = nr; sels[j] = 0; }
+  }
+  __syncthreads();
+  {
+    unsigned long long key = 0ull;
+    double part = 0.0;
+    for (int j = tid; j < ncols; j += QR_THREADS) {
+      const unsigned long long kj = pivot_key(vn1s[j], c0 + j);
+      key = kj > key ? kj : key;
+      part += vn1s[j];
+    }
+    cta_reduce(key, part, sh);
+  }
+
+  int k = 0, k0 = 0;
+  double pn0 = 0.0;   // squared norm of the current panel's first pivot
+  for (;; ++k) {
+    // ---- group winner and ||R22||^2 of step k (as in the unblocked form)
+    if (tid == 0) {
+      sh.stop = 0;
+      if (a.g > 1) {
+        if (k == 0) {
+          StepSlot* sl = slots + a.rank;
+          sl->key = sh.key;
+          sl->sum = sh.sum;
+        } else {
+          red_publish(it.red + 4 * (k % 3), sh.key, sh.fsum);
+        }
+        if (!group_barrier(it.barrier, (unsigned)a.g * (unsigned)(k + 1), spin_limit)) {
+          sh.stop = 1;
+          sh.status = FFC_E_TIMEOUT;
+        } else if (k > 0) {
+          unsigned long long kk;
+          Fix128 f;
+          red_read(it.red + 4 * (k % 3), kk, f);
+          sh.key = kk;
+          sh.fsum = f;
+          if (a.rank == 0) {
+            unsigned long long* z = it.red + 4 * ((k + 2) % 3);
+            z[0] = 0ull; z[1] = 0ull; z[2] = 0ull; z[3] = 0ull;
+          }
+        }
+      } else if (k == 0) {
+        sh.emax = min(dbl_exponent(sh.sum) + 11, 2046);
+      }
+    }
+    __syncthreads();
+    if (a.g > 1 && !sh.stop && k == 0 && warp == 0) {
+      unsigned long long kk = 0ull;
+      int emax = 1;
+      for (int t = lane; t < a.g; t += 32) emax = max(emax, dbl_exponent(__ldcg(&slots[t].sum)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      emax = min(emax + 11, 2046);
+      if (lane == 0) sh.emax = emax;
+      Fix128 f = {0ull, 0ull};
+      for (int t = lane; t < a.g; t += 32) {
+        const unsigned long long kt = __ldcg(&slots[t].key);
+        kk = kt > kk ? kt : kk;
+        fix_add(f, __ldcg(&slots[t].sum), emax);
+      }
+      kk = warp_max_u64(kk);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        Fix128 g2;
+        g2.hi = __shfl_xor_sync(0xffffffffu, f.hi, o);
+        g2.lo = __shfl_xor_sync(0xffffffffu, f.lo, o);
+        fix_add(f, g2);
+      }
+      if (lane == 0) { sh.key = kk; sh.sum = fix_value(f, emax); }
+    }
+    __syncthreads();
+    if (tid == 0 && !sh.stop) {
+      bool reached;
+      if (k == 0) {
+        sh.fro2 = sh.sum;
+        Fix128 t = {0ull, 0ull};
+        if (it.tol > 0.0) fix_add(t, it.tol * it.tol * sh.fro2, sh.emax);
+        sh.thr = t;
+        reached = it.tol > 0.0 && sh.sum <= it.tol * it.tol * sh.fro2;
+      } else {
+        reached = it.tol > 0.0 && fix_le(sh.fsum, sh.thr);
+      }
+      if (reached) {
+        sh.stop = 1;
+        sh.status = FFC_OK;
+      } else if (k >= kmax || (sh.key >> 20) == 0ull) {
+        sh.stop = 1;
+        sh.status = it.tol > 0.0 ? FFC_E_TOL_NOT_REACHED : FFC_OK;
+      }
+    }
+    __syncthreads();
+    if (sh.stop) break;
+    const int p = 0xFFFFF - (int)(sh.key & 0xFFFFFull);
+    const int j = k - k0;   // step within the panel
+    T* __restrict__ vj = Vs + (int64_t)j * ldv;
+    // the pivot's squared norm (the key's top bits); at a panel's first step it bounds every free column
+    const double pk2 = __longlong_as_double((long long)(sh.key & ~0xFFFFFull));
+    if (j == 0) pn0 = pk2;
+
+    // ---- the pivot column's current rows k..s-1 into V(:, j): A(:, p) - V(:, 0:j) F(p, 0:j)^T
+    if (tid < j) fsh[tid] = __ldcg(F + (int64_t)p * QR_NB_MAX + tid);
+    __syncthreads();
+    {
+      const T* cp = A + (int64_t)p * lda;
+      T part = (T)0;
+      const int kb = k & ~(W - 1);
+      const int iend = min(ldv, ((s + 7) & ~7) + 8);
+      for (int i = kb + tid; i < iend; i += QR_THREADS) {
+        T x = (T)0;
+        if (i >= k && i < s) {
+          x = __ldcg(cp + i);
+          for (int t = 0; t < j; ++t) x = fma(-Vs[(int64_t)t * ldv + i], fsh[t], x);
+          if (i > k) part = fma(x, x, part);
+        }
+        vj[i] = x;   // rows kb..k-1 and the padding past s are zero
+      }
+      part = warp_sum(part);
+      if (lane == 0) {
+        if (sizeof(T) == 8) sh.dw[warp] = (double)part; else sh.fw[warp] = (float)part;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T xn2 = (T)0;
+      for (int w = 0; w < QR_WARPS; ++w) xn2 += sizeof(T) == 8 ? (T)sh.dw[w] : (T)sh.fw[w];
+      const T alpha = vj[k];
+      if (xn2 == (T)0) {
+        sh.tau = 0.0;
+        sh.tauf = 0.0f;
+        sh.apply = 0;
+        sh.beta = (double)alpha;
+        vj[k] = (T)0;   // H = I: v is not used (tau = 0), the scale below must not touch it
+      } else {
+        const T nrm = sqrt(fma(alpha, alpha, xn2));
+        const T beta = alpha >= (T)0 ? -nrm : nrm;
+        const T tt = (beta - alpha) / beta;
+        sh.tau = (double)tt;
+        sh.tauf = (float)tt;
+        sh.apply = 1;
+        sh.beta = (double)beta;
+        vj[k] = (T)1 / (alpha - beta);   // the scale, read below, then replaced by 1
+      }
+      if (a.rank == 0) { it.piv[k] = p; it.beta[k] = sh.beta; }
+      if (p >= c0 && p < c1) sels[p - c0] = 1;
+    }
+    __syncthreads();
+    const bool apply = sh.apply != 0;
+    if (apply) {
+      const T scale = vj[k];
+      for (int i = k + 1 + tid; i < s; i += QR_THREADS) vj[i] = vj[i] * scale;
+    }
+    __syncthreads();
+    if (tid == 0) vj[k] = apply ? (T)1 : (T)0;
+    __syncthreads();
+    // w(t) = V(k:s, t)^T v_j for the panel's earlier reflectors (warp t, t + 8, ...)
+    for (int t = warp; t < j; t += QR_WARPS) {
+      const T* vt = Vs + (int64_t)t * ldv;
+      T acc = (T)0;
+      for (int i = k + lane; i < s; i += 32) acc = fma(vt[i], vj[i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) wsh[t] = acc;
+    }
+    __syncthreads();
+
+    // ---- owned free columns: F(c, j), the pivot row, the norm downdate; 4 columns per warp pass
+    const T ttau = sizeof(T) == 8 ? (T)sh.tau : (T)sh.tauf;
+    const int emax = sh.emax;
+    unsigned long long key = 0ull;
+    Fix128 psum = {0ull, 0ull};
+    const int vrows = s - (k & ~(W - 1));
+#define FFC_BCOLS(NC_, M_, CH_)                                                                              \
+  blocked_columns<T, NC_, M_, CH_>(A, lda, F, Fs, nb, c0, ncols, sels, vj, Vs, ldv, wsh, ttau, apply, k, j, s, \
+                                   warp, lane, TOL3Z, vn1s, vn2s, key, psum, emax)
+    if (vrows <= 32 * W) FFC_BCOLS(8, 1, false);
+    else if (vrows <= 64 * W) FFC_BCOLS(4, 2, false);
+    else if (vrows <= 128 * W) FFC_BCOLS(2, 4, false);
+    else if (vrows <= 256 * W) FFC_BCOLS(1, 8, false);
+    else if (BIG && vrows <= 512 * W) FFC_BCOLS(1, 16, false);
+    else FFC_BCOLS(1, 8, true);
+#undef FFC_BCOLS
+    __syncthreads();   // every F(c, j) and pivot-row write of this CTA is done
+
+    // ---- end of the panel: apply it to the rows below once (not after the last step). A panel also
+    // ends once the pivot norm has fallen below a quarter of the panel's first: the current column is
+    // formed as the panel-start column minus V F^T, whose rounding scales with the panel-start norm
+    // (bounded by the first pivot's), so this keeps that error within 4x of the unblocked form's for
+    // every column that competes for the next pivot. The rule reads only the group-wide pivot norms.
+    const bool last = (k + 1 >= kmax);
+    if ((j + 1 == nb || pk2 * 16.0 < pn0) && !last) {
+      const int jn = j + 1, kend = k + 1;
+      const int kbe = kend & ~(W - 1);
+      for (int jc = warp; jc < ncols; jc += QR_WARPS) {
+        if (sels[jc]) continue;
+        T* col = A + (int64_t)(c0 + jc) * lda;
+        const T* fr = Fs + jc * nb;
+        for (int r0 = kbe + W * lane; r0 < s; r0 += 32 * W) {
+          V4 x = *reinterpret_cast<const V4*>(col + r0);
+          for (int t = 0; t < jn; ++t) {
+            const V4 vt = *reinterpret_cast<const V4*>(Vs + (int64_t)t * ldv + r0);
+            const T ft = fr[t];
+#pragma unroll
+            for (int e = 0; e < W; ++e) vset(x, e, fma(-vget(vt, e), ft, vget(x, e)));
+          }
+          // rows below kend only (rows kbe..kend-1 are R and stay), rows past s untouched
+#pragma unroll
+          for (int e = 0; e < W; ++e)
+            if (r0 + e < kend || r0 + e >= s) vset(x, e, col[min(r0 + e, s - 1)]);
+          if (r0 + W <= s && r0 >= kend) {
+            *reinterpret_cast<V4*>(col + r0) = x;
+          } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+              if (r0 + e >= kend && r0 + e < s) col[r0 + e] = vget(x, e);
+          }
+        }
+      }
+      k0 = k + 1;
+      __syncthreads();
+    }
+    cta_reduce_fix(key, psum, sh);
+  }
+
+  if (tid == 0) {
+    if (sh.status == FFC_E_TIMEOUT) atomicExch(it.status_out, (int)FFC_E_TIMEOUT);
+    if (a.rank == 0) {
+      *it.rank_out = k;
+      const double fin = k == 0 ? sh.sum : fix_value(sh.fsum, sh.emax);
+      *it.r22_out = sh.fro2 > 0.0 ? sqrt(fin) / sqrt(sh.fro2) : 0.0;
+      if (sh.status != FFC_E_TIMEOUT) atomicCAS(it.status_out, (int)FFC_OK, sh.status);
+    }
+  }
+  for (int j = tid; j < ncols; j += QR_THREADS) it.selected[c0 + j] = sels[j];
+}
+
 template <typename T, bool BIG>
 __global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
 cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
-            const int32_t* __restrict__ cta_off, long long spin_limit) {
+            const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb) {
+  (void)s_max;
+  (void)nb;
   // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries
   // (QR_NCOL_MAX T), recompute list (QR_NCOL_MAX int16), selected flags
   // (QR_NCOL_MAX bytes), Householder vector (s_max T)
@@ -919,6 +1314,34 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
     if (threadIdx.x == 0) sh.status = FFC_OK;
     __syncthreads();
     factor_item<T, BIG>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh, spin_limit);
+    __syncthreads();
+  }
+}
+
+// The blocked form (every item has F; columns 16-byte aligned): CTA work lists as in cpqr_kernel.
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
+cpqr_blocked_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
+                    const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  double* vn1s = reinterpret_cast<double*>(qsm);
+  double* vn2s = vn1s + QR_NCOL_MAX;
+  uint8_t* sels = reinterpret_cast<uint8_t*>(vn2s + QR_NCOL_MAX);
+  // the panel's reflectors V (nb x ldv), w (QR_NB_MAX) and F rows (QR_NB_MAX, then one per warp)
+  const int ldv = qr_ldv(s_max);
+  T* Vs = reinterpret_cast<T*>(qsm + qr_blocked_off<T>(s_max));
+  T* wsh = Vs + (size_t)nb * ldv;
+  T* fsh = wsh + QR_NB_MAX;
+  T* Fs = fsh + QR_NB_MAX * (1 + QR_WARPS);   // F rows of the CTA's columns (QR_FS_COLS x nb)
+  __shared__ QrShared sh;
+  const int e0 = cta_off ? cta_off[blockIdx.x] : (int)blockIdx.x;
+  const int e1 = cta_off ? cta_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
+  for (int e = e0; e < e1; ++e) {
+    const CtaAssign a = entries[e];
+    const CpqrItem it = items[a.item];
+    if (threadIdx.x == 0) sh.status = FFC_OK;
+    __syncthreads();
+    factor_item_blocked<T, BIG>(it, a, vn1s, vn2s, sels, Vs, ldv, wsh, fsh, Fs, nb, sh, spin_limit);
     __syncthreads();
   }
 }
@@ -1069,23 +1492,39 @@ bool qr_big(int s_max, int big) {
   return big < 0 ? s_max >= QR_BIG_MIN_S_DEFAULT : big != 0;
 }
 
+using QrKernel = void (*)(const CpqrItem*, const CtaAssign*, const int32_t*, long long, int, int);
+
 template <typename T>
-size_t cpqr_smem_bytes(int s_max) {
-  // the Householder vector is last; 8 spare elements keep the vector loads of
-  // its final (partial) 16-byte group inside the allocation
-  return QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) +
-         (size_t)(std::max(s_max, 1) + 8) * sizeof(T);
+QrKernel qr_kernel_fn(int s_max, int big, int nb) {
+  const bool b = qr_big<T>(s_max, big);
+  if (nb > 1) return b ? cpqr_blocked_kernel<T, true> : cpqr_blocked_kernel<T, false>;
+  return b ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+}
+
+template <typename T>
+size_t cpqr_smem_bytes(int s_max, int nb = 1) {
+  // the Householder vector follows the per-column arrays; 8 spare elements keep the vector loads of its
+  // final (partial) 16-byte group inside the allocation; the blocked form's arrays come after it
+  const size_t base = QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) +
+                      (size_t)(std::max(s_max, 1) + 8) * sizeof(T);
+  if (nb <= 1) return base;
+  return qr_blocked_off<T>(s_max) +
+         ((size_t)nb * qr_ldv(s_max) + QR_NB_MAX * (2 + QR_WARPS) + (size_t)QR_FS_COLS * nb) * sizeof(T);
 }
 
 template <typename T>
 ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const int32_t* cta_off, int grid,
-                         int s_max, cudaStream_t st, int big) {
+                         int s_max, cudaStream_t st, int big, int nb) {
   if (s_max > 2048) {
     set_error("cpqr: s = %d exceeds the supported 2048 rows", s_max);
     return FFC_E_INVALID;
   }
-  const size_t smem = cpqr_smem_bytes<T>(s_max);
-  auto kfn = qr_big<T>(s_max, big) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+  if (nb < 1 || nb > QR_PANEL_MAX) {
+    set_error("cpqr: panel width %d outside [1, %d]", nb, QR_PANEL_MAX);
+    return FFC_E_INVALID;
+  }
+  const size_t smem = cpqr_smem_bytes<T>(s_max, nb);
+  auto kfn = qr_kernel_fn<T>(s_max, big, nb);
   FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1097,15 +1536,15 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off, wait_limit()));
+  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off, wait_limit(), s_max, nb));
   return FFC_OK;
 }
 
 template <typename T>
-int max_ctas_t(int s_max, int big) {
+int max_ctas_t(int s_max, int big, int nb) {
   int per_sm = 0;
-  const size_t smem = cpqr_smem_bytes<T>(s_max);
-  auto kfn = qr_big<T>(s_max, big) ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
+  const size_t smem = cpqr_smem_bytes<T>(s_max, nb);
+  auto kfn = qr_kernel_fn<T>(s_max, big, nb);
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, QR_THREADS, smem);
   return per_sm * sm_count();
@@ -1134,15 +1573,33 @@ int64_t trsm_tiles(int64_t n) { return (n + TS_COLS - 1) / TS_COLS; }
 
 int cpqr_min_group(int64_t n) { return (int)std::max<int64_t>(1, (n + QR_NCOL_MAX - 1) / QR_NCOL_MAX); }
 
-int cpqr_max_ctas(int precision, int s_max, int big) {
-  return precision == FFC_MIXED ? max_ctas_t<float>(s_max, big) : max_ctas_t<double>(s_max, 0);
+int cpqr_max_ctas(int precision, int s_max, int big, int nb) {
+  return precision == FFC_MIXED ? max_ctas_t<float>(s_max, big, nb) : max_ctas_t<double>(s_max, 0, nb);
+}
+
+int qr_panel(int precision, int s_max, int big, bool blocked) {
+  // The library's default is the unblocked form: on the L2-resident sub-batches the rounds run in, a
+  // step is bound by its synchronisation (the blocked form halves the bytes a step moves but adds
+  // serial phases between block barriers and measured slower). With `blocked`, the widest panel that
+  // fits: FP32 rounds from s = 1,024 on (smaller rounds are latency bound; FP64 is FMA bound).
+  if (!blocked || precision != FFC_MIXED || s_max < QR_BLOCKED_MIN_S) return 1;
+  // V gets about 68 KB of shared memory with 2 CTAs per SM, 40 KB with 3; a power of two <= 32
+  const size_t esz = precision == FFC_MIXED ? sizeof(float) : sizeof(double);
+  const bool two = precision == FFC_MIXED && qr_big<float>(s_max, big);
+  const size_t budget = two ? (68u << 10) : (40u << 10);
+  // FP32 panels wider than 8 let the within-panel cancellation (panel-start column minus V F^T) move
+  // the tolerance stop by several ranks; up to 8 it stays within one rank of the unblocked form
+  const int nb_cap = QR_PANEL_MAX;
+  int nb = 1;
+  while (2 * nb <= nb_cap && (size_t)(2 * nb) * qr_ldv(s_max) * esz <= budget) nb *= 2;
+  return nb;
 }
 
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid, int s_max,
-                       cudaStream_t st, const int32_t* cta_off, int big) {
+                       cudaStream_t st, const int32_t* cta_off, int big, int nb) {
   if (grid <= 0) return FFC_OK;
-  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st, big);
-  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st, 0);
+  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st, big, nb);
+  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st, 0, nb);
 }
 
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,

@@ -118,6 +118,7 @@ struct CpqrItem {
   int32_t* rank_out;
   double* r22_out;      // ||R22||_F / ||K'||_F
   int32_t* status_out;
+  void* F;              // blocked form: n x 32 (T) panel coefficients, or NULL for the unblocked form
 };
 
 struct CtaAssign { int32_t item, rank, g, pad; };
@@ -257,9 +258,15 @@ ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, in
 // entries: per-CTA work lists (CTA b runs entries[cta_off[b] .. cta_off[b+1]) in order), or with
 // cta_off == NULL one entry per CTA.
 // big: the register-resident variant (mixed precision only; -1 = the default rule s_max >= 1024)
+// nb: panel width of the blocked form (items with F set; 1 = every item unblocked); qr_panel() gives the
+// library's default for a round of s_max rows
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
-                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr, int big = -1);
-int cpqr_max_ctas(int precision, int s_max, int big = -1);
+                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr, int big = -1, int nb = 1);
+int cpqr_max_ctas(int precision, int s_max, int big = -1, int nb = 1);
+int qr_panel(int precision, int s_max, int big, bool blocked = false);
+constexpr int QR_F_STRIDE = 32;   // elements per column of the blocked form's F
+constexpr int QR_PANEL_MAX = 8;   // widest panel of the blocked form
+constexpr int QR_FS_COLS = 128;   // most columns one CTA of the blocked form may own (their F rows are on chip)
 constexpr int QR_BIG_MIN_S_DEFAULT = 1024;
 constexpr int QR_L2_BUDGET_MB_DEFAULT = 96;
 int cpqr_min_group(int64_t n);   // fewest CTAs a group of n columns may have (per-CTA column cap)

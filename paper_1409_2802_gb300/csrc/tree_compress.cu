@@ -402,7 +402,10 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   }
   const int big_min = P.qr_big_min_s > 0 ? P.qr_big_min_s : QR_BIG_MIN_S_DEFAULT;
   const int big = (P.precision == FFC_MIXED && s_nom >= big_min) ? 1 : 0;
-  const int cap = cpqr_max_ctas(P.precision, (int)s_nom, big);
+  // the blocked QR needs 16-byte aligned columns (ld = s_nom elements)
+  int nb = P.qr_panel > 0 ? P.qr_panel : qr_panel(P.precision, (int)s_nom, big);
+  if (((size_t)s_nom * esz) % 16 != 0) nb = 1;
+  const int cap = cpqr_max_ctas(P.precision, (int)s_nom, big, nb);
   if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
   // The round's QR runs as one cooperative launch per sub-batch of
   // consecutive items whose blocks together fit in QR_L2_BUDGET bytes: the
@@ -427,7 +430,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     sb.push_back(W);
   }
   const int n_sb = (int)sb.size() - 1;
-  std::vector<int> sb_grid(n_sb), sb_as(n_sb), sb_coff(n_sb);
+  std::vector<int> sb_grid(n_sb), sb_as(n_sb), sb_coff(n_sb), sb_nb;
   std::vector<int32_t> hoff;
   std::vector<CtaAssign> ha;
   int64_t G = 0;
@@ -453,6 +456,10 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
       Gsum += g[q];
     }
     const int grid = shared_ctas ? cap : (int)Gsum;
+    int ncmax = 0;
+    for (int q = q0; q < q1; ++q)
+      ncmax = std::max<int>(ncmax, (int)((R->count_h[items[q]] + g[q] - 1) / g[q]));
+    sb_nb.push_back(ncmax <= QR_FS_COLS ? nb : 1);
     std::vector<std::vector<CtaAssign>> lists(grid);
     int64_t ptr = 0;
     for (int q = q0; q < q1; ++q) {
@@ -488,7 +495,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
                o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
                o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
-               o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W);
+               o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W),
+               o_F = L.add<char>(nb > 1 ? (size_t)SN * QR_F_STRIDE * esz : 0);
   if (L.off > R->ws_bytes) {
     if (R->ws) {
       FFC_CUDA(cudaStreamSynchronize(st));
@@ -529,6 +537,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   int32_t* flags = (int32_t*)(b + o_flag);
   int32_t* oidx = (int32_t*)(b + o_oidx);
   int32_t* trank = (int32_t*)(b + o_trank);
+  char* Fbuf = nb > 1 ? (char*)(b + o_F) : nullptr;
 
   std::vector<SampleItem> hs(W);
   std::vector<EvalItem> he(W);
@@ -555,6 +564,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     qi.slots = slots + 2 * goff[q]; qi.red = red + 12 * (size_t)q; qi.barrier = bar + q; qi.rank_out = qrank + q;
     qi.r22_out = qr22 + q;
     qi.status_out = qst + q;
+    qi.F = Fbuf ? (void*)(Fbuf + (size_t)noff[q] * QR_F_STRIDE * esz) : nullptr;
     TrsmItem& ti = ht[q];
     ti = TrsmItem{};
     ti.A = (void*)((char*)K + esz * koff[q]); ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = trank + q; ti.piv = qi.piv; ti.beta = qi.beta;
@@ -594,7 +604,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
   // one cooperative QR launch per L2-sized sub-batch of the round
   for (int bb = 0; bb < n_sb; ++bb) {
-    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb], big);
+    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb], big,
+                     sb_nb[bb]);
     if (rc != FFC_OK) return rc;
   }
   const int qr_launches = n_sb;
@@ -668,6 +679,8 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   const ffc_params& P = *params;
   FFC_REQUIRE(P.precision == FFC_FP64 || P.precision == FFC_MIXED, "ffc_compress_tree: bad precision");
   FFC_REQUIRE(P.s0 >= 2 && P.s_max >= P.s0 && P.s_max <= 2048, "ffc_compress_tree: need 2 <= s0 <= s_max <= 2048");
+  FFC_REQUIRE(P.qr_panel >= 0 && P.qr_panel <= QR_PANEL_MAX, "ffc_compress_tree: qr_panel must be in [0, %d]",
+              QR_PANEL_MAX);
   FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");

@@ -67,7 +67,7 @@ class c_params(ctypes.Structure):
                 ("s0", ctypes.c_int32), ("s_max", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
                 ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
-                ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32)]
+                ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -337,10 +337,10 @@ class TreeResult:
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
-                      qr_l2_budget_mb=0, sampler: int | None = None) -> TreeResult:
+                      qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0) -> TreeResult:
     """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
-    ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``: the QR's
-    launch shape (0 = the library's defaults; see ``autotune``)."""
+    ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``, ``qr_panel``:
+    the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``)."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
@@ -352,7 +352,7 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
         sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
                  ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
-                 int(qr_l2_budget_mb))
+                 int(qr_l2_budget_mb), int(qr_panel))
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))

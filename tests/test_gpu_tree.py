@@ -183,3 +183,33 @@ def test_qr_launch_shape_and_autotuner():
     assert len(best["table"]) == len(autotune.BIG_MIN_S) + len(autotune.L2_BUDGET_MB) - 1
     assert best["ms"] == min(r.get("ms", float("inf")) for r in best["table"]
                              if r["qr_big_min_s"] == best["qr_big_min_s"])
+
+
+@pytest.mark.parametrize("precision", [ffc.FP64, ffc.MIXED])
+def test_blocked_qr_panels_agree(precision):
+    """The QR's panel width changes only rounding: unblocked (1), narrow (2) and wide (8) panels give the
+    same samples, ranks, statuses and skeletons in FP64 (integer pivot keys on the same FP64 norms up to
+    rounding) and the same residuals and T to rounding; mixed precision agrees within its FP32 rounding."""
+    P = workloads.gaussian_mixture(N=8192, d=8, k=4, seed=12)
+    t_o = o_tree.build_tree(P, 256)
+    t_g = ffc.ffc_build_tree(cu(P), 256)
+    Pp = P[t_o.perm]
+    k = ffc.Kernel(ffc.GAUSSIAN, h=1.5)
+    outs = [ffc.tree_result_to_host(ffc.ffc_compress_tree(cu(Pp), t_g, k, tol=1e-6, s0=64, s_max=1024,
+                                                          precision=precision, qr_panel=nb)) for nb in (1, 2, 8)]
+    if precision == ffc.FP64:
+        for o in outs[1:]:
+            for key in ("rank", "s", "status", "skel"):
+                assert np.array_equal(outs[0][key], o[key]), key
+            # ||R22|| / ||K'|| from FP64 norm downdates in another order: agreement to ~1e-15 of ||K'||
+            assert np.max(np.abs(o["r22_rel"] - outs[0]["r22_rel"])) <= 1e-12
+            assert np.allclose(o["T"], outs[0]["T"], rtol=1e-7, atol=1e-10 * np.max(np.abs(outs[0]["T"])))
+        # and every node against the oracle with the blocked panel
+        ko = o_kernels.Kernel(o_kernels.GAUSSIAN, h=1.5)
+        nodes = [i for i in range(t_o.n_nodes) if t_o.level[i] >= 2]
+        _compare_nodes(outs[2], t_o, Pp, ko, 1e-6, nodes[::2], 64, 1024)
+    else:
+        for o in outs[1:]:
+            same = o["s"] == outs[0]["s"]
+            assert np.mean(same) >= 0.98
+            assert np.max(np.abs(o["r22_rel"][same] - outs[0]["r22_rel"][same])) <= 1e-6
