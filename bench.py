@@ -644,6 +644,23 @@ def qr_roofline(prof, steps, precision_name, peaks, peak_src, sampler="learned",
     }
 
 
+def trsm_roofline(ffc, results, trsm_ms_per_step, peaks):
+    """The FP64 triangular solve T = R11^-1 R12 against the measured FP64 peak: r^2 (n - r) flops per node
+    (one multiply-add per entry of R11 above the diagonal and column of R12, counted as 2 flops over half
+    the triangle), from the final ranks of every node of every part."""
+    flops = 0.0
+    for res in results:
+        h = ffc.tree_result_to_host(res)
+        r = h["rank"].astype("float64")
+        n = (h["skel_off"][1:] - h["skel_off"][:-1]).astype("float64")
+        flops += float((r * r * (n - r)).sum())
+    tf = flops / (trsm_ms_per_step / 1e3) / 1e12 if trsm_ms_per_step > 0 else 0.0
+    peak, src = alu_peak(peaks, "fp64")
+    return {"kernel": "trsm_kernel (blocked back-substitution, FP64)", "bound": "alu", "achieved": tf, "peak": peak,
+            "unit": "TFLOP/s", "frac": tf / peak, "flops_per_step": flops, "ms_per_step": trsm_ms_per_step,
+            "peak_source": src}
+
+
 def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7, max_n=4096):
     """Full-block ID error of a seeded sample of nodes of one arm's result (outside the timed region): nodes
     of at most max_n sources (the FP64 error of a 65,536-source node against its whole far field takes
@@ -822,6 +839,7 @@ def main():
         select_workload(p.name)
         evals[p.name] = eval_roofline(profs[p.name], args.steps, args.precision, peaks, peak_src)
     roof["eval"] = evals
+    roof["trsm"] = trsm_roofline(ffc, list(res.values()), prof["ms"]["trsm"] / args.steps, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",

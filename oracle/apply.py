@@ -145,3 +145,67 @@ def direct_sum_without_self(kernel: Kernel, Xp, q, log_scale=0.0):
     K = kernel_values(kernel, Xp, Xp, log_scale)
     np.fill_diagonal(K, 0.0)
     return K @ np.asarray(q, dtype=np.float64)
+
+
+def nested_skeleton_charges(tree, results: dict, q, min_level=2):
+    """Skeleton charges of every node of a nested compression (compress.compress_tree_nested), from the
+    leaves up: q~_b = P_b q_cols with q_cols the leaf's charges, or the children's skeleton charges
+    (a child without a usable ID contributes its points' charges)."""
+    from .compress import usable
+    q = np.asarray(q, dtype=np.float64)
+    qt = {}
+    for level in range(tree.depth, min_level - 1, -1):
+        for b in range(tree.n_nodes):
+            if tree.level[b] != level:
+                continue
+            bg, n = int(tree.begin[b]), int(tree.count[b])
+            if level == tree.depth:
+                qc = q[bg:bg + n]
+            else:
+                parts = []
+                for ch in (2 * b + 1, 2 * b + 2):
+                    cb, cn = int(tree.begin[ch]), int(tree.count[ch])
+                    parts.append(qt[ch] if usable(results[ch]) else q[cb:cb + cn])
+                qc = np.concatenate(parts)
+            r = results[b]
+            qt[b] = skeleton_charges(r.skel_perm, r.T, qc) if usable(r) else None
+    return qt
+
+
+def nested_tree_potential(kernel: Kernel, Xp, tree, q, results: dict, xi=1.0, min_level=2, near=True,
+                          log_scale=0.0, targets=None):
+    """tree_potential with the nested representations: node b's skeleton points are its points
+    cols_b[skel_b[0:r_b]] and its charges come from nested_skeleton_charges."""
+    from .compress import usable
+    qt = nested_skeleton_charges(tree, results, q, min_level)
+    ids = {}
+    for b, r in results.items():
+        if usable(r):
+            ids[b] = (r.cols[r.skel_perm], r.T, r.rank, qt[b])
+    Xp = np.asarray(Xp, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    pos = np.arange(len(Xp)) if targets is None else np.asarray(targets, dtype=np.int64)
+    u = np.zeros(pos.size)
+    far, covered = interaction_masks(Xp, tree, xi, min_level, pos)
+    for b in far:
+        bg, n = int(tree.begin[b]), int(tree.count[b])
+        sel = np.flatnonzero(far[b] & ~covered[b])
+        if sel.size == 0:
+            continue
+        if b in ids:
+            pts, _, r, qtb = ids[b]
+            u[sel] += kernel_values(kernel, Xp[pos[sel]], Xp[bg + pts[:r]], log_scale) @ qtb
+        else:
+            u[sel] += kernel_values(kernel, Xp[pos[sel]], Xp[bg:bg + n], log_scale) @ q[bg:bg + n]
+    if near:
+        for b in far:
+            if tree.level[b] != tree.depth:
+                continue
+            bg, n = int(tree.begin[b]), int(tree.count[b])
+            sel = np.flatnonzero(~far[b] & ~covered[b])
+            if sel.size == 0:
+                continue
+            Kb = kernel_values(kernel, Xp[pos[sel]], Xp[bg:bg + n], log_scale)
+            Kb[pos[sel][:, None] == np.arange(bg, bg + n)[None, :]] = 0.0
+            u[sel] += Kb @ q[bg:bg + n]
+    return u

@@ -53,6 +53,7 @@ class NodeResult:
     far_count: int
     status: int
     attempts: list = field(default_factory=list)   # s values tried
+    cols: np.ndarray | None = None                   # nested form: node-local points of the ID's columns
 
 
 @dataclass
@@ -67,11 +68,16 @@ def rank_cap(s_eff: int, n: int, all_rows: bool, r_cap: int) -> int:
 
 
 def compress_node(Xp, tree, node, kernel: Kernel, tol, seed, s0=128, s_max=2048, xi=1.0,
-                  proposal: Proposal | None = None, ranked_rows=None):
+                  proposal: Proposal | None = None, ranked_rows=None, cols=None):
+    """The sampled-row ID of one node; ``cols`` (node-local point indices) restricts the ID's columns to
+    those points (the nested form), default all of the node's points. skel_perm indexes the columns."""
     b, c = int(tree.begin[node]), int(tree.count[node])
     far = far_field_mask(Xp, tree.centroid[node], tree.radius[node], xi, b, b + c)
     far_count = int(far.sum())
     X_node = Xp[b:b + c]
+    if cols is not None:
+        X_node = X_node[np.asarray(cols, dtype=np.int64)]
+        c = X_node.shape[0]
     r_cap = s_max // 2
     s = s0
     tried = []
@@ -109,3 +115,49 @@ def compress_tree(Xp, tree, kernel: Kernel, tol, seed=0, min_level=2, s0=128, s_
         nodes = [i for i in range(tree.n_nodes) if tree.level[i] >= min_level]
     return [compress_node(Xp, tree, i, kernel, tol, seed, s0, s_max, proposal=proposal)
             for i in nodes]
+
+
+# ---------------------------------------------------------------------------
+# Nested skeletonization (the upward pass of a treecode built on these IDs, §2
+# "outgoing representation of each node by combining the representations of its
+# children"; ASKIT, §1): levels are compressed from the leaves up. A leaf's ID
+# has the leaf's points as its columns; a node above has its children's skeleton
+# points as its columns (left child's, then right child's, each in its pivot
+# order), so its skeleton is a subset of theirs and its charges are
+# q~ = P [q~_left; q~_right]. A child without a usable ID (status other than OK
+# or TOL_NOT_REACHED, or no far field) contributes all of its points. Rows: the
+# node's own far-field sample, as in the plain form.
+
+def usable(res: NodeResult) -> bool:
+    return res.status in (STATUS_OK, STATUS_TOL_NOT_REACHED) and res.s > 0
+
+
+def nested_columns(tree, node, results: dict):
+    """Node-local point indices of the ID columns of `node` in the nested form."""
+    b = int(tree.begin[node])
+    if tree.level[node] == tree.depth:
+        return np.arange(int(tree.count[node]), dtype=np.int64)
+    cols = []
+    for ch in (2 * node + 1, 2 * node + 2):
+        cb, cn = int(tree.begin[ch]), int(tree.count[ch])
+        rc = results[ch]
+        if usable(rc):
+            own = rc.cols[rc.skel_perm[:rc.rank]]
+        else:
+            own = np.arange(cn, dtype=np.int64)
+        cols.append(own + (cb - b))
+    return np.concatenate(cols).astype(np.int64)
+
+
+def compress_tree_nested(Xp, tree, kernel: Kernel, tol, seed=0, min_level=2, s0=128, s_max=2048):
+    """Every node at level >= min_level, from the deepest level up; result.cols holds each node's columns."""
+    results = {}
+    for level in range(tree.depth, min_level - 1, -1):
+        for node in range(tree.n_nodes):
+            if tree.level[node] != level:
+                continue
+            cols = nested_columns(tree, node, results)
+            r = compress_node(Xp, tree, node, kernel, tol, seed, s0, s_max, cols=cols)
+            r.cols = cols
+            results[node] = r
+    return results
