@@ -309,6 +309,13 @@ typedef struct {
    *   falls below a quarter of the panel's first; rounds whose CTAs own more than 128 columns each
    *   stay unblocked). Same pivots and outputs up to rounding. */
   int32_t qr_panel;
+  /* nested: 0 = every node's ID has all of the node's points as its columns; 1 = nested skeletonization
+   *   (the upward pass of a treecode, §2; ASKIT, §1): levels are compressed from the deepest up, a leaf's
+   *   columns are its points and a node's columns are its children's skeleton points (left child's,
+   *   then right child's, each in pivot order; a child without an ID of status FFC_OK or
+   *   FFC_E_TOL_NOT_REACHED contributes all of its points). Rows are the node's own far-field sample
+   *   either way. */
+  int32_t nested;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2), the learned proposal
@@ -366,6 +373,9 @@ typedef struct {
   const int32_t* skel_dev;       /* node-local column indices, as ffc_id */
   const int64_t* T_off_dev;      /* node i's T starts at T_dev[T_off[i]], ld = rank */
   const double* T_dev;
+  const int32_t* ncols_dev;      /* number of ID columns of node i (its point count unless nested) */
+  const int32_t* cols_dev;       /* node i's columns (node-local point indices) at cols_dev[skel_off[i]];
+                                    skel indexes these: skeleton point k is cols[skel[k]] */
 } ffc_tree_view;
 
 ffc_status ffc_tree_result_view(const ffc_tree_result* result, ffc_tree_view* view);
@@ -383,15 +393,20 @@ void ffc_tree_result_free(ffc_tree_result* result);
  * contains y while no ancestor at level >= min_level has y in its far field;
  * a leaf reached with no such node on its path is a near leaf. Every source
  * other than y is counted once. mode FFC_APPLY_SKELETON uses each node's ID
- * (q~ = P q, x~ its skeleton points; a node whose status is neither FFC_OK
- * nor FFC_E_TOL_NOT_REACHED is summed from its sources); FFC_APPLY_DIRECT sums
+ * (q~ = P q_cols, x~ its skeleton points; q_cols = the charges of the ID's
+ * columns: its points' charges, or for a nested compression the children's
+ * skeleton charges, computed from the leaves up; a node whose status is
+ * neither FFC_OK nor FFC_E_TOL_NOT_REACHED, or without rows, is summed from
+ * its sources); FFC_APPLY_DIRECT sums
  * every far node from its sources: the exact value the representation
  * approximates. The kernel, xi, min_level and s_max are those of the
  * compression that produced `result` (same tree, same points). qt_dev:
  * skeleton charges, output node i's r_i values at qt + i (s_max / 2)
  * (capacity n_out (s_max / 2) doubles; written in skeleton mode, may be NULL
  * in direct mode). u_dev: N doubles. log_scale as in ffc_potential. FP64
- * arithmetic. Requires 2^min_level + 2 depth + 2 <= 96. Asynchronous.
+ * arithmetic. Requires 2^min_level + 2 depth + 2 <= 96. Skeleton mode
+ * allocates (cudaMallocAsync) and frees a buffer of one double per ID column
+ * and synchronises `stream` once; direct mode is asynchronous.
  */
 typedef enum { FFC_APPLY_SKELETON = 0, FFC_APPLY_DIRECT = 1 } ffc_apply_mode;
 ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N, int32_t d, const ffc_tree* tree,

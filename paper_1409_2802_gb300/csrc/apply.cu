@@ -86,19 +86,51 @@ __device__ void charges_body(const ChargeItem& it, int rhs) {
 
 __global__ void __launch_bounds__(CH_THREADS) charges_kernel(ChargeItem it) { charges_body(it, blockIdx.y); }
 
-// Every compressed node of a tree result: block i takes output node i (heap id first + i), its
-// packed T (ld r) and its charges q[begin .. begin + n) in tree order; q~ goes to qt + i rcap.
+__device__ __forceinline__ bool usable_id(int status, int s) {
+  return (status == FFC_OK || status == FFC_E_TOL_NOT_REACHED) && s > 0;
+}
+
+// The charges of the ID columns of the output nodes [o0, o1) (one level), into qc at skel_off: the
+// points' charges q[begin + cols[c]], or, nested above the leaves, the children's skeleton charges (a
+// child without a usable ID: its points' charges), in the order of the columns.
+__global__ void gather_qcols_kernel(int64_t o0, int64_t first, int nested_parent, int64_t rcap,
+                                    const int64_t* __restrict__ begin, const int64_t* __restrict__ count,
+                                    const int32_t* __restrict__ rank, const int32_t* __restrict__ status,
+                                    const int32_t* __restrict__ sv, const int64_t* __restrict__ skel_off,
+                                    const int32_t* __restrict__ ncols, const int32_t* __restrict__ cols,
+                                    const double* __restrict__ q, const double* __restrict__ qt,
+                                    double* __restrict__ qc) {
+  const int64_t o = o0 + blockIdx.x, b = first + o;
+  double* dst = qc + skel_off[o];
+  if (!nested_parent) {
+    for (int c = threadIdx.x; c < ncols[o]; c += blockDim.x) dst[c] = q[begin[b] + cols[skel_off[o] + c]];
+    return;
+  }
+  int64_t c = 0;
+  for (int64_t ch = 2 * b + 1; ch <= 2 * b + 2; ++ch) {
+    const int64_t oc = ch - first;
+    if (usable_id(status[oc], sv[oc])) {
+      for (int k = threadIdx.x; k < rank[oc]; k += blockDim.x) dst[c + k] = qt[oc * rcap + k];
+      c += rank[oc];
+    } else {
+      for (int64_t j = threadIdx.x; j < count[ch]; j += blockDim.x) dst[c + j] = q[begin[ch] + j];
+      c += count[ch];
+    }
+  }
+}
+
+// Output nodes [o0, o1): block i takes node o0 + i, its packed T (ld r) and its column charges (qc at
+// skel_off); q~ goes to qt + o rcap.
 __global__ void __launch_bounds__(CH_THREADS)
-charges_tree_kernel(int64_t first, int64_t rcap, const int64_t* __restrict__ begin, const int32_t* __restrict__ rank,
-                    const int32_t* __restrict__ status, const int64_t* __restrict__ skel_off,
-                    const int32_t* __restrict__ skel, const int64_t* __restrict__ T_off, const double* __restrict__ T,
-                    const double* __restrict__ q, double* __restrict__ qt) {
-  const int64_t i = blockIdx.x;
-  const int st = status[i];
-  if (st != FFC_OK && st != FFC_E_TOL_NOT_REACHED) return;   // such a node is evaluated from its sources
+charges_tree_kernel(int64_t o0, int64_t rcap, const int32_t* __restrict__ rank, const int32_t* __restrict__ status,
+                    const int32_t* __restrict__ sv, const int64_t* __restrict__ skel_off,
+                    const int32_t* __restrict__ ncols, const int32_t* __restrict__ skel,
+                    const int64_t* __restrict__ T_off, const double* __restrict__ T, const double* __restrict__ qc,
+                    double* __restrict__ qt) {
+  const int64_t i = o0 + blockIdx.x;
+  if (!usable_id(status[i], sv[i])) return;   // such a node is evaluated from its sources
   const int r = rank[i];
-  ChargeItem it{skel + skel_off[i], T + T_off[i], r > 0 ? r : 1, r, (int32_t)(skel_off[i + 1] - skel_off[i]),
-                q + begin[first + i], 0, qt + i * rcap, 0};
+  ChargeItem it{skel + skel_off[i], T + T_off[i], r > 0 ? r : 1, r, ncols[i], qc + skel_off[i], 0, qt + i * rcap, 0};
   charges_body(it, 0);
 }
 
@@ -167,6 +199,8 @@ struct TreeApplyArgs {
   const int32_t* status;
   const int64_t* skel_off;
   const int32_t* skel;
+  const int32_t* cols;      // the ID's columns (node-local points) at skel_off
+  const int32_t* sv;        // rows sampled per node (0: no ID)
   const double* q;          // N charges, tree order
   const double* qt;         // skeleton charges, node i at qt + i rcap
   double* u;
@@ -223,15 +257,16 @@ __global__ void __launch_bounds__(AP_THREADS) tree_apply_kernel(TreeApplyArgs a,
     if (any_far) {
       const int64_t o = b - a.first;
       const int st = a.status[o];
-      const bool skel_ok = a.mode == FFC_APPLY_SKELETON && (st == FFC_OK || st == FFC_E_TOL_NOT_REACHED);
+      const bool skel_ok = a.mode == FFC_APPLY_SKELETON && usable_id(st, a.sv[o]);
       const int64_t ns = skel_ok ? a.rank[o] : n;
       const int32_t* sk = a.skel + a.skel_off[o];
+      const int32_t* cl = a.cols + a.skel_off[o];
       const double* w = skel_ok ? a.qt + o * a.rcap : a.q + bg;
       for (int64_t c0 = 0; c0 < ns; c0 += kp_max) {
         const int kp = (int)std::min<int64_t>(kp_max, ns - c0);
         for (int e = threadIdx.x; e < kp * d; e += AP_THREADS) {
           const int c = e / d, j = e % d;
-          const int64_t src = bg + (skel_ok ? sk[c0 + c] : c0 + c);
+          const int64_t src = bg + (skel_ok ? cl[sk[c0 + c]] : c0 + c);
           xs[e] = ld_point(X + src * d + j);
         }
         for (int c = threadIdx.x; c < kp; c += AP_THREADS) ws[c] = w[c0 + c];
@@ -340,10 +375,25 @@ ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N,
   cudaStream_t st = as_stream(stream);
   const int64_t rcap = P->s_max / 2;
   const int64_t first = tree_result_first_node(result);
+  double* qc = nullptr;
   if (mode == FFC_APPLY_SKELETON) {
-    charges_tree_kernel<<<(unsigned)v.n_out, CH_THREADS, 0, st>>>(first, rcap, tree->begin_dev, v.rank_dev,
-                                                                 v.status_dev, v.skel_off_dev, v.skel_dev,
-                                                                 v.T_off_dev, v.T_dev, q_dev, qt_dev);
+    // column charges (skel_off layout, total = the skeleton buffer's length) and the skeleton charges,
+    // a level at a time from the deepest (a nested node's columns are its children's skeletons)
+    int64_t tot = 0;
+    FFC_CUDA(cudaMemcpyAsync(&tot, v.skel_off_dev + v.n_out, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FFC_CUDA(cudaStreamSynchronize(st));
+    FFC_CUDA(cudaMallocAsync((void**)&qc, sizeof(double) * std::max<int64_t>(tot, 1), st));
+    for (int L = tree->depth; L >= P->min_level; --L) {
+      const int64_t o0 = ((int64_t)1 << L) - 1 - first, o1 = ((int64_t)1 << (L + 1)) - 1 - first;
+      const int nested_parent = P->nested && L < tree->depth;
+      gather_qcols_kernel<<<(unsigned)(o1 - o0), 128, 0, st>>>(o0, first, nested_parent, rcap, tree->begin_dev,
+                                                               tree->count_dev, v.rank_dev, v.status_dev, v.s_dev,
+                                                               v.skel_off_dev, v.ncols_dev, v.cols_dev, q_dev,
+                                                               qt_dev, qc);
+      charges_tree_kernel<<<(unsigned)(o1 - o0), CH_THREADS, 0, st>>>(o0, rcap, v.rank_dev, v.status_dev, v.s_dev,
+                                                                      v.skel_off_dev, v.ncols_dev, v.skel_dev,
+                                                                      v.T_off_dev, v.T_dev, qc, qt_dev);
+    }
     FFC_CUDA(cudaGetLastError());
   }
   TreeApplyArgs a{};
@@ -351,7 +401,7 @@ ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N,
   a.near_field = near_field ? 1 : 0; a.N = N; a.first = first; a.rcap = rcap; a.xi = P->xi;
   a.log_scale = log_scale; a.begin = tree->begin_dev; a.count = tree->count_dev; a.centroid = tree->centroid_dev;
   a.radius = tree->radius_dev; a.rank = v.rank_dev; a.status = v.status_dev; a.skel_off = v.skel_off_dev;
-  a.skel = v.skel_dev; a.q = q_dev; a.qt = qt_dev; a.u = u_dev;
+  a.skel = v.skel_dev; a.cols = v.cols_dev; a.sv = v.s_dev; a.q = q_dev; a.qt = qt_dev; a.u = u_dev;
   const int kp = chunk_points(d);
   const size_t smem = chunk_smem(d);
   const unsigned grid = (unsigned)((N + AP_THREADS - 1) / AP_THREADS);
@@ -362,7 +412,9 @@ ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N,
     FFC_CUDA(cudaFuncSetAttribute(tree_apply_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tree_apply_kernel<float><<<grid, AP_THREADS, smem, st>>>(a, (const float*)points_perm_dev, kp);
   }
-  FFC_CUDA(cudaGetLastError());
+  const cudaError_t e = cudaGetLastError();
+  if (qc) FFC_CUDA(cudaFreeAsync(qc, st));
+  if (e != cudaSuccess) return cuda_fail(e, "tree_apply_kernel");
   return FFC_OK;
 }
 

@@ -14,6 +14,7 @@
 // triangular solve, epilogue); only the epilogue's per-node "needs a larger
 // sample" flags come back to the host, once per round.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -44,6 +45,12 @@ struct ffc_tree_result {
   // packed at the end of each call into Tp (node i at Tp_off[i], r_i x (n_i - r_i), ld r_i)
   double* Tp = nullptr;
   int64_t *Tp_off = nullptr, *count_dev = nullptr;
+  // ID columns per node (node-local point indices at skel_off): identity unless nested
+  int32_t *cols = nullptr, *ncols = nullptr;
+  int64_t* ncols64 = nullptr;          // the same counts as int64, for the packing of T
+  std::vector<int64_t> ncols_h;
+  std::vector<int32_t> cols_h;         // host copy of cols
+  bool cols_custom = false;            // cols differ from the identity (a nested call ran)
   // round workspace (grow-only)
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -72,6 +79,26 @@ struct Layout {
     return o;
   }
 };
+
+// Nested form: the column points of item q (cols of its node, node-local) copied to rows xoff.. of the
+// arena, so that the block evaluation reads them as a contiguous source range.
+struct GatherItem {
+  int64_t xoff, begin;
+  const int32_t* cols;
+  int64_t n;
+};
+
+__global__ void gather_cols_kernel(const GatherItem* __restrict__ items, const void* __restrict__ X,
+                                   void* __restrict__ Xc, int d, size_t esz) {
+  const GatherItem it = items[blockIdx.y];
+  const int64_t tot = it.n * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / d, j = e % d;
+    const int64_t src = (it.begin + it.cols[c]) * d + j, dst = (it.xoff + c) * d + j;
+    if (esz == sizeof(double)) reinterpret_cast<double*>(Xc)[dst] = reinterpret_cast<const double*>(X)[src];
+    else reinterpret_cast<float*>(Xc)[dst] = reinterpret_cast<const float*>(X)[src];
+  }
+}
 
 __global__ void patch_kernel(int W, const int64_t* s_out, int64_t s_nom, int r_cap, EvalItem* ev, CpqrItem* qr) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +195,8 @@ ffc_status alloc_outputs(ffc_tree_result* R) {
          o_fc = L.add<int64_t>(n), o_rows_off = L.add<int64_t>(n + 1), o_rows = L.add<int64_t>(rows_cap),
          o_skel_off = L.add<int64_t>(n + 1), o_skel = L.add<int32_t>(skel_cap), o_T_off = L.add<int64_t>(n + 1),
          o_T = L.add<double>(T_cap), o_Tp = L.add<double>(T_cap), o_Tp_off = L.add<int64_t>(n + 1),
-         o_cnt = L.add<int64_t>(n);
+         o_cnt = L.add<int64_t>(n), o_cols = L.add<int32_t>(skel_cap), o_nc = L.add<int32_t>(n),
+         o_nc64 = L.add<int64_t>(n);
   FFC_CUDA(cudaMalloc((void**)&R->out_mem, L.off));
   char* b = R->out_mem;
   R->node = (int32_t*)(b + o_node); R->rank = (int32_t*)(b + o_rank); R->s = (int32_t*)(b + o_s);
@@ -177,7 +205,21 @@ ffc_status alloc_outputs(ffc_tree_result* R) {
   R->skel_off = (int64_t*)(b + o_skel_off); R->skel = (int32_t*)(b + o_skel); R->T_off = (int64_t*)(b + o_T_off);
   R->T = (double*)(b + o_T);
   R->Tp = (double*)(b + o_Tp); R->Tp_off = (int64_t*)(b + o_Tp_off); R->count_dev = (int64_t*)(b + o_cnt);
+  R->cols = (int32_t*)(b + o_cols); R->ncols = (int32_t*)(b + o_nc); R->ncols64 = (int64_t*)(b + o_nc64);
   FFC_CUDA(cudaMemcpy(R->count_dev, R->count_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+  // every node starts with all of its points as its columns
+  R->ncols_h = R->count_h;
+  {
+    std::vector<int32_t> c(skel_cap), nc(n);
+    for (int64_t i = 0; i < n; ++i) {
+      nc[i] = (int32_t)R->count_h[i];
+      for (int64_t j = 0; j < R->count_h[i]; ++j) c[R->skel_off_h[i] + j] = (int32_t)j;
+    }
+    FFC_CUDA(cudaMemcpy(R->cols, c.data(), sizeof(int32_t) * skel_cap, cudaMemcpyHostToDevice));
+    R->cols_h = c;
+    FFC_CUDA(cudaMemcpy(R->ncols, nc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    FFC_CUDA(cudaMemcpy(R->ncols64, R->count_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+  }
   FFC_CUDA(cudaMemcpy(R->node, R->node_h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   FFC_CUDA(cudaMemcpy(R->rows_off, R->rows_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
   FFC_CUDA(cudaMemcpy(R->skel_off, R->skel_off_h.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
@@ -210,6 +252,62 @@ ffc_status grow(char** buf, size_t* have, size_t want, cudaStream_t st) {
   const size_t bytes = want + want / 4;
   FFC_CUDA(cudaMalloc((void**)buf, bytes));
   *have = bytes;
+  return FFC_OK;
+}
+
+// Every node's columns back to all of its points.
+ffc_status reset_columns(ffc_tree_result* R, cudaStream_t st) {
+  const int64_t n = R->n_out;
+  for (int64_t i = 0; i < n; ++i) {
+    R->ncols_h[i] = R->count_h[i];
+    for (int64_t j = 0; j < R->count_h[i]; ++j) R->cols_h[R->skel_off_h[i] + j] = (int32_t)j;
+  }
+  std::vector<int32_t> nc(R->ncols_h.begin(), R->ncols_h.end());
+  FFC_CUDA(cudaMemcpyAsync(R->cols, R->cols_h.data(), sizeof(int32_t) * R->cols_h.size(), cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(R->ncols, nc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(R->ncols64, R->ncols_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaStreamSynchronize(st));   // the host vectors may change before the copies would run
+  R->cols_custom = false;
+  return FFC_OK;
+}
+
+// Nested form: the columns of the output nodes `lv` (one level) from their children's results: the
+// left child's skeleton points, then the right child's, each in pivot order (node-local indices of
+// the parent); a child whose ID is not usable (status other than OK / TOL_NOT_REACHED, or no rows)
+// contributes all of its points.
+ffc_status nested_columns(ffc_tree_result* R, const std::vector<int>& lv, int64_t first, cudaStream_t st) {
+  const int64_t n = R->n_out;
+  std::vector<int32_t> rank(n), status(n), sv(n), skel(R->cols_h.size());
+  FFC_CUDA(cudaMemcpyAsync(rank.data(), R->rank, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaMemcpyAsync(status.data(), R->status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaMemcpyAsync(sv.data(), R->s, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaMemcpyAsync(skel.data(), R->skel, sizeof(int32_t) * skel.size(), cudaMemcpyDeviceToHost, st));
+  FFC_CUDA(cudaStreamSynchronize(st));
+  int64_t lo = INT64_MAX, hi = 0;
+  for (int o : lv) {
+    const int64_t b = R->node_h[o];
+    int64_t c = 0;
+    for (int64_t ch = 2 * b + 1; ch <= 2 * b + 2; ++ch) {
+      const int64_t oc = ch - first;
+      const int64_t shift = R->begin_h[oc] - R->begin_h[o];
+      const bool usable = (status[oc] == FFC_OK || status[oc] == FFC_E_TOL_NOT_REACHED) && sv[oc] > 0;
+      const int64_t base = R->skel_off_h[oc];
+      if (usable) {
+        for (int k = 0; k < rank[oc]; ++k)
+          R->cols_h[R->skel_off_h[o] + c++] = (int32_t)(shift + R->cols_h[base + skel[base + k]]);
+      } else {
+        for (int64_t j = 0; j < R->count_h[oc]; ++j) R->cols_h[R->skel_off_h[o] + c++] = (int32_t)(shift + j);
+      }
+    }
+    R->ncols_h[o] = c;
+    lo = std::min(lo, R->skel_off_h[o]);
+    hi = std::max(hi, R->skel_off_h[o] + c);
+  }
+  std::vector<int32_t> nc(R->ncols_h.begin(), R->ncols_h.end());
+  FFC_CUDA(cudaMemcpyAsync(R->cols + lo, R->cols_h.data() + lo, sizeof(int32_t) * (hi - lo), cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(R->ncols, nc.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaMemcpyAsync(R->ncols64, R->ncols_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  FFC_CUDA(cudaStreamSynchronize(st));
   return FFC_OK;
 }
 
@@ -383,12 +481,14 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   const int r_cap_glob = P.s_max / 2;
   const int rcap_round = (int)std::min<int64_t>(s_nom, r_cap_glob);
   const size_t esz = P.precision == FFC_MIXED ? sizeof(float) : sizeof(double);   // K' element size
+  const bool nested = P.nested != 0;
+  const size_t pts_esz = R->dtype == FFC_F64 ? sizeof(double) : sizeof(float);
   // per-item sizes
   std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W);
   std::vector<int> g(W);
   int64_t SN = 0, elems = 0, RC = 0, tiles_tot = 0, n_max = 0;
   for (int q = 0; q < W; ++q) {
-    const int64_t n = R->count_h[items[q]];
+    const int64_t n = R->ncols_h[items[q]];
     noff[q] = SN;
     koff[q] = SN * s_nom;
     SN += n;
@@ -420,7 +520,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const size_t QR_L2_BUDGET = (size_t)(P.qr_l2_budget_mb > 0 ? P.qr_l2_budget_mb : QR_L2_BUDGET_MB_DEFAULT) << 20;
     size_t acc = 0;
     for (int q = 0; q < W; ++q) {
-      const size_t bq = esz * (size_t)s_nom * (size_t)R->count_h[items[q]];
+      const size_t bq = esz * (size_t)s_nom * (size_t)R->ncols_h[items[q]];
       if (q == 0 || acc + bq > QR_L2_BUDGET) {
         sb.push_back(q);
         acc = 0;
@@ -438,7 +538,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const int q0 = sb[b], q1 = sb[b + 1];
     int64_t Gb = 0, elems_b = 0;
     for (int q = q0; q < q1; ++q) {
-      const int64_t n = R->count_h[items[q]];
+      const int64_t n = R->ncols_h[items[q]];
       Gb += std::max<int64_t>(cpqr_min_group(n), group_size_tree(s_nom, n, 4096));
       elems_b += s_nom * n;
     }
@@ -446,7 +546,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const int64_t per_cta = shared_ctas ? std::max<int64_t>(1, elems_b / cap) : 16384;
     int64_t Gsum = 0;
     for (int q = q0; q < q1; ++q) {
-      const int64_t n = R->count_h[items[q]];
+      const int64_t n = R->ncols_h[items[q]];
       int64_t gq = shared_ctas ? (s_nom * n) / per_cta : group_size_tree(s_nom, n, 4096);
       gq = std::max<int64_t>(1, std::min<int64_t>({gq, (int64_t)cap, std::max<int64_t>(1, n / 4)}));
       gq = std::max<int64_t>(gq, cpqr_min_group(n));   // per-CTA column cap (<= cap for N <= 1.5M)
@@ -458,7 +558,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const int grid = shared_ctas ? cap : (int)Gsum;
     int ncmax = 0;
     for (int q = q0; q < q1; ++q)
-      ncmax = std::max<int>(ncmax, (int)((R->count_h[items[q]] + g[q] - 1) / g[q]));
+      ncmax = std::max<int>(ncmax, (int)((R->ncols_h[items[q]] + g[q] - 1) / g[q]));
     sb_nb.push_back(ncmax <= QR_FS_COLS ? nb : 1);
     std::vector<std::vector<CtaAssign>> lists(grid);
     int64_t ptr = 0;
@@ -479,7 +579,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   // triangular-solve tiles
   std::vector<int64_t> ttiles(W);
   int64_t ttot = 0;
-  for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += trsm_tiles(R->count_h[items[q]]); }
+  for (int q = 0; q < W; ++q) { ttiles[q] = ttot; ttot += trsm_tiles(R->ncols_h[items[q]]); }
 
   const int64_t scratch_ctas = std::min<int64_t>(W, 2048);
   const bool learned = P.sampler != FFC_SAMPLE_UNIFORM;   // learned or paper sampler: rows drawn once per call
@@ -496,7 +596,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
                o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
                o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W),
-               o_F = L.add<char>(nb > 1 ? (size_t)SN * QR_F_STRIDE * esz : 0);
+               o_F = L.add<char>(nb > 1 ? (size_t)SN * QR_F_STRIDE * esz : 0),
+               o_xa = L.add<char>(nested ? (size_t)SN * d * pts_esz : 0), o_gi = L.add<GatherItem>(nested ? W : 0);
   if (L.off > R->ws_bytes) {
     if (R->ws) {
       FFC_CUDA(cudaStreamSynchronize(st));
@@ -538,6 +639,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   int32_t* oidx = (int32_t*)(b + o_oidx);
   int32_t* trank = (int32_t*)(b + o_trank);
   char* Fbuf = nb > 1 ? (char*)(b + o_F) : nullptr;
+  void* Xcols = nested ? (void*)(b + o_xa) : nullptr;
+  GatherItem* d_gi = (GatherItem*)(b + o_gi);
 
   std::vector<SampleItem> hs(W);
   std::vector<EvalItem> he(W);
@@ -546,14 +649,15 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   std::vector<int32_t> ho(W);
   for (int q = 0; q < W; ++q) {
     const int o = items[q];
-    const int64_t node = R->node_h[o], bgn = R->begin_h[o], n = R->count_h[o];
+    // n: the ID's columns (the node's points unless nested); the far field excludes all of its points
+    const int64_t node = R->node_h[o], bgn = R->begin_h[o], npts = R->count_h[o], n = R->ncols_h[o];
     ho[q] = o;
     SampleItem& si = hs[q];
-    si.M = R->N; si.ex_begin = bgn; si.ex_end = bgn + n;
+    si.M = R->N; si.ex_begin = bgn; si.ex_end = bgn + npts;
     si.x_c = tree->centroid_dev + node * d; si.thr2 = 0.0; si.radius = tree->radius_dev + node; si.xi = P.xi;
     si.s = s_nom; si.stream_id = (uint64_t)node; si.rows = R->rows + R->rows_off_h[o];
     EvalItem& ei = he[q];
-    ei.rows = R->rows + R->rows_off_h[o]; ei.s = s_nom; ei.x_begin = bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
+    ei.rows = R->rows + R->rows_off_h[o]; ei.s = s_nom; ei.x_begin = nested ? noff[q] : bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
     ei.center = P.precision == FFC_MIXED ? tree->centroid_dev + node * d : nullptr;
     ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom, eval_shape(P.kernel, d, P.precision));
     CpqrItem& qi = hq[q];
@@ -599,7 +703,17 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   }
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[1], st));
   patch_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
-  rc = launch_eval(P.kernel, X, R->dtype, X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
+  if (nested) {   // the ID's column points of every item, packed (item q at rows noff[q] of the arena)
+    std::vector<GatherItem> hg(W);
+    for (int q = 0; q < W; ++q) {
+      const int o = items[q];
+      hg[q] = GatherItem{noff[q], R->begin_h[o], R->cols + R->skel_off_h[o], R->ncols_h[o]};
+    }
+    FFC_CUDA(cudaMemcpyAsync(d_gi, hg.data(), sizeof(GatherItem) * W, cudaMemcpyHostToDevice, st));
+    gather_cols_kernel<<<dim3(8, (unsigned)W), 256, 0, st>>>(d_gi, X, Xcols, d, pts_esz);
+    FFC_CUDA(cudaGetLastError());
+  }
+  rc = launch_eval(P.kernel, X, R->dtype, nested ? Xcols : X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
   if (rc != FFC_OK) return rc;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
   // one cooperative QR launch per L2-sized sub-batch of the round
@@ -648,7 +762,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     pf.rounds += 1;
     const double per_coord = P.kernel.kind == FFC_POLYNOMIAL ? 2.0 : 3.0;
     for (int q = 0; q < W; ++q) {
-      const double s = (double)hsz[q], n = (double)R->count_h[items[q]];
+      const double s = (double)hsz[q], n = (double)R->ncols_h[items[q]];
       double fl = 0.0;
       for (int k = 0; k < hr[q]; ++k) fl += 4.0 * (s - k) * (n - k);
       pf.qr_flops += fl;
@@ -742,14 +856,39 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
       R->prof.ms[0] += ms;
     }
   }
-  while (!active.empty()) {
-    ffc_status rc = run_round(R, points_perm_dev, tree, active, s_nom, again, st);
+  auto rounds_of = [&](std::vector<int> act) -> ffc_status {
+    int64_t sn = P.s0;
+    while (!act.empty()) {
+      ffc_status rc = run_round(R, points_perm_dev, tree, act, sn, again, st);
+      if (rc != FFC_OK) return rc;
+      ++R->rounds;
+      act.swap(again);
+      sn *= 2;
+    }
+    return FFC_OK;
+  };
+  if (!P.nested) {
+    if (R->cols_custom) {
+      ffc_status rc = reset_columns(R, st);
+      if (rc != FFC_OK) return rc;
+    }
+    ffc_status rc = rounds_of(active);
     if (rc != FFC_OK) return rc;
-    ++R->rounds;
-    active.swap(again);
-    s_nom *= 2;
+  } else {
+    // the upward pass: each level after the one below it, with its children's skeletons as columns
+    const int64_t first = R->node_h.empty() ? 0 : R->node_h[0];
+    for (int L = tree->depth; L >= P.min_level; --L) {
+      std::vector<int> lv;
+      for (int64_t o = ((int64_t)1 << L) - 1 - first; o < ((int64_t)1 << (L + 1)) - 1 - first; ++o) lv.push_back((int)o);
+      ffc_status rc = L == tree->depth ? reset_columns(R, st) : nested_columns(R, lv, first, st);
+      if (rc != FFC_OK) return rc;
+      R->cols_custom = true;
+      rc = rounds_of(lv);
+      if (rc != FFC_OK) return rc;
+    }
   }
-  pack_offsets_kernel<<<1, 1024, 0, st>>>(R->n_out, R->rank, R->count_dev, R->Tp_off);
+  (void)s_nom;
+  pack_offsets_kernel<<<1, 1024, 0, st>>>(R->n_out, R->rank, R->ncols64, R->Tp_off);
   pack_copy_kernel<<<dim3(8, (unsigned)R->n_out), 256, 0, st>>>(R->n_out, R->T_off, R->Tp_off, R->T, R->Tp);
   FFC_CUDA(cudaGetLastError());
   if (R->prof.enabled) R->prof.launches += 2;
@@ -763,6 +902,7 @@ ffc_status ffc_tree_result_view(const ffc_tree_result* R, ffc_tree_view* v) {
   v->r22_rel_dev = R->r22; v->log_scale_dev = R->log_scale; v->far_count_dev = R->far_count;
   v->rows_off_dev = R->rows_off; v->rows_dev = R->rows; v->skel_off_dev = R->skel_off; v->skel_dev = R->skel;
   v->T_off_dev = R->Tp_off; v->T_dev = R->Tp;
+  v->ncols_dev = R->ncols; v->cols_dev = R->cols;
   return FFC_OK;
 }
 

@@ -67,14 +67,15 @@ class c_params(ctypes.Structure):
                 ("s0", ctypes.c_int32), ("s_max", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
                 ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
-                ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32)]
+                ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32),
+                ("nested", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
     _fields_ = [("n_out", ctypes.c_int64), ("rounds", ctypes.c_int32)] + [
         (name, ctypes.c_void_p) for name in (
             "node_dev", "rank_dev", "s_dev", "status_dev", "r22_rel_dev", "log_scale_dev", "far_count_dev",
-            "rows_off_dev", "rows_dev", "skel_off_dev", "skel_dev", "T_off_dev", "T_dev")]
+            "rows_off_dev", "rows_dev", "skel_off_dev", "skel_dev", "T_off_dev", "T_dev", "ncols_dev", "cols_dev")]
 
 
 class c_tree_profile(ctypes.Structure):
@@ -337,7 +338,7 @@ class TreeResult:
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
-                      qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0) -> TreeResult:
+                      qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0, nested=False) -> TreeResult:
     """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
     ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``, ``qr_panel``:
     the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``)."""
@@ -352,7 +353,7 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
         sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
                  ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
-                 int(qr_l2_budget_mb), int(qr_panel))
+                 int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0)
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
@@ -462,6 +463,8 @@ def tree_result_views(res: TreeResult) -> dict:
     out["rows"] = device_view(v.rows_dev, int(out["rows_off"][-1].item()) if n else 0, "int64")
     out["skel"] = device_view(v.skel_dev, int(out["skel_off"][-1].item()) if n else 0, "int32")
     out["T"] = device_view(v.T_dev, int(out["T_off"][-1].item()) if n else 0, "float64")
+    out["ncols"] = device_view(v.ncols_dev, n, "int32")
+    out["cols"] = device_view(v.cols_dev, int(out["skel_off"][-1].item()) if n else 0, "int32")
     return out
 
 
