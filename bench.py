@@ -661,6 +661,80 @@ def trsm_roofline(ffc, results, trsm_ms_per_step, peaks):
             "peak_source": src}
 
 
+def timed_call(torch, stream, fn, reps=2):
+    """Milliseconds of the last of `reps` calls of fn() on `stream` (CUDA events), and its result."""
+    out = None
+    ms = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    return ms, out
+
+
+def d16_studies(torch, ffc, part, prop, stream, prec):
+    """On the d = 16 tree (untimed in the headline): the paper's samplers beside the learned one at equal s,
+    nested skeletonization, and the evaluation of the potential from the representations."""
+    import numpy as np
+    out = {}
+    W = dict(WORKLOADS[part.name], **COMMON)
+    select_workload(part.name)
+    # (1) samplers at equal s: every node sampled with s = 256 rows (rank cap 128), mixed precision
+    s_eq = 256
+    samplers = {"uniform": (ffc.SAMPLE_UNIFORM, None), "learned": (None, prop),
+                "distance": (ffc.SAMPLE_DISTANCE, None), "inverse_distance": (ffc.SAMPLE_INV_DISTANCE, None),
+                "nearest_neighbours": (ffc.SAMPLE_NEAREST, None)}
+    sam = {}
+    for name, (code, pr) in samplers.items():
+        kw = dict(tol=W["tol"], min_level=W["min_level"], s0=s_eq, s_max=s_eq, xi=W["xi"], seed=W["sample_seed"])
+        ms, res = timed_call(torch, stream, lambda: ffc.ffc_compress_tree(part.Pp, part.tree, part.kern,
+                                                                          precision=prec, stream=stream, proposal=pr,
+                                                                          sampler=code, **kw))
+        n = int(ffc.tree_result_views(res)["n_out"])
+        e = arm_errors(torch, ffc, part.Pp, part.tree, part.kern, res)
+        ee = np.asarray(e["errors"])
+        sam[name] = {"nodes_per_s": n / (ms / 1e3), "ms_per_call": ms, "median_full_block_error": float(np.median(ee)),
+                     "max_full_block_error": float(ee.max()), "fraction_at_or_below_1e-6": float(np.mean(ee <= 1e-6)),
+                     "mean_rank": e["mean_rank"]}
+        res.close()
+    out["samplers_at_equal_s"] = {"s": s_eq, "precision": "mixed" if prec == ffc.MIXED else "fp64",
+                                  "nodes_checked": 12, "note": "leverage sampling needs the full block's SVD "
+                                  "(n <= 1024) and is compared single-node in the tests", "by_sampler": sam}
+    # (2) nested skeletonization against the plain form, same sampler (learned) and tolerance
+    kw = compress_kwargs()
+    nest = {}
+    for label, nested in (("plain", False), ("nested", True)):
+        ms, res = timed_call(torch, stream, lambda: ffc.ffc_compress_tree(part.Pp, part.tree, part.kern,
+                                                                          precision=prec, stream=stream,
+                                                                          proposal=prop, nested=nested, **kw))
+        h = ffc.tree_result_to_host(res)
+        nest[label] = {"nodes_per_s": len(h["node"]) / (ms / 1e3), "ms_per_call": ms,
+                       "mean_columns": float(h["ncols"].mean()), "mean_rank": float(h["rank"].mean())}
+        if label == "nested":
+            # (3) the potential at every point from the nested representations, against the direct sum
+            q = torch.as_tensor(np.random.default_rng(11).standard_normal(part.Pp.shape[0])).to(part.Pp.device)
+            ms_s, (u_s, _) = timed_call(torch, stream, lambda: ffc.ffc_tree_apply(part.Pp, part.tree, res, q,
+                                                                                  mode=ffc.APPLY_SKELETON,
+                                                                                  stream=stream))
+            ms_d, (u_d, _) = timed_call(torch, stream, lambda: ffc.ffc_tree_apply(part.Pp, part.tree, res, q,
+                                                                                  mode=ffc.APPLY_DIRECT,
+                                                                                  stream=stream))
+            err = float(torch.linalg.vector_norm(u_s - u_d) / torch.linalg.vector_norm(u_d))
+            npts = int(part.Pp.shape[0])
+            out["apply"] = {"targets": npts, "skeleton_ms": ms_s, "direct_ms": ms_d,
+                            "targets_per_s_skeleton": npts / (ms_s / 1e3), "targets_per_s_direct": npts / (ms_d / 1e3),
+                            "relative_error_vs_direct": err, "representation": "nested, learned rows, mixed",
+                            "what": "potential at every point: far field from the outgoing representations, near "
+                                    "leaves direct (ffc_tree_apply)"}
+        res.close()
+    out["nested_skeletonization"] = nest
+    return out
+
+
 def arm_errors(torch, ffc, Pp, tree, k, res, n_sample=12, seed=7, max_n=4096):
     """Full-block ID error of a seeded sample of nodes of one arm's result (outside the timed region): nodes
     of at most max_n sources (the FP64 error of a 65,536-source node against its whole far field takes
@@ -913,6 +987,9 @@ def main():
                 v2 = job_throughput(nn, args.arm_steps, world, ms2)
                 ent["fp64_plain"] = {"value": v2, "ms_per_step": ms2 / args.arm_steps, "steps": args.arm_steps}
                 ent["speedup_vs_fp64"] = v1 / v2
+            if cname == "c2" and rank == 0:
+                ent["studies"] = d16_studies(torch, ffc, cparts[0], cprop[cparts[0].name] if cprop else None, stream,
+                                             prec)
             extra[cname] = ent
             del cparts
             torch.cuda.empty_cache()

@@ -86,6 +86,32 @@ const char* ffc_version(void);
  */
 ffc_status ffc_set_wait_limit(int64_t polls);
 
+/* Evaluation paths of the mixed-precision Gaussian and polynomial blocks (the
+ * same arithmetic: three BF16 parts per FP32 coordinate, six partial
+ * products, FP32 accumulation; they differ in summation order only):
+ * FFC_EVAL_DEFAULT: tcgen05 for d >= 64, SIMT below;
+ * FFC_EVAL_SIMT: FP32 direct differences (no tensor cores), any d;
+ * FFC_EVAL_MMA_SYNC: mma.sync m16n8k16, 128 x 128 tiles, synchronous staging;
+ * FFC_EVAL_TCGEN05: tcgen05.mma with TMEM accumulators and TMA staging, the
+ *   library's tile; FFC_EVAL_TCGEN05_TILE0 + v, v < FFC_EVAL_TCGEN05_TILES: the
+ *   same with tile variant v (targets x sources per tile, coordinates per
+ *   stage, stages): 0: 128 x 256, 32, 3; 1: 128 x 128, 64, 2;
+ *   2: 128 x 128, 32, 4; 3: 128 x 256, 16, 6; 4: 128 x 128, 16, 8. */
+#define FFC_EVAL_DEFAULT 0
+#define FFC_EVAL_SIMT 1
+#define FFC_EVAL_MMA_SYNC 2
+#define FFC_EVAL_TCGEN05 3
+#define FFC_EVAL_TCGEN05_TILE0 4
+#define FFC_EVAL_TCGEN05_TILES 5
+
+/*
+ * ffc_set_eval_path - the evaluation path FFC_EVAL_DEFAULT stands for, for
+ * ffc_eval_block and for ffc_compress_tree calls whose params.eval_path is
+ * FFC_EVAL_DEFAULT (the project's autotuner compares them). Process-wide,
+ * for calls made after it. FFC_E_INVALID for an unknown path.
+ */
+ffc_status ffc_set_eval_path(int32_t path);
+
 /*
  * ffc_far_field - list the far field of a source set (§4.1, setup step 3):
  *   T = { j in [0, M) \ [ex_begin, ex_end) : ||Y_j - x_c|| >= xi * radius }.
@@ -135,7 +161,10 @@ ffc_status ffc_sample_rows(const void* Y_dev, int32_t dtype, int64_t M, int32_t 
  *   Gaussian, polynomial, d < 64: FP32 direct differences (inner products).
  *   Gaussian, polynomial, d >= 64: tensor cores, each FP32 coordinate split
  *     into three BF16 parts, FP32 accumulation; Gaussian D2 recomputed from
- *     FP32 differences where ||y||^2 + ||x||^2 - 2 y.x cancels.
+ *     FP32 differences where ||y||^2 + ||x||^2 - 2 y.x cancels. By default the
+ *     tcgen05 path (TMA-staged BF16 planes, TMEM accumulators, 128 x 256
+ *     tiles; device scratch of about 6 (s + n) d bytes, allocated and freed on
+ *     `stream`); ffc_set_eval_path selects another.
  *   Laplace: FP32 distances; FP64 where they cancel and for every entry at or
  *     above 1e-6 of the largest. The block is scaled by the minimum of those
  *     distances: the same block as FP64's up to a constant factor within
@@ -316,6 +345,9 @@ typedef struct {
    *   FFC_E_TOL_NOT_REACHED contributes all of its points). Rows are the node's own far-field sample
    *   either way. */
   int32_t nested;
+  /* eval_path: FFC_EVAL_* evaluation path of the sampled blocks (mixed precision, Gaussian and
+   *   polynomial); FFC_EVAL_DEFAULT (0) = the process default (ffc_set_eval_path) */
+  int32_t eval_path;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2), the learned proposal

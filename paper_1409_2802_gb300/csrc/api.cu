@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ffc_internal.cuh"
@@ -93,6 +94,32 @@ const char* ffc_last_error(void) { return g_err; }
 
 ffc_status ffc_set_wait_limit(int64_t polls) {
   g_wait_limit.store(polls < 0 ? SPIN_LIMIT_DEFAULT : (long long)polls, std::memory_order_relaxed);
+  return FFC_OK;
+}
+
+namespace {
+// The current device's default memory pool keeps what stream-ordered frees return instead of handing it
+// back to the system at each synchronisation, so large per-call scratch (the tcgen05 evaluation's
+// plane arena) is reused rather than mapped again on every call. Process-local; set once per device.
+void retain_pool_memory() {
+  static std::once_flag once[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { (void)cudaGetLastError(); return; }
+  std::call_once(once[dev], [dev] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) (void)cudaGetLastError();
+    } else {
+      (void)cudaGetLastError();
+    }
+  });
+}
+}  // namespace
+
+ffc_status ffc_set_eval_path(int32_t path) {
+  FFC_REQUIRE(path >= FFC_EVAL_DEFAULT && path <= FFC_EVAL_LAST, "ffc_set_eval_path: unknown path %d", (int)path);
+  set_eval_default_path(path);
   return FFC_OK;
 }
 
@@ -192,12 +219,24 @@ ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype, c
   EvalItem h;
   h.rows = rows_dev; h.s = s; h.x_begin = 0; h.n = n; h.K = K_dev; h.ldk = ldk; h.center = center_dev;
   h.tile_begin = 0;
-  const int shape = eval_shape(kernel, d, precision);
+  const int shape = eval_shape(kernel, d, precision, FFC_EVAL_DEFAULT);
   h.row_tiles = eval_row_tiles(s, shape);
+  h.tc_base = 0;
+  h.tc_spad = eval_tc5_pad_s(s);
+  h.tc_npad = eval_tc5_pad_n(n);
+  char* tc_raw = nullptr;
+  void* tc_scr = nullptr;
+  const int64_t tc_rows = h.tc_spad + h.tc_npad;
+  if (shape >= 2) {   // the tcgen05 path's plane arena, 256-byte aligned
+    retain_pool_memory();
+    FFC_CUDA(cudaMallocAsync((void**)&tc_raw, eval_tc5_scratch_bytes(tc_rows, d) + 256, st));
+    tc_scr = (void*)(((uintptr_t)tc_raw + 255) & ~(uintptr_t)255);
+  }
   FFC_CUDA(cudaMemcpyAsync(item, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  ffc_status rc = launch_eval(kernel, Y_dev, dtype, X_dev, d, precision, item, 1, eval_tiles(s, n, shape), mind2, lsc,
-                              status, st);
+  ffc_status rc = launch_eval(kernel, Y_dev, dtype, X_dev, d, precision, shape, item, 1, eval_tiles(s, n, shape), mind2,
+                              lsc, status, tc_scr, tc_rows, st);
+  if (tc_raw) FFC_CUDA(cudaFreeAsync(tc_raw, st));
   if (rc != FFC_OK) return rc;
   double hl = 0.0;
   int32_t hst = 0;
@@ -207,6 +246,7 @@ ffc_status ffc_eval_block(ffc_kernel kernel, const void* Y_dev, int32_t dtype, c
   FFC_CUDA(cudaStreamSynchronize(st));
   if (log_scale_host) *log_scale_host = hl;
   if (hst == FFC_E_SINGULAR) set_error("ffc_eval_block: Laplace kernel at a zero distance");
+  if (hst == FFC_E_TIMEOUT) set_error("ffc_eval_block: a bounded wait of the tcgen05 pipeline ran out");
   return (ffc_status)hst;
 }
 

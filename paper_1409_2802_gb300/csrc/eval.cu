@@ -9,6 +9,8 @@
 // in 32-coordinate chunks. Distances are formed from direct differences in
 // FP64. A Laplace block is scaled by its largest entry, which needs the
 // block's smallest distance first (a min-reduction pass over the same tiles).
+#include <atomic>
+
 #include "ffc_internal.cuh"
 
 namespace ffc {
@@ -234,25 +236,45 @@ ffc_status launch_eval_t(ffc_kernel k, const TP* Y, const TP* X, int d, const Ev
 
 }  // namespace
 
-// Mixed precision, Gaussian or polynomial, d >= 64: the tensor-core path (its
-// 128 x 128 tiles); otherwise the SIMT path (64 x 32 tiles). At small d the
-// block is bound by its stores and the SIMT path's direct FP32 differences are
-// the more accurate form.
+// Mixed precision, Gaussian or polynomial, d >= 64: the tensor cores, by default the tcgen05 path
+// (128 x 256 tiles); otherwise the SIMT path (64 x 32 tiles). At small d the block is bound by its
+// stores and the SIMT path's direct FP32 differences are the more accurate form. An explicit path
+// request takes a tensor-core path for any d, where the kernel and precision allow it.
 constexpr int TC_MIN_D = 64;
 
-int eval_shape(ffc_kernel k, int d, int precision) {
-  return (precision == FFC_MIXED && (k.kind == FFC_GAUSSIAN || k.kind == FFC_POLYNOMIAL) && d >= TC_MIN_D) ? 1 : 0;
+namespace {
+std::atomic<int> g_eval_path{FFC_EVAL_DEFAULT};
+}
+
+int eval_default_path() { return g_eval_path.load(std::memory_order_relaxed); }
+void set_eval_default_path(int path) { g_eval_path.store(path, std::memory_order_relaxed); }
+
+int eval_shape(ffc_kernel k, int d, int precision, int path) {
+  if (path == FFC_EVAL_DEFAULT) path = eval_default_path();
+  const bool tc_ok = precision == FFC_MIXED && (k.kind == FFC_GAUSSIAN || k.kind == FFC_POLYNOMIAL);
+  if (!tc_ok || path == FFC_EVAL_SIMT) return 0;
+  if (path == FFC_EVAL_MMA_SYNC) return 1;
+  if (path == FFC_EVAL_TCGEN05) return 2 + FFC_EVAL_TCGEN05_DEFAULT_TILE;
+  if (path >= FFC_EVAL_TCGEN05_TILE0 && path < FFC_EVAL_TCGEN05_TILE0 + FFC_EVAL_TCGEN05_TILES)
+    return 2 + (path - FFC_EVAL_TCGEN05_TILE0);
+  return d >= TC_MIN_D ? 2 + FFC_EVAL_TCGEN05_DEFAULT_TILE : 0;
 }
 
 int64_t eval_tiles(int64_t s, int64_t n, int shape) {
-  return shape ? eval_tc_tiles(s, n) : ((s + TI - 1) / TI) * ((n + TJ - 1) / TJ);
+  return shape >= 2 ? eval_tc5_tiles(s, n, shape - 2)
+         : shape == 1 ? eval_tc_tiles(s, n) : ((s + TI - 1) / TI) * ((n + TJ - 1) / TJ);
 }
-int64_t eval_row_tiles(int64_t s, int shape) { return shape ? eval_tc_row_tiles(s) : (s + TI - 1) / TI; }
+int64_t eval_row_tiles(int64_t s, int shape) {
+  return shape >= 2 ? eval_tc5_row_tiles(s) : shape == 1 ? eval_tc_row_tiles(s) : (s + TI - 1) / TI;
+}
 
-ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
+ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision, int shape,
                        const EvalItem* items_dev, int n_items, int64_t total_tiles, double* min_d2,
-                       double* log_scale, int32_t* status, cudaStream_t st) {
-  if (eval_shape(k, d, precision))
+                       double* log_scale, int32_t* status, void* tc5_scratch, int64_t tc5_rows, cudaStream_t st) {
+  if (shape >= 2)
+    return launch_eval_tc5(k, Y, dtype, X, d, shape - 2, items_dev, n_items, total_tiles, tc5_rows, tc5_scratch,
+                           log_scale, status, st);
+  if (shape == 1)
     return launch_eval_tc(k, Y, dtype, X, d, items_dev, n_items, total_tiles, log_scale, st);
   if (precision == FFC_MIXED) {
     if (dtype == FFC_F64)

@@ -98,6 +98,10 @@ struct EvalItem {
   const double* center; // d doubles or NULL
   int64_t tile_begin;   // prefix of tiles over items
   int64_t row_tiles;    // row tiles of the nominal s (tiles past the actual s are skipped)
+  // tcgen05 path only: the item's first row of the plane arena's norm index (a prefix over items of
+  // tc_spad + tc_npad; its planes start at row 3 tc_base) and its padded target / source counts
+  int64_t tc_base;
+  int64_t tc_spad, tc_npad;
 };
 
 struct CpqrItem {
@@ -242,19 +246,37 @@ ffc_status launch_far_field(const void* Y, int dtype, int64_t M, int d, const do
 ffc_status launch_sample(const void* Y, int dtype, int d, const SampleItem* items_dev, int n_items,
                          int64_t M_max, int64_t s_max, uint64_t seed, int64_t* s_out, int64_t* far_count,
                          int32_t* status, int32_t* scratch, cudaStream_t st);
-// Tile decomposition of the evaluation: shape = eval_shape(k, d, precision); items' tile_begin and
-// row_tiles must come from eval_tiles / eval_row_tiles of that shape.
-int eval_shape(ffc_kernel k, int d, int precision);
+// Tile decomposition of the evaluation: shape = eval_shape(k, d, precision, path) (0 SIMT, 1 mma.sync
+// tensor cores, 2 + v tcgen05 with tile variant v); items' tile_begin and row_tiles must come from
+// eval_tiles / eval_row_tiles of that shape. path: an FFC_EVAL_* request (FFC_EVAL_DEFAULT: the library default, which
+// eval_default_path() may override).
+int eval_shape(ffc_kernel k, int d, int precision, int path);
+constexpr int FFC_EVAL_TCGEN05_DEFAULT_TILE = 0;   // the tcgen05 tile variant FFC_EVAL_TCGEN05 stands for
+constexpr int FFC_EVAL_LAST = FFC_EVAL_TCGEN05_TILE0 + FFC_EVAL_TCGEN05_TILES - 1;
+int eval_default_path();
+void set_eval_default_path(int path);
 int64_t eval_tiles(int64_t s, int64_t n, int shape);
 int64_t eval_row_tiles(int64_t s, int shape);
 int64_t eval_tc_tiles(int64_t s, int64_t n);
 int64_t eval_tc_row_tiles(int64_t s);
 ffc_status launch_eval_tc(ffc_kernel k, const void* Y, int dtype, const void* X, int d, const EvalItem* items_dev,
                           int n_items, int64_t total_tiles, double* log_scale, cudaStream_t st);
-ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision,
+// tcgen05 shape: items carry tc_base / tc_spad / tc_npad (tc_spad = eval_tc5_pad_s(nominal s),
+// tc_npad = eval_tc5_pad_n(n)); the scratch holds eval_tc5_scratch_bytes(sum of tc_spad + tc_npad, d)
+// bytes, 256-byte aligned.
+int64_t eval_tc5_pad_s(int64_t s);
+int64_t eval_tc5_pad_n(int64_t n);
+int eval_tc5_dpad(int d);
+int64_t eval_tc5_tiles(int64_t s, int64_t n, int v);
+int64_t eval_tc5_row_tiles(int64_t s);
+size_t eval_tc5_scratch_bytes(int64_t total_rows, int d);
+ffc_status launch_eval_tc5(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int v,
+                           const EvalItem* items_dev, int n_items, int64_t total_tiles, int64_t total_rows,
+                           void* scratch, double* log_scale, int32_t* status, cudaStream_t st);
+ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, int d, int precision, int shape,
                        const EvalItem* items_dev, int n_items, int64_t total_tiles,
                        double* min_d2 /* n_items, Laplace */, double* log_scale /* n_items */,
-                       int32_t* status /* n_items */, cudaStream_t st);
+                       int32_t* status /* n_items */, void* tc5_scratch, int64_t tc5_rows, cudaStream_t st);
 // entries: per-CTA work lists (CTA b runs entries[cta_off[b] .. cta_off[b+1]) in order), or with
 // cta_off == NULL one entry per CTA.
 // big: the register-resident variant (mixed precision only; -1 = the default rule s_max >= 1024)

@@ -484,9 +484,10 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   const bool nested = P.nested != 0;
   const size_t pts_esz = R->dtype == FFC_F64 ? sizeof(double) : sizeof(float);
   // per-item sizes
-  std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W);
+  std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W), t5base(W);
   std::vector<int> g(W);
-  int64_t SN = 0, elems = 0, RC = 0, tiles_tot = 0, n_max = 0;
+  int64_t SN = 0, elems = 0, RC = 0, tiles_tot = 0, n_max = 0, t5rows = 0;
+  const int eshape = eval_shape(P.kernel, d, P.precision, P.eval_path);
   for (int q = 0; q < W; ++q) {
     const int64_t n = R->ncols_h[items[q]];
     noff[q] = SN;
@@ -497,8 +498,10 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     const int64_t rc = std::min<int64_t>(n, rcap_round);
     RC += rc * rc;
     tiles[q] = tiles_tot;
-    tiles_tot += eval_tiles(s_nom, n, eval_shape(P.kernel, d, P.precision));
+    tiles_tot += eval_tiles(s_nom, n, eshape);
     n_max = std::max(n_max, n);
+    t5base[q] = t5rows;
+    if (eshape >= 2) t5rows += eval_tc5_pad_s(s_nom) + eval_tc5_pad_n(n);
   }
   const int big_min = P.qr_big_min_s > 0 ? P.qr_big_min_s : QR_BIG_MIN_S_DEFAULT;
   const int big = (P.precision == FFC_MIXED && s_nom >= big_min) ? 1 : 0;
@@ -597,7 +600,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
                o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W),
                o_F = L.add<char>(nb > 1 ? (size_t)SN * QR_F_STRIDE * esz : 0),
-               o_xa = L.add<char>(nested ? (size_t)SN * d * pts_esz : 0), o_gi = L.add<GatherItem>(nested ? W : 0);
+               o_xa = L.add<char>(nested ? (size_t)SN * d * pts_esz : 0), o_gi = L.add<GatherItem>(nested ? W : 0),
+               o_t5 = L.add<char>(eshape >= 2 ? eval_tc5_scratch_bytes(t5rows, d) : 0);
   if (L.off > R->ws_bytes) {
     if (R->ws) {
       FFC_CUDA(cudaStreamSynchronize(st));
@@ -641,6 +645,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   char* Fbuf = nb > 1 ? (char*)(b + o_F) : nullptr;
   void* Xcols = nested ? (void*)(b + o_xa) : nullptr;
   GatherItem* d_gi = (GatherItem*)(b + o_gi);
+  void* t5scr = eshape >= 2 ? (void*)(b + o_t5) : nullptr;
 
   std::vector<SampleItem> hs(W);
   std::vector<EvalItem> he(W);
@@ -659,7 +664,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     EvalItem& ei = he[q];
     ei.rows = R->rows + R->rows_off_h[o]; ei.s = s_nom; ei.x_begin = nested ? noff[q] : bgn; ei.n = n; ei.K = (void*)((char*)K + esz * koff[q]); ei.ldk = s_nom;
     ei.center = P.precision == FFC_MIXED ? tree->centroid_dev + node * d : nullptr;
-    ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom, eval_shape(P.kernel, d, P.precision));
+    ei.tile_begin = tiles[q]; ei.row_tiles = eval_row_tiles(s_nom, eshape);
+    ei.tc_base = t5base[q]; ei.tc_spad = eval_tc5_pad_s(s_nom); ei.tc_npad = eval_tc5_pad_n(n);
     CpqrItem& qi = hq[q];
     qi = CpqrItem{};
     qi.A = (void*)((char*)K + esz * koff[q]); qi.lda = s_nom; qi.s = (int32_t)s_nom; qi.n = (int32_t)n; qi.r_max = 0; qi.tol = P.tol;
@@ -713,7 +719,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     gather_cols_kernel<<<dim3(8, (unsigned)W), 256, 0, st>>>(d_gi, X, Xcols, d, pts_esz);
     FFC_CUDA(cudaGetLastError());
   }
-  rc = launch_eval(P.kernel, X, R->dtype, nested ? Xcols : X, d, P.precision, d_ei, W, tiles_tot, mind2, lsc, est, st);
+  rc = launch_eval(P.kernel, X, R->dtype, nested ? Xcols : X, d, P.precision, eshape, d_ei, W, tiles_tot, mind2, lsc,
+                   est, t5scr, t5rows, st);
   if (rc != FFC_OK) return rc;
   if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
   // one cooperative QR launch per L2-sized sub-batch of the round
@@ -795,6 +802,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   FFC_REQUIRE(P.s0 >= 2 && P.s_max >= P.s0 && P.s_max <= 2048, "ffc_compress_tree: need 2 <= s0 <= s_max <= 2048");
   FFC_REQUIRE(P.qr_panel >= 0 && P.qr_panel <= QR_PANEL_MAX, "ffc_compress_tree: qr_panel must be in [0, %d]",
               QR_PANEL_MAX);
+  FFC_REQUIRE(P.eval_path >= FFC_EVAL_DEFAULT && P.eval_path <= FFC_EVAL_LAST, "ffc_compress_tree: bad eval_path");
   FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");

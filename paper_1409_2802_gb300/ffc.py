@@ -31,6 +31,8 @@ GAUSSIAN, LAPLACE, POLYNOMIAL = 0, 1, 2
 SAMPLE_UNIFORM, SAMPLE_LEARNED, SAMPLE_DISTANCE, SAMPLE_INV_DISTANCE, SAMPLE_NEAREST = 0, 1, 2, 3, 4
 F64, F32 = 0, 1
 FP64, MIXED = 0, 1
+EVAL_DEFAULT, EVAL_SIMT, EVAL_MMA_SYNC, EVAL_TCGEN05 = 0, 1, 2, 3
+EVAL_TCGEN05_TILE0, EVAL_TCGEN05_TILES = 4, 5   # EVAL_TCGEN05_TILE0 + v: tcgen05 tile variant v
 
 EXPORTS = (
     "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
@@ -39,7 +41,7 @@ EXPORTS = (
     "ffc_id_noalloc", "ffc_features", "ffc_mlp_forward", "ffc_sample_weighted", "ffc_propose_rows",
     "ffc_mlp_loss_grad", "ffc_adam_step", "ffc_leverage", "ffc_leverage_batched", "ffc_set_wait_limit",
     "ffc_skeleton_charges", "ffc_potential", "ffc_tree_apply", "ffc_sample_paper", "ffc_sample_leverage",
-    "ffc_spectrum",
+    "ffc_spectrum", "ffc_set_eval_path",
 )
 MLP_PARAMS = 18305
 N_FEATURES = 12
@@ -68,7 +70,7 @@ class c_params(ctypes.Structure):
                 ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
                 ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
                 ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32),
-                ("nested", ctypes.c_int32)]
+                ("nested", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -139,6 +141,7 @@ def lib() -> ctypes.CDLL:
     L.ffc_leverage.argtypes = [vp, i64, i64, i64, dbl, i64, vp, vp, pi64, vp]
     L.ffc_leverage_batched.argtypes = [i32, vp, vp, vp, vp, dbl, i64, vp, vp, vp, vp]
     L.ffc_set_wait_limit.argtypes = [i64]
+    L.ffc_set_eval_path.argtypes = [i32]
     L.ffc_skeleton_charges.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
     L.ffc_potential.argtypes = [c_kernel, vp, i32, vp, i64, vp, i64, i32, vp, i64, vp, dbl, vp, vp]
     L.ffc_spectrum.argtypes = [vp, i64, i64, i64, dbl, vp, pi64, vp]
@@ -189,6 +192,11 @@ def version() -> str:
 def ffc_set_wait_limit(polls: int) -> None:
     """Polls of a bounded device wait before it gives up (< 0: the library's default)."""
     _check(lib().ffc_set_wait_limit(int(polls)))
+
+
+def ffc_set_eval_path(path: int) -> None:
+    """The evaluation path EVAL_DEFAULT stands for (one of EVAL_*), process-wide."""
+    _check(lib().ffc_set_eval_path(int(path)))
 
 
 def ffc_far_field(Y, x_c=None, radius=0.0, xi=1.0, ex_begin=0, ex_end=0, stream=None):
@@ -338,10 +346,12 @@ class TreeResult:
 def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, precision=FP64, min_level=2, s0=128,
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
-                      qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0, nested=False) -> TreeResult:
+                      qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0, nested=False,
+                      eval_path=EVAL_DEFAULT) -> TreeResult:
     """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
     ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``, ``qr_panel``:
-    the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``)."""
+    the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``);
+    ``eval_path``: one of EVAL_* for the mixed-precision Gaussian / polynomial blocks."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
@@ -353,7 +363,7 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
         sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
                  ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
-                 int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0)
+                 int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0, int(eval_path))
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
