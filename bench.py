@@ -549,7 +549,8 @@ def eval_roofline(prof, steps, precision_name, peaks, peak_src):
     if tensor:
         # timed inside a long step: the sustained figure
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1710.8))
-        return {"kernel": "eval_tc_kernel (split-BF16 mma.sync, FP32 accumulate)", "bound": "tensor",
+        return {"kernel": "tc5_kernel (tcgen05.mma, TMEM accumulators, TMA-staged split-BF16 planes, FP32 "
+                          "accumulate; with its plane-prep kernel)", "bound": "tensor",
                 "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
                 "tensor_work_tflops": 6.0 * tflops, "tensor_work_frac": 6.0 * tflops / peak,
                 "peak_source": f"{peak_src} dense BF16, sustained (MEASURED_PEAKS.json bf16_tflops_sustained, "
@@ -787,13 +788,18 @@ def accuracy_summary(per_arm):
 
 
 def tune_parts(ffc, parts, prec, stream, proposal, max_step_s=1.5):
-    """The QR launch shape per part from the project's autotuner (untimed); a part whose single call takes
-    longer than max_step_s keeps the library defaults (tuning would cost minutes)."""
+    """The launch shapes per part from the project's autotuner (untimed): the evaluation path (timed on single
+    blocks of the tree's node sizes, cheap) always; the QR launch shape unless a part's single call takes
+    longer than max_step_s (that part keeps the library's QR defaults: tuning would cost minutes)."""
     from paper_1409_2802_gb300 import autotune
     import torch
     kw, info = {}, {}
     for p in parts:
         select_workload(p.name)
+        W = dict(WORKLOADS[p.name], **COMMON)
+        te = autotune.tune_tree_eval(p.tree, p.kern, int(p.Pp.shape[1]), prec, s_max=W["s_max"],
+                                     min_level=W["min_level"], dtype=p.Pp.dtype)
+        kw[p.name] = {"eval_path": te["eval_path"]}
         prop = proposal[p.name] if isinstance(proposal, dict) else proposal
         t0 = time.perf_counter()
         r = ffc.ffc_compress_tree(p.Pp, p.tree, p.kern, precision=prec, stream=stream, proposal=prop,
@@ -802,15 +808,16 @@ def tune_parts(ffc, parts, prec, stream, proposal, max_step_s=1.5):
         dt = time.perf_counter() - t0
         r.close()
         if dt > max_step_s:
-            info[p.name] = {"source": f"library defaults (one call takes {dt:.1f} s, too long to tune here)"}
+            info[p.name] = {"source": f"library defaults (one call takes {dt:.1f} s, too long to tune here)",
+                            "eval": te}
             continue
         try:
             t = autotune.tune_tree(p.Pp, p.tree, p.kern, precision=prec, stream=stream, proposal=prop,
-                                   **compress_kwargs())
-            kw[p.name] = {k_: t[k_] for k_ in ("qr_big_min_s", "qr_l2_budget_mb")}
-            info[p.name] = dict(t, source="autotune")
+                                   eval_path=te["eval_path"], **compress_kwargs())
+            kw[p.name].update({k_: t[k_] for k_ in ("qr_big_min_s", "qr_l2_budget_mb")})
+            info[p.name] = dict(t, source="autotune", eval=te)
         except ffc.FFCError as e:
-            info[p.name] = {"source": f"library defaults (autotune failed: {e})"}
+            info[p.name] = {"source": f"library defaults (autotune failed: {e})", "eval": te}
     return kw, info
 
 

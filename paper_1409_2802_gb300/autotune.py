@@ -18,9 +18,19 @@ coordinate search:
 2. the budget at the best threshold.
 
 It returns the fastest setting and the table of everything it timed.
+
+``tune_eval`` picks the evaluation path of the mixed-precision Gaussian and
+polynomial blocks: the mma.sync tiles or one of the tcgen05 tile variants
+(output tile, coordinates per stage, stage count). The choice is keyed by
+(d, precision, kernel, n-bucket, s, point dtype) and cached; it times single
+blocks of s rows against n sources of that bucket. ``tune_tree_eval`` weighs
+the buckets of a tree's levels by how many blocks of each a call evaluates.
 """
 from __future__ import annotations
 
+import json
+import math
+import os
 import time
 
 import torch
@@ -80,3 +90,92 @@ def tune_tree(points_perm, tree: ffc.DeviceTree, kernel: ffc.Kernel, precision=f
         raise ffc.FFCError(ffc.FFC_E_CUDA, "autotune: no candidate launch shape ran")
     return {"qr_big_min_s": big, "qr_l2_budget_mb": budget, "ms": round(budgets[budget], 3), "table": table,
             "seconds": round(time.perf_counter() - t0, 1)}
+
+
+EVAL_CANDIDATES = (ffc.EVAL_MMA_SYNC,) + tuple(ffc.EVAL_TCGEN05_TILE0 + v for v in range(ffc.EVAL_TCGEN05_TILES))
+N_BUCKETS = (256, 1024, 4096, 16384, 65536)
+_EVAL_CACHE: dict = {}
+
+
+def n_bucket(n: int) -> int:
+    """The smallest bucket at or above n (the largest bucket beyond it)."""
+    for b in N_BUCKETS:
+        if n <= b:
+            return b
+    return N_BUCKETS[-1]
+
+
+def _eval_key(d, precision, kind, nb, s, dtype):
+    return f"d={d},precision={precision},kernel={kind},n={nb},s={s},dtype={str(dtype).split('.')[-1]}"
+
+
+def tune_eval(kernel: ffc.Kernel, d: int, n: int, precision=ffc.MIXED, s: int = 2048, dtype=torch.float64,
+              reps: int = 3, cache_path: str | None = None, device=None) -> dict:
+    """Fastest evaluation path for one s x n block in d dimensions (synthetic standard-normal points of the
+    given dtype; the time does not depend on the values). Only the mixed-precision Gaussian and polynomial
+    blocks have a choice; the others return EVAL_DEFAULT. Results are cached in memory and, with
+    ``cache_path``, in a JSON file."""
+    if precision != ffc.MIXED or kernel.kind == ffc.LAPLACE:
+        return {"eval_path": ffc.EVAL_DEFAULT, "source": "no choice"}
+    nb = n_bucket(n)
+    key = _eval_key(d, precision, kernel.kind, nb, s, dtype)
+    if key not in _EVAL_CACHE and cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            _EVAL_CACHE.update(json.load(f))
+    if key in _EVAL_CACHE:
+        return dict(_EVAL_CACHE[key], source="cache")
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev).manual_seed(d * 7919 + nb)
+    X = torch.randn(nb, d, device=dev, dtype=dtype, generator=g)
+    Y = torch.randn(2 * s, d, device=dev, dtype=dtype, generator=g)
+    rows = torch.arange(s, dtype=torch.int64, device=dev)
+    ctr = X.double().mean(0)
+    K = torch.empty((nb, s), dtype=torch.float32, device=dev)
+    table = {}
+    try:
+        for path in EVAL_CANDIDATES:
+            ffc.ffc_set_eval_path(path)
+            ffc.ffc_eval_block(kernel, Y, rows, X, precision=precision, center=ctr, K=K)   # untimed
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                ffc.ffc_eval_block(kernel, Y, rows, X, precision=precision, center=ctr, K=K)
+            e1.record()
+            e1.synchronize()
+            table[path] = e0.elapsed_time(e1) / reps
+    finally:
+        ffc.ffc_set_eval_path(ffc.EVAL_DEFAULT)
+    best = min(table, key=table.get)
+    out = {"eval_path": best, "ms": round(table[best], 4), "table": {str(k): round(v, 4) for k, v in table.items()}}
+    _EVAL_CACHE[key] = out
+    if cache_path:
+        with open(cache_path, "w") as f:
+            json.dump(_EVAL_CACHE, f, indent=1, sort_keys=True)
+    return dict(out, source="measured")
+
+
+def tune_tree_eval(tree: ffc.DeviceTree, kernel: ffc.Kernel, d: int, precision=ffc.MIXED, s_max: int = 2048,
+                   min_level: int = 2, dtype=torch.float64, cache_path: str | None = None) -> dict:
+    """One evaluation path for a tree call: every level's node size is timed by bucket (``tune_eval``) and
+    each candidate's time is weighted by the number of nodes of that bucket; the path with the least
+    weighted time wins."""
+    if precision != ffc.MIXED or kernel.kind == ffc.LAPLACE:
+        return {"eval_path": ffc.EVAL_DEFAULT, "source": "no choice"}
+    count = tree.count.cpu().numpy()
+    weights: dict = {}
+    for lv in range(min_level, tree.depth + 1):
+        for n in count[(1 << lv) - 1:(1 << (lv + 1)) - 1]:
+            if n > 0:
+                nb = n_bucket(int(n))
+                weights[nb] = weights.get(nb, 0) + 1
+    per = {nb: tune_eval(kernel, d, nb, precision, s_max, dtype, cache_path=cache_path) for nb in weights}
+    total = {}
+    for path in EVAL_CANDIDATES:
+        t = 0.0
+        for nb, w in weights.items():
+            t += w * per[nb].get("table", {}).get(str(path), math.inf)
+        total[path] = t
+    best = min(total, key=total.get)
+    return {"eval_path": best, "weighted_ms": round(total[best], 3), "buckets": {str(k): v for k, v in weights.items()},
+            "by_bucket": {str(k): v.get("eval_path") for k, v in per.items()}}

@@ -763,8 +763,9 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
         pf.items_round[rd] += W;
       }
     }
-    const int eval_launches = P.kernel.kind == FFC_LAPLACE ? 4 : 1;
-    pf.launches += 1 + 1 + eval_launches + qr_launches + 1 + 2 + 1;
+    // Laplace: distances, scale and block; tcgen05: plane prep and block; else one block kernel
+    const int eval_launches = P.kernel.kind == FFC_LAPLACE ? 4 : eshape >= 2 ? 2 : 1;
+    pf.launches += 1 + 1 + (nested ? 1 : 0) + eval_launches + qr_launches + 1 + 2 + 1;
     pf.qr_launches += qr_launches;
     pf.rounds += 1;
     const double per_coord = P.kernel.kind == FFC_POLYNOMIAL ? 2.0 : 3.0;

@@ -141,3 +141,20 @@ def test_tcgen05_wait_that_runs_out_returns_timeout_and_the_device_recovers():
     torch.cuda.synchronize()
     again = _eval(ffc.EVAL_TCGEN05, o_kernels.GAUSSIAN, X, Y, rows, 1.0, centre)
     assert np.array_equal(again, ref)
+
+
+def test_autotuner_picks_an_evaluation_path_per_bucket(tmp_path):
+    from paper_1409_2802_gb300 import autotune
+    k = ffc.Kernel(ffc.GAUSSIAN, h=2.0)
+    cache = str(tmp_path / "eval_tune.json")
+    a = autotune.tune_eval(k, 128, 3000, ffc.MIXED, s=512, cache_path=cache)
+    assert a["source"] == "measured" and a["eval_path"] in autotune.EVAL_CANDIDATES
+    assert set(a["table"]) == {str(p) for p in autotune.EVAL_CANDIDATES}
+    b = autotune.tune_eval(k, 128, 4000, ffc.MIXED, s=512, cache_path=cache)    # same bucket (4096): cached
+    assert b["source"] == "cache" and b["eval_path"] == a["eval_path"]
+    assert autotune.tune_eval(ffc.Kernel(ffc.LAPLACE), 128, 3000)["eval_path"] == ffc.EVAL_DEFAULT
+    P = workloads.gaussian_mixture(N=16384, d=64, k=4, seed=3)
+    t = ffc.ffc_build_tree(cu(P), 256)
+    tt = autotune.tune_tree_eval(t, k, 64, ffc.MIXED, s_max=512, cache_path=cache)
+    assert tt["eval_path"] in autotune.EVAL_CANDIDATES
+    assert sum(tt["buckets"].values()) == (1 << (t.depth + 1)) - 1 - 3    # every node from level 2 down
