@@ -273,8 +273,11 @@ def run_gpu_steps(torch, ffc, parts, precision, steps, warmup, flush_buf, stream
                                                     stream=stream, proposal=prop, sampler=sampler,
                                                     **compress_kwargs(), **qr_kw.get(p.name, {}))
 
-    for _ in range(warmup):
+    for w in range(warmup):
         step()
+        if w == 0:   # profile from the second warm-up step on, so its rounds' graphs are captured untimed
+            for r in results.values():
+                r.profile_enable(True)
     for r in results.values():
         r.profile_enable(True)
         r.profile_reset()

@@ -348,6 +348,18 @@ typedef struct {
   /* eval_path: FFC_EVAL_* evaluation path of the sampled blocks (mixed precision, Gaussian and
    *   polynomial); FFC_EVAL_DEFAULT (0) = the process default (ffc_set_eval_path) */
   int32_t eval_path;
+  /* graphs: 0 = each sample-size round's memsets and launches are captured into a CUDA graph the first
+   *   time that round (same items, sizes, workspace and parameters) runs on this result, and replayed as
+   *   one graph launch whenever it recurs, e.g. in every later call on the same tree; 1 = every kernel is
+   *   launched directly. Identical results either way. */
+  int32_t graphs;
+  /* qr_defer: write-back depth of the pivoted QR's lazy form, for mixed-precision rounds that run the
+   *   register-resident variant (s of 1,024 or 2,048) unblocked. A step still reads every trailing
+   *   column, applies the reflectors not yet written back (kept on chip) and the new one, but writes
+   *   the columns back only every qr_defer steps. 0 = the library's default, 1 = every step (the plain
+   *   form), 2..4 = that depth. Every depth >= 2 gives bitwise the same outputs; against 1 they differ
+   *   by FP32 summation order only. */
+  int32_t qr_defer;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2), the learned proposal
@@ -452,7 +464,8 @@ ffc_status ffc_tree_apply(const void* points_perm_dev, int32_t dtype, int64_t N,
  * the profile; ffc_tree_profile_reset zeroes it. Phases: 0 sampling,
  * 1 block evaluation, 2 pivoted QR, 3 finalize + triangular solve,
  * 4 bookkeeping (size patch, epilogue, table uploads). `launches` counts
- * the library's kernel launches, `qr_flops` the algorithmic flops of the QR
+ * the library's kernels launched (directly or as nodes of a round's CUDA
+ * graph), `qr_flops` the algorithmic flops of the QR
  * steps taken, sum over steps k of 4 (s - k)(n - k) (one dot product and
  * one update per remaining element), `eval_flops` 3 s n d per block
  * (difference, square, add per coordinate; 2 s n d for the polynomial).
@@ -470,6 +483,8 @@ typedef struct {
   double qr_bytes;      /* one read + one write of every QR block, accumulated */
   double qr_ms_round[8];      /* QR time of sample-size round i (s = s0 2^i), accumulated */
   int64_t items_round[8];     /* nodes that round i processed, accumulated */
+  int64_t graph_launches;     /* rounds run as one CUDA graph launch (params.graphs = 0), accumulated */
+  int64_t graph_captures;     /* rounds captured into a new graph, accumulated */
 } ffc_tree_profile;
 
 ffc_status ffc_tree_profile_enable(ffc_tree_result* result, int32_t enabled);

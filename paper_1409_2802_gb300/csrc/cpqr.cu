@@ -646,13 +646,215 @@ __device__ __forceinline__ void update_column_vec_chunked(T* __restrict__ A, int
   }
 }
 
+// ---- lazy form (FP32 columns of at most 128 M rows, held whole in registers) ----------------------
+// Lane l, vector m of a warp holds rows 4 (l + 32 m) .. + 3 of a column, anchored at row 0, so one
+// reflector's arithmetic on a column does not depend on the step it is applied in. The stored columns
+// stay at the state after reflector w (the last write-back); a step re-applies reflectors w + 1 .. k
+// from a ring of D slots in shared memory and writes the columns back only every D steps. Every
+// reflector is applied with the same operations in the same order whatever D is, so the results do not
+// depend on D; a column is then read every step but written once per D steps.
+constexpr int QR_DEFER_MAX = 4;   // slots of the reflector ring
+
+// H_i = I - tau v v^T (v: rows i .. s-1 of a ring slot, v[i] = 1) on NC register-resident columns
+template <int NC, int M>
+__device__ __forceinline__ void lazy_reflect(float4 (&x)[NC][M], const bool (&va)[NC], const float* __restrict__ v,
+                                             float tau, int i, int s, int lane) {
+  float acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int r0 = 4 * (lane + 32 * m);
+    if (r0 + 3 >= i && r0 < s) {
+      const float4 vv = *reinterpret_cast<const float4*>(v + r0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + e;
+        const float vr = (r >= i && r < s) ? vget(vv, e) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fmaf(vr, vget(x[c][m], e), acc[c]);
+      }
+    }
+  }
+  float tw[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) tw[c] = tau * warp_sum(acc[c]);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int r0 = 4 * (lane + 32 * m);
+    if (r0 + 3 >= i && r0 < s) {
+      const float4 vv = *reinterpret_cast<const float4*>(v + r0);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (!va[c]) continue;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = r0 + e;
+          if (r >= i && r < s) vset(x[c][m], e, fmaf(-tw[c], vget(vv, e), vget(x[c][m], e)));
+        }
+      }
+    }
+  }
+}
+
+// Rows [lo, s) of NC columns from global memory (lo a multiple of 4; rows below it are not needed)
+template <int NC, int M>
+__device__ __forceinline__ void lazy_load(float4 (&x)[NC][M], const bool (&va)[NC], const float* __restrict__ base,
+                                          int64_t lda, int lo, int s, int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int r0 = 4 * (lane + 32 * m);
+      x[c][m] = (va[c] && r0 >= lo && r0 < s) ? __ldcg(reinterpret_cast<const float4*>(base + (int64_t)c * lda + r0))
+                                               : float4{0.0f, 0.0f, 0.0f, 0.0f};
+    }
+}
+
+template <int NC, int M>
+__device__ __forceinline__ void lazy_store(const float4 (&x)[NC][M], const bool (&va)[NC], float* __restrict__ base,
+                                           int64_t lda, int lo, int s, int lane) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int r0 = 4 * (lane + 32 * m);
+      if (va[c] && r0 >= lo && r0 < s) *reinterpret_cast<float4*>(base + (int64_t)c * lda + r0) = x[c][m];
+    }
+}
+
+// Entry of row k of column c (every lane)
+template <int NC, int M>
+__device__ __forceinline__ float lazy_row(const float4 (&x)[NC][M], int c, int k) {
+  const int mk = k >> 7, ek = k & 3, lk = (k >> 2) & 31;
+  float v = 0.0f;
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      if (cc == c && m == mk) v = vget(x[cc][m], ek);
+  return __shfl_sync(0xffffffffu, v, lk);
+}
+
+// Squared norm of rows (k, s) of column c from the registers: compensated FP32 sums of exact squares,
+// then the pairwise error-free combination of col_sumsq_f32; meaningful in lane 0
+template <int NC, int M>
+__device__ __forceinline__ double lazy_sumsq(const float4 (&x)[NC][M], int c, int k, int s, int lane) {
+  float sm = 0.f, cm = 0.f;
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    if (cc != c) continue;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int r0 = 4 * (lane + 32 * m);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + e;
+        if (r > k && r < s) comp_add_square(vget(x[cc][m], e), sm, cm);
+      }
+    }
+  }
+  float hi = sm, lo = -cm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float t = hi + h2;
+    const float bb = t - hi;
+    const float err = (hi - (t - bb)) + (h2 - bb);
+    hi = t;
+    lo = lo + l2 + err;
+  }
+  return lane == 0 ? (double)hi + (double)lo : 0.0;
+}
+
+// One step of the lazy form over the CTA's free columns: load (state after w), apply reflectors
+// w + 1 .. k from the ring, downdate with row k, and store when `store` (the state after k).
+template <int NC, int M>
+__device__ __forceinline__ void update_columns_lazy(float* __restrict__ A, int64_t lda, int c0, int ncols,
+                                                    const uint8_t* __restrict__ sels, const float* __restrict__ ring,
+                                                    int ldv, const float* __restrict__ taur, int D, int w, int k,
+                                                    int s, bool store, int warp, int lane, double tol3z,
+                                                    double* __restrict__ vn1s, double* __restrict__ vn2s,
+                                                    unsigned long long& key, Fix128& psum, int emax) {
+  const int lo = (w + 1) & ~3;
+  for (int j0 = warp * NC; j0 < ncols; j0 += QR_WARPS * NC) {
+    bool va[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) va[c] = (j0 + c < ncols) && !sels[j0 + c];
+    float* base = A + (int64_t)(c0 + j0) * lda;
+    float4 x[NC][M];
+    lazy_load<NC, M>(x, va, base, lda, lo, s, lane);
+    for (int i = w + 1; i <= k; ++i) lazy_reflect<NC, M>(x, va, ring + (size_t)(i % D) * ldv, taur[i % D], i, s, lane);
+    if (store) lazy_store<NC, M>(x, va, base, lda, lo, s, lane);
+    // downdate (lane c owns column c), recomputing unsafe norms from the registers
+    float my_ak = 0.0f;
+    bool mine = false;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float akc = lazy_row<NC, M>(x, c, k);
+      if (lane == c) { my_ak = akc; mine = va[c]; }
+    }
+    const int j = j0 + lane;
+    int unsafe = 0;
+    if (mine) {
+      const double rest = fma(-(double)my_ak, (double)my_ak, vn1s[j]);
+      if (rest <= tol3z * vn2s[j]) unsafe = 1;
+      else vn1s[j] = rest;
+    }
+    unsigned um = __ballot_sync(0xffffffffu, unsafe);
+    while (um) {
+      const int src = __ffs(um) - 1;
+      um &= um - 1u;
+      const double nr = lazy_sumsq<NC, M>(x, src, k, s, lane);
+      if (lane == 0) { vn1s[j0 + src] = nr; vn2s[j0 + src] = nr; }
+    }
+    __syncwarp();
+    if (mine) {
+      const double v = vn1s[j];
+      const unsigned long long kj = pivot_key(v, c0 + j);
+      key = kj > key ? kj : key;
+      fix_add(psum, v, emax);
+    }
+  }
+}
+
+// The pivot column p after reflector k - 1 (one warp, the same arithmetic as the pass that last held it):
+// rows [k, s) into the ring slot of reflector k; rows w + 1 .. k - 1 (now final rows of R) into keep[].
+template <int M>
+__device__ __forceinline__ void lazy_pivot_column(const float* __restrict__ cp, const float* __restrict__ ring,
+                                                  int ldv, const float* __restrict__ taur, int D, int w, int k, int s,
+                                                  float* __restrict__ slot, float* __restrict__ keep, int lane) {
+  const bool va[1] = {true};
+  float4 x[1][M];
+  const int lo = (w + 1) & ~3;
+  lazy_load<1, M>(x, va, cp, 0, lo, s, lane);
+  for (int i = w + 1; i < k; ++i) lazy_reflect<1, M>(x, va, ring + (size_t)(i % D) * ldv, taur[i % D], i, s, lane);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int r0 = 4 * (lane + 32 * m);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + e;
+      if (r >= k && r < s) slot[r] = vget(x[0][m], e);
+      if (r > w && r < k) keep[r - w - 1] = vget(x[0][m], e);
+    }
+  }
+}
+
 // BIG: the launch has the register budget (2 CTAs per SM) to hold FP32 columns of up to
 // 512 W rows in registers, so the longest columns (s = 2,048) are read once per step, and
 // to take columns of up to 256 W rows two at a time
-template <typename T, bool BIG>
+// LZ = M > 0 (FP32, BIG, s <= 128 M): the lazy form above with ring depth D; the pivot
+// column is rebuilt by every CTA, and the group's rank-0 CTA writes its new rows of R after the next
+// group barrier, when no CTA reads that column any more.
+template <typename T, bool BIG, int LZ = 0>
 __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict__ vsh, double* __restrict__ vn1s,
                             double* __restrict__ vn2s, T* __restrict__ aks, uint8_t* __restrict__ sels,
-                            int16_t* __restrict__ rcl, QrShared& sh, long long spin_limit) {
+                            int16_t* __restrict__ rcl, QrShared& sh, long long spin_limit,
+                            float* __restrict__ ring = nullptr, int ldv = 0, float* __restrict__ taur = nullptr,
+                            float* __restrict__ keep = nullptr, int D = 1) {
+  constexpr bool LAZY = LZ > 0;
+  constexpr int LZM = LZ > 0 ? LZ : 8, LZNC = LZM >= 16 ? 1 : 2;   // lazy form: vectors per lane, columns per warp
   const int s = it.s, n = it.n;
   T* __restrict__ A = reinterpret_cast<T*>(it.A);
   const int64_t lda = it.lda;
@@ -686,6 +888,8 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
   }
 
   int k = 0;
+  int w = -1;                             // LAZY: reflector the stored columns are up to date with
+  int pend_p = -1, pend_n = 0, pend_lo = 0;   // LAZY: rows of R of the last pivot still to write
   for (;; ++k) {
     // group winner and ||R22||^2 for step k: publish, barrier, reduce the
     // group's slots (integer max of the keys, exact integer sum of the sums)
@@ -718,6 +922,11 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
       }
     }
     __syncthreads();
+    if (LAZY && pend_p >= 0) {   // every CTA of the group is past its last read of the previous pivot column
+      if (a.rank == 0)
+        for (int r = tid; r < pend_n; r += QR_THREADS) A[(int64_t)pend_p * lda + pend_lo + r] = (T)keep[r];
+      pend_p = -1;
+    }
     if (a.g > 1 && !sh.stop && k == 0 && warp == 0) {
       const StepSlot* base = slots;
       unsigned long long kk = 0ull;
@@ -773,12 +982,23 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (sh.stop) break;
     const int p = 0xFFFFF - (int)(sh.key & 0xFFFFFull);
 
-    // reflector from column p, rows k..s-1 (written by its owner before the barrier)
+    // reflector from column p, rows k..s-1 (written by its owner before the barrier; LAZY: rebuilt here
+    // from the state after reflector w, into the ring slot of reflector k)
     const T* cp = A + (int64_t)p * lda;
+    T* const vk = LAZY ? reinterpret_cast<T*>(ring + (size_t)(k % D) * ldv) : vsh;
+    if constexpr (LAZY) {
+      if (warp == 0)
+        lazy_pivot_column<LZM>(reinterpret_cast<const float*>(cp), ring, ldv, taur, D, w, k, s,
+                               reinterpret_cast<float*>(vk), keep, lane);
+      pend_p = p;
+      pend_n = k - 1 - w;
+      pend_lo = w + 1;
+      __syncthreads();
+    }
     T part = (T)0;
     for (int i = k + tid; i < s; i += QR_THREADS) {
-      const T x = __ldcg(cp + i);
-      vsh[i] = x;
+      const T x = LAZY ? vk[i] : __ldcg(cp + i);
+      vk[i] = x;
       if (i > k) part = fma(x, x, part);
     }
     part = warp_sum(part);
@@ -789,7 +1009,7 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     if (tid == 0) {
       T xn2 = (T)0;
       for (int w = 0; w < QR_WARPS; ++w) xn2 += sizeof(T) == 8 ? (T)sh.dw[w] : (T)sh.fw[w];
-      const T alpha = vsh[k];
+      const T alpha = vk[k];
       if (xn2 == (T)0) {
         sh.tau = 0.0;
         sh.tauf = 0.0f;
@@ -804,19 +1024,20 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
         sh.tauf = (float)tt;
         sh.apply = 1;
         sh.beta = (double)beta;
-        vsh[k] = scale;   // read below, then replaced by 1
+        vk[k] = scale;   // read below, then replaced by 1
       }
+      if (LAZY) taur[k % D] = sh.apply ? sh.tauf : 0.0f;
       if (a.rank == 0) { it.piv[k] = p; it.beta[k] = sh.beta; }
       if (p >= c0 && p < c1) sels[p - c0] = 1;
     }
     __syncthreads();
     const bool apply = sh.apply != 0;
     if (apply) {
-      const T scale = vsh[k];
-      for (int i = k + 1 + tid; i < s; i += QR_THREADS) vsh[i] = vsh[i] * scale;
+      const T scale = vk[k];
+      for (int i = k + 1 + tid; i < s; i += QR_THREADS) vk[i] = vk[i] * scale;
     }
     __syncthreads();
-    if (tid == 0) vsh[k] = (T)1;
+    if (tid == 0) vk[k] = (T)1;
     if (tid == 0) sh.n_rc = 0;
     __syncthreads();
 
@@ -828,7 +1049,12 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     Fix128 psum = {0ull, 0ull};
     constexpr int W = Vec<T>::W;
     const int vrows = s - (k & ~(W - 1));
-    if (vec_ok) {
+    if constexpr (LAZY) {
+      const bool store = k - w >= D;
+      update_columns_lazy<LZNC, LZM>(reinterpret_cast<float*>(A), lda, c0, ncols, sels, ring, ldv, taur, D, w, k, s,
+                                     store, warp, lane, TOL3Z, vn1s, vn2s, key, psum, emax);
+      if (store) w = k;
+    } else if (vec_ok) {
       if (vrows <= 32 * W)
         update_columns_vec<T, 8, 1>(A, lda, c0, ncols, sels, vsh, ttau, apply, k, s, warp, lane, TOL3Z, vn1s, vn2s,
                                     key, psum, emax);
@@ -882,6 +1108,24 @@ __device__ void factor_item(const CpqrItem& it, const CtaAssign a, T* __restrict
     cta_reduce_fix(key, psum, sh);
   }
 
+  if constexpr (LAZY) {
+    // the free columns catch up with the reflectors since the last write-back (rows of R12); the last
+    // pivot's rows of R follow (no CTA reads that column any more)
+    if (w < k - 1) {
+      const int lo = (w + 1) & ~3;
+      float* Af = reinterpret_cast<float*>(A);
+      for (int j0 = warp; j0 < ncols; j0 += QR_WARPS) {
+        const bool va[1] = {!sels[j0]};
+        float4 x[1][LZM];
+        float* base = Af + (int64_t)(c0 + j0) * lda;
+        lazy_load<1, LZM>(x, va, base, lda, lo, s, lane);
+        for (int i = w + 1; i < k; ++i) lazy_reflect<1, LZM>(x, va, ring + (size_t)(i % D) * ldv, taur[i % D], i, s, lane);
+        lazy_store<1, LZM>(x, va, base, lda, lo, s, lane);
+      }
+    }
+    if (pend_p >= 0 && a.rank == 0)
+      for (int r = tid; r < pend_n; r += QR_THREADS) A[(int64_t)pend_p * lda + pend_lo + r] = (T)keep[r];
+  }
   // outputs; status_out starts at FFC_OK and a timeout anywhere in the group wins
   if (tid == 0) {
     if (sh.status == FFC_E_TIMEOUT) atomicExch(it.status_out, (int)FFC_E_TIMEOUT);
@@ -1289,11 +1533,10 @@ __device__ void factor_item_blocked(const CpqrItem& it, const CtaAssign a, doubl
   for (int j = tid; j < ncols; j += QR_THREADS) it.selected[c0 + j] = sels[j];
 }
 
-template <typename T, bool BIG>
+template <typename T, bool BIG, int LZ = 0>
 __global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
 cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
-            const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb) {
-  (void)s_max;
+            const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb, int defer) {
   (void)nb;
   // dynamic shared memory: vn1, vn2 (QR_NCOL_MAX doubles each), row-k entries
   // (QR_NCOL_MAX T), recompute list (QR_NCOL_MAX int16), selected flags
@@ -1305,6 +1548,11 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
   int16_t* rcl = reinterpret_cast<int16_t*>(aks + QR_NCOL_MAX);
   uint8_t* sels = reinterpret_cast<uint8_t*>(rcl + QR_NCOL_MAX);
   T* vsh = reinterpret_cast<T*>(sels + QR_NCOL_MAX);
+  // LAZY: the reflector ring (QR_DEFER_MAX slots of qr_ldv(s_max) floats), its taus and the pivot's rows
+  const int ldv = qr_ldv(s_max);
+  float* ring = reinterpret_cast<float*>(vsh + (std::max(s_max, 1) + 8));
+  float* taur = ring + (size_t)QR_DEFER_MAX * ldv;
+  float* keep = taur + QR_DEFER_MAX;
   __shared__ QrShared sh;
   const int e0 = cta_off ? cta_off[blockIdx.x] : (int)blockIdx.x;
   const int e1 = cta_off ? cta_off[blockIdx.x + 1] : (int)blockIdx.x + 1;
@@ -1313,7 +1561,7 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
     const CpqrItem it = items[a.item];
     if (threadIdx.x == 0) sh.status = FFC_OK;
     __syncthreads();
-    factor_item<T, BIG>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh, spin_limit);
+    factor_item<T, BIG, LZ>(it, a, vsh, vn1s, vn2s, aks, sels, rcl, sh, spin_limit, ring, ldv, taur, keep, defer);
     __syncthreads();
   }
 }
@@ -1322,7 +1570,8 @@ cpqr_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ en
 template <typename T, bool BIG>
 __global__ void __launch_bounds__(QR_THREADS, BIG ? 2 : FFC_QR_MIN_BLOCKS)
 cpqr_blocked_kernel(const CpqrItem* __restrict__ items, const CtaAssign* __restrict__ entries,
-                    const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb) {
+                    const int32_t* __restrict__ cta_off, long long spin_limit, int s_max, int nb, int defer) {
+  (void)defer;
   extern __shared__ __align__(16) unsigned char qsm[];
   double* vn1s = reinterpret_cast<double*>(qsm);
   double* vn2s = vn1s + QR_NCOL_MAX;
@@ -1492,21 +1741,34 @@ bool qr_big(int s_max, int big) {
   return big < 0 ? s_max >= QR_BIG_MIN_S_DEFAULT : big != 0;
 }
 
-using QrKernel = void (*)(const CpqrItem*, const CtaAssign*, const int32_t*, long long, int, int);
+using QrKernel = void (*)(const CpqrItem*, const CtaAssign*, const int32_t*, long long, int, int, int);
+
+// the lazy form runs with a ring of defer >= 2 reflectors: FP32 register-resident (BIG) rounds whose columns
+// fit the registers whole (s a multiple of 128, at most 2,048), unblocked
+template <typename T>
+bool qr_lazy(int s_max, int big, int nb, int defer) {
+  return defer >= 2 && nb <= 1 && sizeof(T) == 4 && qr_big<T>(s_max, big) && s_max % 128 == 0 && s_max <= 2048;
+}
 
 template <typename T>
-QrKernel qr_kernel_fn(int s_max, int big, int nb) {
+QrKernel qr_kernel_fn(int s_max, int big, int nb, int defer = 0) {
   const bool b = qr_big<T>(s_max, big);
   if (nb > 1) return b ? cpqr_blocked_kernel<T, true> : cpqr_blocked_kernel<T, false>;
+  if constexpr (sizeof(T) == 4) {
+    if (qr_lazy<T>(s_max, big, nb, defer)) return s_max > 1024 ? cpqr_kernel<T, true, 16> : cpqr_kernel<T, true, 8>;
+  }
   return b ? cpqr_kernel<T, true> : cpqr_kernel<T, false>;
 }
 
 template <typename T>
-size_t cpqr_smem_bytes(int s_max, int nb = 1) {
+size_t cpqr_smem_bytes(int s_max, int nb = 1, int defer = 0, int big = -1) {
   // the Householder vector follows the per-column arrays; 8 spare elements keep the vector loads of its
-  // final (partial) 16-byte group inside the allocation; the blocked form's arrays come after it
+  // final (partial) 16-byte group inside the allocation; the blocked form's arrays or the lazy form's
+  // ring, taus and pivot rows come after it
   const size_t base = QR_NCOL_MAX * (2 * sizeof(double) + sizeof(T) + sizeof(int16_t) + 1) +
                       (size_t)(std::max(s_max, 1) + 8) * sizeof(T);
+  if (qr_lazy<T>(s_max, big, nb, defer))
+    return base + ((size_t)QR_DEFER_MAX * qr_ldv(s_max) + 2 * QR_DEFER_MAX) * sizeof(float);
   if (nb <= 1) return base;
   return qr_blocked_off<T>(s_max) +
          ((size_t)nb * qr_ldv(s_max) + QR_NB_MAX * (2 + QR_WARPS) + (size_t)QR_FS_COLS * nb) * sizeof(T);
@@ -1514,7 +1776,11 @@ size_t cpqr_smem_bytes(int s_max, int nb = 1) {
 
 template <typename T>
 ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const int32_t* cta_off, int grid,
-                         int s_max, cudaStream_t st, int big, int nb) {
+                         int s_max, cudaStream_t st, int big, int nb, int defer) {
+  if (defer < 0 || defer > QR_DEFER_MAX) {
+    set_error("cpqr: deferral depth %d outside [0, %d]", defer, QR_DEFER_MAX);
+    return FFC_E_INVALID;
+  }
   if (s_max > 2048) {
     set_error("cpqr: s = %d exceeds the supported 2048 rows", s_max);
     return FFC_E_INVALID;
@@ -1523,8 +1789,8 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
     set_error("cpqr: panel width %d outside [1, %d]", nb, QR_PANEL_MAX);
     return FFC_E_INVALID;
   }
-  const size_t smem = cpqr_smem_bytes<T>(s_max, nb);
-  auto kfn = qr_kernel_fn<T>(s_max, big, nb);
+  const size_t smem = cpqr_smem_bytes<T>(s_max, nb, defer, big);
+  auto kfn = qr_kernel_fn<T>(s_max, big, nb, defer);
   FFC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1536,15 +1802,16 @@ ffc_status launch_cpqr_t(const CpqrItem* items, const CtaAssign* assign, const i
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off, wait_limit(), s_max, nb));
+  FFC_CUDA(cudaLaunchKernelEx(&cfg, kfn, items, assign, cta_off, wait_limit(), s_max, nb,
+                              qr_lazy<T>(s_max, big, nb, defer) ? defer : 1));
   return FFC_OK;
 }
 
 template <typename T>
-int max_ctas_t(int s_max, int big, int nb) {
+int max_ctas_t(int s_max, int big, int nb, int defer) {
   int per_sm = 0;
-  const size_t smem = cpqr_smem_bytes<T>(s_max, nb);
-  auto kfn = qr_kernel_fn<T>(s_max, big, nb);
+  const size_t smem = cpqr_smem_bytes<T>(s_max, nb, defer, big);
+  auto kfn = qr_kernel_fn<T>(s_max, big, nb, defer);
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, QR_THREADS, smem);
   return per_sm * sm_count();
@@ -1573,8 +1840,8 @@ int64_t trsm_tiles(int64_t n) { return (n + TS_COLS - 1) / TS_COLS; }
 
 int cpqr_min_group(int64_t n) { return (int)std::max<int64_t>(1, (n + QR_NCOL_MAX - 1) / QR_NCOL_MAX); }
 
-int cpqr_max_ctas(int precision, int s_max, int big, int nb) {
-  return precision == FFC_MIXED ? max_ctas_t<float>(s_max, big, nb) : max_ctas_t<double>(s_max, 0, nb);
+int cpqr_max_ctas(int precision, int s_max, int big, int nb, int defer) {
+  return precision == FFC_MIXED ? max_ctas_t<float>(s_max, big, nb, defer) : max_ctas_t<double>(s_max, 0, nb, 0);
 }
 
 int qr_panel(int precision, int s_max, int big, bool blocked) {
@@ -1596,10 +1863,15 @@ int qr_panel(int precision, int s_max, int big, bool blocked) {
 }
 
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid, int s_max,
-                       cudaStream_t st, const int32_t* cta_off, int big, int nb) {
+                       cudaStream_t st, const int32_t* cta_off, int big, int nb, int defer) {
   if (grid <= 0) return FFC_OK;
-  if (precision == FFC_MIXED) return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st, big, nb);
-  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st, 0, nb);
+  if (precision == FFC_MIXED)
+    return launch_cpqr_t<float>(items_dev, assign_dev, cta_off, grid, s_max, st, big, nb, defer);
+  return launch_cpqr_t<double>(items_dev, assign_dev, cta_off, grid, s_max, st, 0, nb, 0);
+}
+
+bool cpqr_lazy(int precision, int s_max, int big, int nb, int defer) {
+  return precision == FFC_MIXED && qr_lazy<float>(s_max, big, nb, defer);
 }
 
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,

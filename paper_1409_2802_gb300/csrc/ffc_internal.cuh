@@ -282,9 +282,14 @@ ffc_status launch_eval(ffc_kernel k, const void* Y, int dtype, const void* X, in
 // big: the register-resident variant (mixed precision only; -1 = the default rule s_max >= 1024)
 // nb: panel width of the blocked form (items with F set; 1 = every item unblocked); qr_panel() gives the
 // library's default for a round of s_max rows
+// defer: >= 2 runs the lazy form (write-back every `defer` steps, at most 4) where cpqr_lazy() allows it;
+// the same results as 0 or 1 up to FP32 summation order (and the same for every depth >= 2)
 ffc_status launch_cpqr(int precision, const CpqrItem* items_dev, const CtaAssign* assign_dev, int grid,
-                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr, int big = -1, int nb = 1);
-int cpqr_max_ctas(int precision, int s_max, int big = -1, int nb = 1);
+                       int s_max, cudaStream_t st, const int32_t* cta_off = nullptr, int big = -1, int nb = 1,
+                       int defer = 0);
+int cpqr_max_ctas(int precision, int s_max, int big = -1, int nb = 1, int defer = 0);
+bool cpqr_lazy(int precision, int s_max, int big, int nb, int defer);
+constexpr int QR_DEFER_DEFAULT = 1;   // deferral depth of the lazy form when ffc_params.qr_defer is 0
 int qr_panel(int precision, int s_max, int big, bool blocked = false);
 constexpr int QR_F_STRIDE = 32;   // elements per column of the blocked form's F
 constexpr int QR_PANEL_MAX = 8;   // widest panel of the blocked form

@@ -17,6 +17,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "ffc_internal.cuh"
@@ -66,6 +67,16 @@ struct ffc_tree_result {
   // tracing
   ffc_tree_profile prof{};
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // CUDA graphs of the rounds already run: a round's memsets and launches, keyed by every byte that shapes
+  // them (its item tables, launch sizes, pointers, parameters); replayed when the same round recurs
+  struct RoundGraph {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+  };
+  std::vector<RoundGraph> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t cap_stream = nullptr;   // private stream the rounds are captured on
 };
 
 namespace {
@@ -508,7 +519,9 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   // the blocked QR needs 16-byte aligned columns (ld = s_nom elements)
   int nb = P.qr_panel > 0 ? P.qr_panel : qr_panel(P.precision, (int)s_nom, big);
   if (((size_t)s_nom * esz) % 16 != 0) nb = 1;
-  const int cap = cpqr_max_ctas(P.precision, (int)s_nom, big, nb);
+  // the lazy form's write-back depth (unblocked rounds only; cpqr_lazy() says where it runs)
+  const int defer = nb > 1 ? 0 : (P.qr_defer > 0 ? P.qr_defer : QR_DEFER_DEFAULT);
+  const int cap = cpqr_max_ctas(P.precision, (int)s_nom, big, nb, defer);
   if (cap <= 0) { set_error("compress_tree: QR kernel cannot be resident"); return FFC_E_CUDA; }
   // The round's QR runs as one cooperative launch per sub-batch of
   // consecutive items whose blocks together fit in QR_L2_BUDGET bytes: the
@@ -689,57 +702,129 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   FFC_CUDA(cudaMemcpyAsync(d_as, ha.data(), sizeof(CtaAssign) * ha.size(), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_coff, hoff.data(), sizeof(int32_t) * hoff.size(), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(oidx, ho.data(), sizeof(int32_t) * W, cudaMemcpyHostToDevice, st));
-  FFC_CUDA(cudaMemsetAsync(est, 0, sizeof(int32_t) * W, st));
-  FFC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * W, st));
-  FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * G, st));   // the QR's group accumulators start at zero
-  FFC_CUDA(cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 12 * (size_t)W, st));
-  FFC_CUDA(cudaMemsetAsync(qst, 0, sizeof(int32_t) * W, st));
-  FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, st));
-  FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, st));
+  std::vector<GatherItem> hg(nested ? W : 0);
+  for (int q = 0; q < (int)hg.size(); ++q) {
+    const int o = items[q];
+    hg[q] = GatherItem{noff[q], R->begin_h[o], R->cols + R->skel_off_h[o], R->ncols_h[o]};
+  }
+  if (nested) FFC_CUDA(cudaMemcpyAsync(d_gi, hg.data(), sizeof(GatherItem) * W, cudaMemcpyHostToDevice, st));
 
   const bool prof = R->prof.enabled != 0;
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[0], st));
-  ffc_status rc = FFC_OK;
-  if (learned) {   // the node's best s_max rows were drawn once per call: take the first s_nom
-    learned_round_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, oidx, s_nom, R->lcount, R->lfar, s_out, fc);
-    FFC_CUDA(cudaGetLastError());
-  } else {
-    rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, st);
+  // The round's memsets and launches on stream cs; while cs is capturing, the profile's events become
+  // event-record nodes of the graph.
+  auto record = [&](int i, cudaStream_t cs, bool capturing) -> ffc_status {
+    if (prof)
+      FFC_CUDA(capturing ? cudaEventRecordWithFlags(R->ev[i], cs, cudaEventRecordExternal) : cudaEventRecord(R->ev[i], cs));
+    return FFC_OK;
+  };
+  auto enqueue = [&](cudaStream_t cs, bool capturing) -> ffc_status {
+    FFC_CUDA(cudaMemsetAsync(est, 0, sizeof(int32_t) * W, cs));
+    FFC_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned) * W, cs));
+    FFC_CUDA(cudaMemsetAsync(slots, 0, sizeof(Slot) * 2 * G, cs));   // the QR's group accumulators start at zero
+    FFC_CUDA(cudaMemsetAsync(red, 0, sizeof(unsigned long long) * 12 * (size_t)W, cs));
+    FFC_CUDA(cudaMemsetAsync(qst, 0, sizeof(int32_t) * W, cs));
+    FFC_CUDA(cudaMemsetAsync(qrank, 0, sizeof(int32_t) * W, cs));
+    FFC_CUDA(cudaMemsetAsync(qr22, 0, sizeof(double) * W, cs));
+    ffc_status rc = record(0, cs, capturing);
     if (rc != FFC_OK) return rc;
-  }
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[1], st));
-  patch_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
-  if (nested) {   // the ID's column points of every item, packed (item q at rows noff[q] of the arena)
-    std::vector<GatherItem> hg(W);
-    for (int q = 0; q < W; ++q) {
-      const int o = items[q];
-      hg[q] = GatherItem{noff[q], R->begin_h[o], R->cols + R->skel_off_h[o], R->ncols_h[o]};
+    if (learned) {   // the node's best s_max rows were drawn once per call: take the first s_nom
+      learned_round_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, oidx, s_nom, R->lcount, R->lfar, s_out, fc);
+      FFC_CUDA(cudaGetLastError());
+    } else {
+      rc = launch_sample(X, R->dtype, d, d_si, W, R->N, s_nom, P.seed, s_out, fc, sst, scratch, cs);
+      if (rc != FFC_OK) return rc;
     }
-    FFC_CUDA(cudaMemcpyAsync(d_gi, hg.data(), sizeof(GatherItem) * W, cudaMemcpyHostToDevice, st));
-    gather_cols_kernel<<<dim3(8, (unsigned)W), 256, 0, st>>>(d_gi, X, Xcols, d, pts_esz);
+    if ((rc = record(1, cs, capturing)) != FFC_OK) return rc;
+    patch_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, s_out, s_nom, r_cap_glob, d_ei, d_qi);
+    if (nested) {   // the ID's column points of every item, packed (item q at rows noff[q] of the arena)
+      gather_cols_kernel<<<dim3(8, (unsigned)W), 256, 0, cs>>>(d_gi, X, Xcols, d, pts_esz);
+      FFC_CUDA(cudaGetLastError());
+    }
+    rc = launch_eval(P.kernel, X, R->dtype, nested ? Xcols : X, d, P.precision, eshape, d_ei, W, tiles_tot, mind2,
+                     lsc, est, t5scr, t5rows, cs);
+    if (rc != FFC_OK) return rc;
+    if ((rc = record(2, cs, capturing)) != FFC_OK) return rc;
+    // one cooperative QR launch per L2-sized sub-batch of the round
+    for (int bb = 0; bb < n_sb; ++bb) {
+      rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, cs, d_coff + sb_coff[bb], big,
+                       sb_nb[bb], sb_nb[bb] > 1 ? 0 : defer);
+      if (rc != FFC_OK) return rc;
+    }
+    if ((rc = record(3, cs, capturing)) != FFC_OK) return rc;
+    gate_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, s_nom, P.s_max, s_out, qst, qrank, trank);
+    rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, cs);
+    if (rc != FFC_OK) return rc;
+    if ((rc = record(4, cs, capturing)) != FFC_OK) return rc;
+    epilogue_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, oidx, s_nom, P.s_max, s_out, fc, lsc, est, qrank, qr22, qst,
+                                                     R->rank, R->s, R->status, R->r22, R->log_scale, R->far_count,
+                                                     flags);
     FFC_CUDA(cudaGetLastError());
+    return record(5, cs, capturing);
+  };
+  bool launched = false;
+  if (P.graphs == 0) {
+    // the key: every byte the launches depend on (the tables hold the items' device pointers)
+    std::string key;
+    auto put = [&key](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
+    const long long wl = wait_limit();
+    const void* ptrs[] = {X, Xcols, R->ws, R->lcount, R->lfar, R->rank, R->s, R->status, R->r22, R->log_scale,
+                          R->far_count};
+    const int64_t sc[] = {W, s_nom, learned, nested, prof, eshape, tiles_tot, t5rows, n_sb, big, ttot, rcap_round,
+                          r_cap_glob, G, d, R->dtype, R->N, (int64_t)R->ws_bytes, (int64_t)pts_esz, wl};
+    put(ptrs, sizeof(ptrs));
+    put(sc, sizeof(sc));
+    put(&P, sizeof(P));
+    put(sb_grid.data(), sizeof(int) * sb_grid.size());
+    put(sb_as.data(), sizeof(int) * sb_as.size());
+    put(sb_coff.data(), sizeof(int) * sb_coff.size());
+    put(sb_nb.data(), sizeof(int) * sb_nb.size());
+    put(hs.data(), sizeof(SampleItem) * W);
+    put(he.data(), sizeof(EvalItem) * W);
+    put(hq.data(), sizeof(CpqrItem) * W);
+    put(ht.data(), sizeof(TrsmItem) * W);
+    put(ha.data(), sizeof(CtaAssign) * ha.size());
+    put(hoff.data(), sizeof(int32_t) * hoff.size());
+    put(ho.data(), sizeof(int32_t) * W);
+    put(hg.data(), sizeof(GatherItem) * hg.size());
+    ffc_tree_result::RoundGraph* hit = nullptr;
+    for (auto& g : R->graphs)
+      if (g.key == key) { hit = &g; break; }
+    if (!hit) {
+      // capture on the result's private stream; any refusal leaves the round to the direct launches below
+      if (!R->cap_stream) FFC_CUDA(cudaStreamCreateWithFlags(&R->cap_stream, cudaStreamNonBlocking));
+      cudaGraphExec_t ex = nullptr;
+      if (cudaStreamBeginCapture(R->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const ffc_status crc = enqueue(R->cap_stream, true);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(R->cap_stream, &gr);
+        if (crc == FFC_OK && ce == cudaSuccess && gr && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) ex = nullptr;
+        if (gr) cudaGraphDestroy(gr);
+      }
+      (void)cudaGetLastError();
+      if (ex) {
+        if (R->graphs.size() >= 16) {   // least recently used out
+          auto lru = std::min_element(R->graphs.begin(), R->graphs.end(),
+                                      [](const auto& x, const auto& y) { return x.used < y.used; });
+          cudaGraphExecDestroy(lru->exec);
+          R->graphs.erase(lru);
+        }
+        R->graphs.push_back({std::move(key), ex, 0});
+        hit = &R->graphs.back();
+        R->prof.graph_captures += 1;
+      }
+    }
+    if (hit) {
+      hit->used = ++R->graph_clock;
+      FFC_CUDA(cudaGraphLaunch(hit->exec, st));
+      R->prof.graph_launches += 1;
+      launched = true;
+    }
   }
-  rc = launch_eval(P.kernel, X, R->dtype, nested ? Xcols : X, d, P.precision, eshape, d_ei, W, tiles_tot, mind2, lsc,
-                   est, t5scr, t5rows, st);
-  if (rc != FFC_OK) return rc;
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[2], st));
-  // one cooperative QR launch per L2-sized sub-batch of the round
-  for (int bb = 0; bb < n_sb; ++bb) {
-    rc = launch_cpqr(P.precision, d_qi, d_as + sb_as[bb], sb_grid[bb], (int)s_nom, st, d_coff + sb_coff[bb], big,
-                     sb_nb[bb]);
+  if (!launched) {
+    const ffc_status rc = enqueue(st, false);
     if (rc != FFC_OK) return rc;
   }
   const int qr_launches = n_sb;
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[3], st));
-  gate_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, s_nom, P.s_max, s_out, qst, qrank, trank);
-  rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, st);
-  if (rc != FFC_OK) return rc;
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[4], st));
-  epilogue_kernel<<<(W + 127) / 128, 128, 0, st>>>(W, oidx, s_nom, P.s_max, s_out, fc, lsc, est, qrank, qr22, qst,
-                                                   R->rank, R->s, R->status, R->r22, R->log_scale, R->far_count,
-                                                   flags);
-  FFC_CUDA(cudaGetLastError());
-  if (prof) FFC_CUDA(cudaEventRecord(R->ev[5], st));
   std::vector<int32_t> hf(W), hr(prof ? W : 0);
   std::vector<int64_t> hsz(prof ? W : 0);
   FFC_CUDA(cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, st));
@@ -804,6 +889,8 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   FFC_REQUIRE(P.qr_panel >= 0 && P.qr_panel <= QR_PANEL_MAX, "ffc_compress_tree: qr_panel must be in [0, %d]",
               QR_PANEL_MAX);
   FFC_REQUIRE(P.eval_path >= FFC_EVAL_DEFAULT && P.eval_path <= FFC_EVAL_LAST, "ffc_compress_tree: bad eval_path");
+  FFC_REQUIRE(P.graphs == 0 || P.graphs == 1, "ffc_compress_tree: graphs must be 0 or 1");
+  FFC_REQUIRE(P.qr_defer >= 0 && P.qr_defer <= 4, "ffc_compress_tree: qr_defer must be in [0, 4]");
   FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");
@@ -917,6 +1004,8 @@ ffc_status ffc_tree_result_view(const ffc_tree_result* R, ffc_tree_view* v) {
 
 void ffc_tree_result_free(ffc_tree_result* R) {
   if (!R) return;
+  for (auto& g : R->graphs) cudaGraphExecDestroy(g.exec);
+  if (R->cap_stream) cudaStreamDestroy(R->cap_stream);
   if (R->out_mem) cudaFree(R->out_mem);
   if (R->ws) cudaFree(R->ws);
   if (R->pws) cudaFree(R->pws);

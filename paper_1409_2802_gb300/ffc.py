@@ -70,7 +70,8 @@ class c_params(ctypes.Structure):
                 ("xi", ctypes.c_double), ("seed", ctypes.c_uint64), ("sampler", ctypes.c_int32),
                 ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
                 ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32),
-                ("nested", ctypes.c_int32), ("eval_path", ctypes.c_int32)]
+                ("nested", ctypes.c_int32), ("eval_path", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("qr_defer", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -85,7 +86,8 @@ class c_tree_profile(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("launches", ctypes.c_int64), ("qr_launches", ctypes.c_int64),
                 ("ms", ctypes.c_double * 5), ("qr_flops", ctypes.c_double), ("eval_flops", ctypes.c_double),
                 ("qr_bytes", ctypes.c_double), ("qr_ms_round", ctypes.c_double * 8),
-                ("items_round", ctypes.c_int64 * 8)]
+                ("items_round", ctypes.c_int64 * 8), ("graph_launches", ctypes.c_int64),
+                ("graph_captures", ctypes.c_int64)]
 
 
 @dataclass(frozen=True)
@@ -329,7 +331,8 @@ class TreeResult:
         _check(lib().ffc_tree_profile_get(self.handle, ctypes.byref(p)))
         return {"calls": p.calls, "rounds": p.rounds, "launches": p.launches, "qr_launches": p.qr_launches,
                 "ms": dict(zip(PROFILE_PHASES, list(p.ms))), "qr_flops": p.qr_flops, "eval_flops": p.eval_flops,
-                "qr_bytes": p.qr_bytes, "qr_ms_round": list(p.qr_ms_round), "items_round": list(p.items_round)}
+                "qr_bytes": p.qr_bytes, "qr_ms_round": list(p.qr_ms_round), "items_round": list(p.items_round),
+                "graph_launches": p.graph_launches, "graph_captures": p.graph_captures}
 
     def close(self):
         if self.handle and self.handle.value:
@@ -347,11 +350,13 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
                       qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0, nested=False,
-                      eval_path=EVAL_DEFAULT) -> TreeResult:
+                      eval_path=EVAL_DEFAULT, graphs=True, qr_defer=0) -> TreeResult:
     """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
     ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``, ``qr_panel``:
     the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``);
-    ``eval_path``: one of EVAL_* for the mixed-precision Gaussian / polynomial blocks."""
+    ``eval_path``: one of EVAL_* for the mixed-precision Gaussian / polynomial blocks; ``graphs``: run each round
+    as a captured CUDA graph (replayed when the round recurs) instead of direct launches; ``qr_defer``: the QR's
+    write-back depth (0 = the library's default, 1 = every step, 2..4 = the lazy form)."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
@@ -363,7 +368,8 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
         sampler, proj_p, mlp_p = 1, proj.data_ptr(), mlp.data_ptr()
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
                  ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
-                 int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0, int(eval_path))
+                 int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0, int(eval_path), 0 if graphs else 1,
+                 int(qr_defer))
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
