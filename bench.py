@@ -998,8 +998,11 @@ def main():
                 ent["fp64_plain"] = {"value": v2, "ms_per_step": ms2 / args.arm_steps, "steps": args.arm_steps}
                 ent["speedup_vs_fp64"] = v1 / v2
             if cname == "c2" and rank == 0:
-                ent["studies"] = d16_studies(torch, ffc, cparts[0], cprop[cparts[0].name] if cprop else None, stream,
-                                             prec)
+                try:   # auxiliary (untimed) studies: a failure there is recorded, not fatal to the line
+                    ent["studies"] = d16_studies(torch, ffc, cparts[0], cprop[cparts[0].name] if cprop else None,
+                                                 stream, prec)
+                except Exception as e:   # noqa: BLE001
+                    ent["studies"] = {"error": f"{type(e).__name__}: {str(e)[:200]}"}
             extra[cname] = ent
             del cparts
             torch.cuda.empty_cache()
