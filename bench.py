@@ -800,8 +800,7 @@ def tune_parts(ffc, parts, prec, stream, proposal, max_step_s=1.5):
     for p in parts:
         select_workload(p.name)
         W = dict(WORKLOADS[p.name], **COMMON)
-        te = autotune.tune_tree_eval(p.tree, p.kern, int(p.Pp.shape[1]), prec, s_max=W["s_max"],
-                                     min_level=W["min_level"], dtype=p.Pp.dtype)
+        te = autotune.tune_tree_eval(p.Pp, p.tree, p.kern, prec, min_level=W["min_level"], stream=stream)
         kw[p.name] = {"eval_path": te["eval_path"]}
         prop = proposal[p.name] if isinstance(proposal, dict) else proposal
         t0 = time.perf_counter()

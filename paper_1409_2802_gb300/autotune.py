@@ -23,13 +23,13 @@ It returns the fastest setting and the table of everything it timed.
 polynomial blocks: the mma.sync tiles or one of the tcgen05 tile variants
 (output tile, coordinates per stage, stage count). The choice is keyed by
 (d, precision, kernel, n-bucket, s, point dtype) and cached; it times single
-blocks of s rows against n sources of that bucket. ``tune_tree_eval`` weighs
-the buckets of a tree's levels by how many blocks of each a call evaluates.
+blocks of s rows against n sources of that bucket. ``tune_tree_eval`` times
+the candidates where they run: the evaluation phase of a one-round compression
+call on the caller's tree.
 """
 from __future__ import annotations
 
 import json
-import math
 import os
 import time
 
@@ -155,27 +155,39 @@ def tune_eval(kernel: ffc.Kernel, d: int, n: int, precision=ffc.MIXED, s: int = 
     return dict(out, source="measured")
 
 
-def tune_tree_eval(tree: ffc.DeviceTree, kernel: ffc.Kernel, d: int, precision=ffc.MIXED, s_max: int = 2048,
-                   min_level: int = 2, dtype=torch.float64, cache_path: str | None = None) -> dict:
-    """One evaluation path for a tree call: every level's node size is timed by bucket (``tune_eval``) and
-    each candidate's time is weighted by the number of nodes of that bucket; the path with the least
-    weighted time wins."""
+def tune_tree_eval(points_perm, tree: ffc.DeviceTree, kernel: ffc.Kernel, precision=ffc.MIXED, s_probe: int = 512,
+                   min_level: int = 2, stream=None, reps: int = 1, cache_path: str | None = None) -> dict:
+    """One evaluation path for a tree call, timed where it runs: for every candidate, a compression call of a
+    single sample-size round (s0 = s_max = s_probe, uniform rows) on the caller's tree with the tree profile
+    on, after one untimed call; the candidate with the least evaluation-phase time (its prep and block
+    kernels, CUDA events) wins. Single-block timings (``tune_eval``) carry a per-call overhead of the order
+    of the small blocks' kernel time and cannot rank the paths at d = 128; the round holds the tree's real
+    mix of block sizes. Keyed by (d, precision, kernel, N, depth, s_probe, point dtype) and cached."""
     if precision != ffc.MIXED or kernel.kind == ffc.LAPLACE:
         return {"eval_path": ffc.EVAL_DEFAULT, "source": "no choice"}
-    count = tree.count.cpu().numpy()
-    weights: dict = {}
-    for lv in range(min_level, tree.depth + 1):
-        for n in count[(1 << lv) - 1:(1 << (lv + 1)) - 1]:
-            if n > 0:
-                nb = n_bucket(int(n))
-                weights[nb] = weights.get(nb, 0) + 1
-    per = {nb: tune_eval(kernel, d, nb, precision, s_max, dtype, cache_path=cache_path) for nb in weights}
-    total = {}
+    N, d = points_perm.shape
+    key = (f"tree:d={d},precision={precision},kernel={kernel.kind},N={N},depth={tree.depth},s={s_probe},"
+           f"dtype={str(points_perm.dtype).split('.')[-1]}")
+    if key not in _EVAL_CACHE and cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            _EVAL_CACHE.update(json.load(f))
+    if key in _EVAL_CACHE:
+        return dict(_EVAL_CACHE[key], source="cache")
+    kw = dict(tol=1e-6, precision=precision, s0=s_probe, s_max=s_probe, min_level=min_level, stream=stream)
+    table = {}
     for path in EVAL_CANDIDATES:
-        t = 0.0
-        for nb, w in weights.items():
-            t += w * per[nb].get("table", {}).get(str(path), math.inf)
-        total[path] = t
-    best = min(total, key=total.get)
-    return {"eval_path": best, "weighted_ms": round(total[best], 3), "buckets": {str(k): v for k, v in weights.items()},
-            "by_bucket": {str(k): v.get("eval_path") for k, v in per.items()}}
+        res = ffc.ffc_compress_tree(points_perm, tree, kernel, eval_path=path, **kw)   # untimed
+        res.profile_enable(True)
+        res.profile_reset()
+        for _ in range(reps):
+            res = ffc.ffc_compress_tree(points_perm, tree, kernel, eval_path=path, result=res, **kw)
+        table[path] = res.profile()["ms"]["eval"] / reps
+        res.close()
+    best = min(table, key=table.get)
+    out = {"eval_path": best, "eval_ms": round(table[best], 3), "s_probe": s_probe,
+           "table": {str(k): round(v, 3) for k, v in table.items()}}
+    _EVAL_CACHE[key] = out
+    if cache_path:
+        with open(cache_path, "w") as f:
+            json.dump(_EVAL_CACHE, f, indent=1, sort_keys=True)
+    return dict(out, source="measured")

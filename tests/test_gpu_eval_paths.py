@@ -155,6 +155,9 @@ def test_autotuner_picks_an_evaluation_path_per_bucket(tmp_path):
     assert autotune.tune_eval(ffc.Kernel(ffc.LAPLACE), 128, 3000)["eval_path"] == ffc.EVAL_DEFAULT
     P = workloads.gaussian_mixture(N=16384, d=64, k=4, seed=3)
     t = ffc.ffc_build_tree(cu(P), 256)
-    tt = autotune.tune_tree_eval(t, k, 64, ffc.MIXED, s_max=512, cache_path=cache)
-    assert tt["eval_path"] in autotune.EVAL_CANDIDATES
-    assert sum(tt["buckets"].values()) == (1 << (t.depth + 1)) - 1 - 3    # every node from level 2 down
+    Pp = cu(P)[t.perm].contiguous()
+    tt = autotune.tune_tree_eval(Pp, t, k, ffc.MIXED, s_probe=256, cache_path=cache)
+    assert tt["source"] == "measured" and tt["eval_path"] in autotune.EVAL_CANDIDATES
+    assert set(tt["table"]) == {str(p) for p in autotune.EVAL_CANDIDATES}
+    assert all(v > 0 for v in tt["table"].values())
+    assert autotune.tune_tree_eval(Pp, t, k, ffc.MIXED, s_probe=256, cache_path=cache)["source"] == "cache"
