@@ -104,6 +104,14 @@ ffc_status ffc_set_wait_limit(int64_t polls);
 #define FFC_EVAL_TCGEN05_TILE0 4
 #define FFC_EVAL_TCGEN05_TILES 5
 
+/* Triangular solve T = R11^-1 R12 of the mixed-precision path (the FP64 path always solves in FP64):
+ * FFC_SOLVE_DEFAULT: FP32 solves refined once (T1 with R11 rounded to FP32; the residual
+ *   R12 - R11 T1 from exact products summed in double-float, the diagonal term in FP64; its FP32
+ *   solve added to T1 in FP64), about the FP64 solve's accuracy at the FP32 rate;
+ * FFC_SOLVE_FP64: FP64 back-substitution. */
+#define FFC_SOLVE_DEFAULT 0
+#define FFC_SOLVE_FP64 1
+
 /*
  * ffc_set_eval_path - the evaluation path FFC_EVAL_DEFAULT stands for, for
  * ffc_eval_block and for ffc_compress_tree calls whose params.eval_path is
@@ -360,6 +368,8 @@ typedef struct {
    *   form), 2..4 = that depth. Every depth >= 2 gives bitwise the same outputs; against 1 they differ
    *   by FP32 summation order only. */
   int32_t qr_defer;
+  /* solve: FFC_SOLVE_* of the mixed-precision triangular solve (FFC_SOLVE_DEFAULT = 0) */
+  int32_t solve;
 } ffc_params;
 
 /* Row sampler of a tree compression: uniform (§2.2), the learned proposal

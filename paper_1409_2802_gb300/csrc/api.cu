@@ -280,6 +280,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
                  round_up(sizeof(CtaAssign) * g) + round_up(sizeof(int32_t) * rc_cap) +
                  round_up(sizeof(double) * rc_cap) + 2 * round_up(sizeof(double) * n) + round_up((size_t)n) +
                  round_up(sizeof(Slot) * 2 * g) + round_up((size_t)rc_cap * rc_cap * sizeof(double)) +
+                 (precision == FFC_MIXED ? round_up((size_t)((rc_cap + 3) & ~3) * ((rc_cap + 3) & ~3) * sizeof(float)) : 0) +
                  round_up(12 * sizeof(unsigned long long)) +
                  (nbl > 1 ? round_up((size_t)n * QR_F_STRIDE * esz) : 0);
   FFC_CUDA(cudaMallocAsync((void**)&ar.base, bytes, st));
@@ -293,6 +294,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   uint8_t* sel = ar.take<uint8_t>(n);
   Slot* slots = ar.take<Slot>(2 * g);
   double* R11 = ar.take<double>((size_t)rc_cap * rc_cap);
+  float* R11f = precision == FFC_MIXED ? ar.take<float>((size_t)((rc_cap + 3) & ~3) * ((rc_cap + 3) & ~3)) : nullptr;
   unsigned* barrier = ar.take<unsigned>(1);
   unsigned long long* red = ar.take<unsigned long long>(12);
   int32_t* rank = ar.take<int32_t>(1);
@@ -308,7 +310,7 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
   for (int c = 0; c < g; ++c) asg[c] = CtaAssign{0, c, g, 0};
   TrsmItem ti = {};
   ti.A = K_dev; ti.lda = ldk; ti.n = (int32_t)n; ti.rank = rank; ti.piv = piv; ti.beta = beta; ti.selected = sel;
-  ti.skel_perm = skel_perm_dev; ti.R11 = R11; ti.T = T_dev; ti.ldt = ldt; ti.r_cap = rc_cap;
+  ti.skel_perm = skel_perm_dev; ti.R11 = R11; ti.R11f = R11f; ti.T = T_dev; ti.ldt = ldt; ti.r_cap = rc_cap;
   ti.tile_begin = 0;
   FFC_CUDA(cudaMemcpyAsync(d_item, &hi, sizeof(hi), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(d_titem, &ti, sizeof(ti), cudaMemcpyHostToDevice, st));

@@ -138,6 +138,8 @@ struct TrsmItem {
   const uint8_t* selected;
   int32_t* skel_perm;   // n
   double* R11;          // r_cap x r_cap workspace (row-major, ld r)
+  float* R11f;          // FP32 copy, column-major, ld = r rounded up to 4, (r_cap rounded up to 4)^2 floats,
+                        // 16-byte aligned (mixed precision's refined solve; NULL otherwise)
   double* T;            // output
   int64_t ldt;          // <= 0: ld = rank (packed)
   int32_t r_cap, pad1;
@@ -298,8 +300,9 @@ constexpr int QR_BIG_MIN_S_DEFAULT = 1024;
 constexpr int QR_L2_BUDGET_MB_DEFAULT = 96;
 int cpqr_min_group(int64_t n);   // fewest CTAs a group of n columns may have (per-CTA column cap)
 int64_t trsm_tiles(int64_t n);   // CTAs of the triangular solve for n columns
+// solve: FFC_SOLVE_DEFAULT (mixed precision: FP32 solves refined once) or FFC_SOLVE_FP64
 ffc_status launch_trsm_batched(int precision, const TrsmItem* items_dev, int n_items, int64_t total_tiles,
-                               int r_cap_max, cudaStream_t st);
+                               int r_cap_max, cudaStream_t st, int solve = FFC_SOLVE_DEFAULT);
 ffc_status launch_id_error(ffc_kernel k, const void* Y, int dtype, const int64_t* rows, int64_t m,
                            const void* X, int64_t n, int d, const int32_t* skel, const double* T,
                            int64_t ldt, int64_t r, double* partial /* workspace */, int64_t n_partial,

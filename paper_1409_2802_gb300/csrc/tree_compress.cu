@@ -495,9 +495,9 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   const bool nested = P.nested != 0;
   const size_t pts_esz = R->dtype == FFC_F64 ? sizeof(double) : sizeof(float);
   // per-item sizes
-  std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), tiles(W), t5base(W);
+  std::vector<int64_t> koff(W), noff(W), goff(W), r11off(W), r11foff(W), tiles(W), t5base(W);
   std::vector<int> g(W);
-  int64_t SN = 0, elems = 0, RC = 0, tiles_tot = 0, n_max = 0, t5rows = 0;
+  int64_t SN = 0, elems = 0, RC = 0, RCF = 0, tiles_tot = 0, n_max = 0, t5rows = 0;
   const int eshape = eval_shape(P.kernel, d, P.precision, P.eval_path);
   for (int q = 0; q < W; ++q) {
     const int64_t n = R->ncols_h[items[q]];
@@ -508,6 +508,8 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     r11off[q] = RC;
     const int64_t rc = std::min<int64_t>(n, rcap_round);
     RC += rc * rc;
+    r11foff[q] = RCF;
+    RCF += ((rc + 3) & ~3) * ((rc + 3) & ~3);   // the FP32 copy's padded leading dimension
     tiles[q] = tiles_tot;
     tiles_tot += eval_tiles(s_nom, n, eshape);
     n_max = std::max(n_max, n);
@@ -610,6 +612,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
                o_slots = L.add<Slot>(2 * G), o_red = L.add<unsigned long long>(12 * (size_t)W),
                o_bar = L.add<unsigned>(W), o_rank = L.add<int32_t>(W),
                o_r22 = L.add<double>(W), o_qst = L.add<int32_t>(W), o_R11 = L.add<double>(std::max<int64_t>(RC, 1)),
+               o_R11f = L.add<float>(P.precision == FFC_MIXED ? std::max<int64_t>(RCF, 1) : 0),
                o_scr = L.add<int32_t>((size_t)scratch_ctas * R->N), o_flag = L.add<int32_t>(W),
                o_oidx = L.add<int32_t>(W), o_trank = L.add<int32_t>(W),
                o_F = L.add<char>(nb > 1 ? (size_t)SN * QR_F_STRIDE * esz : 0),
@@ -651,6 +654,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
   double* qr22 = (double*)(b + o_r22);
   int32_t* qst = (int32_t*)(b + o_qst);
   double* R11 = (double*)(b + o_R11);
+  float* R11f = P.precision == FFC_MIXED ? (float*)(b + o_R11f) : nullptr;
   int32_t* scratch = (int32_t*)(b + o_scr);
   int32_t* flags = (int32_t*)(b + o_flag);
   int32_t* oidx = (int32_t*)(b + o_oidx);
@@ -691,7 +695,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     TrsmItem& ti = ht[q];
     ti = TrsmItem{};
     ti.A = (void*)((char*)K + esz * koff[q]); ti.lda = s_nom; ti.n = (int32_t)n; ti.rank = trank + q; ti.piv = qi.piv; ti.beta = qi.beta;
-    ti.selected = qi.selected; ti.skel_perm = R->skel + R->skel_off_h[o]; ti.R11 = R11 + r11off[q];
+    ti.selected = qi.selected; ti.skel_perm = R->skel + R->skel_off_h[o]; ti.R11 = R11 + r11off[q]; ti.R11f = R11f ? R11f + r11foff[q] : nullptr;
     ti.T = R->T + R->T_off_h[o]; ti.ldt = 0; ti.r_cap = (int32_t)std::min<int64_t>(n, rcap_round);
     ti.tile_begin = ttiles[q];
   }
@@ -752,7 +756,7 @@ ffc_status run_round(ffc_tree_result* R, const void* X, const ffc_tree* tree, co
     }
     if ((rc = record(3, cs, capturing)) != FFC_OK) return rc;
     gate_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, s_nom, P.s_max, s_out, qst, qrank, trank);
-    rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, cs);
+    rc = launch_trsm_batched(P.precision, d_ti, W, ttot, rcap_round, cs, P.solve);
     if (rc != FFC_OK) return rc;
     if ((rc = record(4, cs, capturing)) != FFC_OK) return rc;
     epilogue_kernel<<<(W + 127) / 128, 128, 0, cs>>>(W, oidx, s_nom, P.s_max, s_out, fc, lsc, est, qrank, qr22, qst,
@@ -891,6 +895,7 @@ ffc_status ffc_compress_tree(const void* points_perm_dev, int32_t dtype, int64_t
   FFC_REQUIRE(P.eval_path >= FFC_EVAL_DEFAULT && P.eval_path <= FFC_EVAL_LAST, "ffc_compress_tree: bad eval_path");
   FFC_REQUIRE(P.graphs == 0 || P.graphs == 1, "ffc_compress_tree: graphs must be 0 or 1");
   FFC_REQUIRE(P.qr_defer >= 0 && P.qr_defer <= 4, "ffc_compress_tree: qr_defer must be in [0, 4]");
+  FFC_REQUIRE(P.solve == FFC_SOLVE_DEFAULT || P.solve == FFC_SOLVE_FP64, "ffc_compress_tree: bad solve");
   FFC_REQUIRE(P.tol > 0.0 && P.xi > 0.0, "ffc_compress_tree: need tol > 0 and xi > 0");
   FFC_REQUIRE(tree->depth >= 0 && tree->n_nodes == ((int64_t)1 << (tree->depth + 1)) - 1,
               "ffc_compress_tree: n_nodes must be 2^(depth+1) - 1");

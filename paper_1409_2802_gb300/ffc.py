@@ -33,6 +33,7 @@ F64, F32 = 0, 1
 FP64, MIXED = 0, 1
 EVAL_DEFAULT, EVAL_SIMT, EVAL_MMA_SYNC, EVAL_TCGEN05 = 0, 1, 2, 3
 EVAL_TCGEN05_TILE0, EVAL_TCGEN05_TILES = 4, 5   # EVAL_TCGEN05_TILE0 + v: tcgen05 tile variant v
+SOLVE_DEFAULT, SOLVE_FP64 = 0, 1
 
 EXPORTS = (
     "ffc_last_error", "ffc_version", "ffc_far_field", "ffc_sample_rows", "ffc_eval_block", "ffc_id",
@@ -71,7 +72,7 @@ class c_params(ctypes.Structure):
                 ("pool_rows", ctypes.c_int32), ("proj_dev", ctypes.c_void_p), ("mlp_dev", ctypes.c_void_p),
                 ("qr_big_min_s", ctypes.c_int32), ("qr_l2_budget_mb", ctypes.c_int32), ("qr_panel", ctypes.c_int32),
                 ("nested", ctypes.c_int32), ("eval_path", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("qr_defer", ctypes.c_int32)]
+                ("qr_defer", ctypes.c_int32), ("solve", ctypes.c_int32)]
 
 
 class c_tree_view(ctypes.Structure):
@@ -350,13 +351,14 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
                       s_max=2048, xi=1.0, seed=0, result: TreeResult | None = None, stream=None,
                       proposal: tuple | None = None, pool_rows=0, qr_big_min_s=0,
                       qr_l2_budget_mb=0, sampler: int | None = None, qr_panel=0, nested=False,
-                      eval_path=EVAL_DEFAULT, graphs=True, qr_defer=0) -> TreeResult:
+                      eval_path=EVAL_DEFAULT, graphs=True, qr_defer=0, solve=SOLVE_DEFAULT) -> TreeResult:
     """Compress every node at level >= min_level; ``proposal`` = (params, proj) selects the learned sampler,
     ``sampler`` one of SAMPLE_* otherwise (default uniform). ``qr_big_min_s``, ``qr_l2_budget_mb``, ``qr_panel``:
     the QR's launch shape and panel width (0 = the library's defaults; 1 = unblocked; see ``autotune``);
     ``eval_path``: one of EVAL_* for the mixed-precision Gaussian / polynomial blocks; ``graphs``: run each round
     as a captured CUDA graph (replayed when the round recurs) instead of direct launches; ``qr_defer``: the QR's
-    write-back depth (0 = the library's default, 1 = every step, 2..4 = the lazy form)."""
+    write-back depth (0 = the library's default, 1 = every step, 2..4 = the lazy form); ``solve``: SOLVE_* of the
+    mixed-precision triangular solve."""
     _dev(points_perm, "points_perm")
     N, d = points_perm.shape
     res = result if result is not None else TreeResult()
@@ -369,7 +371,7 @@ def ffc_compress_tree(points_perm, tree: DeviceTree, kernel: Kernel, tol=1e-6, p
     p = c_params(kernel.c_struct(), int(precision), int(min_level), int(s0), int(s_max), float(tol), float(xi),
                  ctypes.c_uint64(int(seed)), sampler, int(pool_rows), proj_p, mlp_p, int(qr_big_min_s),
                  int(qr_l2_budget_mb), int(qr_panel), 1 if nested else 0, int(eval_path), 0 if graphs else 1,
-                 int(qr_defer))
+                 int(qr_defer), int(solve))
     tr = tree.c_struct()
     _check(lib().ffc_compress_tree(_ptr(points_perm), _dtype_code(points_perm), N, d, ctypes.byref(tr),
                                    ctypes.byref(p), ctypes.byref(res.handle), _stream(stream)))
