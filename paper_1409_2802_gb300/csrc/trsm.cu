@@ -253,50 +253,57 @@ trsm_refine_kernel(const TrsmItem* __restrict__ items, int n_items) {
   }
   __syncthreads();
   solve_f32_block(Tf, R11f, r, nc, Rd, dinv);
-  // E = R12 - R11 T1, rows in 4 x 4 register tiles: the diagonal term in FP64, the rest exact products
-  // summed in double-float from the diagonal outwards
+  // E = R12 - R11 T1 in tasks of 4 rows x 2 columns: the diagonal term in FP64, the rest exact products
+  // summed in double-float from the diagonal outwards. A thread takes row groups g and G - 1 - g, so every
+  // thread sums about r terms (the triangle's rows are long at the top and short at the bottom).
   {
-    const int cg = 4 * (tid & 3);
-    for (int j0 = 4 * (tid >> 2); j0 < r; j0 += 4 * (int)(blockDim.x >> 2)) {
-      float hi[4][4], lo[4][4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = j0 + u;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          hi[u][v] = 0.0f;
-          lo[u][v] = 0.0f;
-          if (i < r && cg + v < nc) {
-            const double b = (double)A[i + (int64_t)it.skel_perm[r + c0 + cg + v] * it.lda];
-            const double s0 = fma(-R11[(int64_t)i * r + i], (double)Tf[i * TS_COLS + cg + v], b);
-            hi[u][v] = (float)s0;
-            lo[u][v] = (float)(s0 - (double)hi[u][v]);
-          }
-        }
-      }
-      const int64_t ldf = (r + 3) & ~3;
-      for (int k = j0 + 1; k < r; ++k) {
-        const float4 t4 = *reinterpret_cast<const float4*>(&Tf[k * TS_COLS + cg]);
-        const float t[4] = {t4.x, t4.y, t4.z, t4.w};
-        const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)k * ldf + j0));
-        const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+    const int G = (r + 3) >> 2;
+    const int cg = 2 * (tid & 7);
+    const int64_t ldf = (r + 3) & ~3;
+    for (int pg = tid >> 3; pg < (G + 1) >> 1; pg += (int)(blockDim.x >> 3)) {
+      for (int half = 0; half < 2; ++half) {
+        const int g = half == 0 ? pg : G - 1 - pg;
+        if (half == 1 && g == pg) break;   // the middle group of an odd count
+        const int j0 = 4 * g;
+        float hi[4][2], lo[4][2];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float a = (j0 + u < r && k > j0 + u) ? rv[u] : 0.0f;
+          const int i = j0 + u;
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const float p = a * t[v];
-            const float pe = fmaf(a, t[v], -p);   // a t = p + pe exactly
-            df_add(hi[u][v], lo[u][v], -p);
-            lo[u][v] -= pe;
+          for (int v = 0; v < 2; ++v) {
+            hi[u][v] = 0.0f;
+            lo[u][v] = 0.0f;
+            if (i < r && cg + v < nc) {
+              const double b = (double)A[i + (int64_t)it.skel_perm[r + c0 + cg + v] * it.lda];
+              const double s0 = fma(-R11[(int64_t)i * r + i], (double)Tf[i * TS_COLS + cg + v], b);
+              hi[u][v] = (float)s0;
+              lo[u][v] = (float)(s0 - (double)hi[u][v]);
+            }
           }
         }
+        for (int k = j0 + 1; k < r; ++k) {
+          const float2 t2 = *reinterpret_cast<const float2*>(&Tf[k * TS_COLS + cg]);
+          const float t[2] = {t2.x, t2.y};
+          const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)k * ldf + j0));
+          const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float a = (j0 + u < r && k > j0 + u) ? rv[u] : 0.0f;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              const float p = a * t[v];
+              const float pe = fmaf(a, t[v], -p);   // a t = p + pe exactly
+              df_add(hi[u][v], lo[u][v], -p);
+              lo[u][v] -= pe;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u < r)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) Ef[(j0 + u) * TS_COLS + cg + v] = hi[u][v] + lo[u][v];
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (j0 + u < r)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) Ef[(j0 + u) * TS_COLS + cg + v] = hi[u][v] + lo[u][v];
     }
   }
   __syncthreads();
