@@ -552,8 +552,12 @@ ffc_status ffc_mlp_forward(const float* params_dev, const float* feats_dev, int6
  * domain 2) (Philox layout as in ffc_sample_rows). The min(s, P) largest keys
  * win (ties: lower pool position) and are written in decreasing key order,
  * so a size-s draw is a prefix of the size-2s draw. Keys are formed in FP64
- * from the FP32 logits. min(s, P) <= FFC_MAX_DRAW; any P.
- * rows_dev: capacity min(s, P). Asynchronous.
+ * from the FP32 logits; pools above 16,384 rows are first ranked by FP32
+ * keys within a proven relative error of 2^-18 of the FP64 ones, and only
+ * the rows that can be among the selection get their FP64 key, so the result
+ * is the FP64 keys' selection. min(s, P) <= FFC_MAX_DRAW; any P.
+ * rows_dev: capacity min(s, P). Allocates P + 256 words of stream-ordered
+ * device memory for the call. Asynchronous.
  */
 ffc_status ffc_sample_weighted(const int64_t* pool_dev, const float* logits_dev, int64_t P, int64_t s,
                                uint64_t seed, uint64_t stream_id, int64_t* rows_dev, void* stream);

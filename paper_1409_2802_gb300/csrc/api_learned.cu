@@ -63,14 +63,17 @@ ffc_status ffc_sample_weighted(const int64_t* pool_dev, const float* logits_dev,
   if (P == 0 || s == 0) return FFC_OK;
   FFC_REQUIRE(pool_dev && logits_dev && rows_dev, "ffc_sample_weighted: null pointer");
   cudaStream_t st = as_stream(stream);
-  SelectItem* item = nullptr;
-  FFC_CUDA(cudaMallocAsync((void**)&item, sizeof(SelectItem), st));
+  // one allocation: the item, then a key buffer of P words (used by pools above the shared-memory sort)
+  const size_t kbeg = (sizeof(SelectItem) + 255) & ~(size_t)255;
+  unsigned char* buf = nullptr;
+  FFC_CUDA(cudaMallocAsync((void**)&buf, kbeg + (size_t)P * sizeof(uint64_t), st));
+  SelectItem* item = reinterpret_cast<SelectItem*>(buf);
   SelectItem h{};
   h.pool = pool_dev; h.count = nullptr; h.P = P; h.logits = logits_dev; h.s = s; h.stream_id = stream_id;
-  h.rows_out = rows_dev; h.s_out = nullptr; h.keys = nullptr;
+  h.rows_out = rows_dev; h.s_out = nullptr; h.keys = reinterpret_cast<uint64_t*>(buf + kbeg);
   FFC_CUDA(cudaMemcpyAsync(item, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   ffc_status rc = launch_select(item, 1, std::min(P, s), seed, st);
-  cudaFreeAsync(item, st);
+  cudaFreeAsync(buf, st);
   return rc;
 }
 
@@ -96,8 +99,8 @@ ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int6
   const bool whole = pool_rows == 0;
   const int64_t cap = whole ? M : std::min(pool_rows, M);
   Scratch sc;
-  const size_t bytes = 10 * 256 + sizeof(SampleItem) + sizeof(FeatItem) + sizeof(SelectItem) +
-                       (size_t)cap * (sizeof(int64_t) + FFC_N_FEATURES * sizeof(float) + sizeof(float)) +
+  const size_t bytes = 12 * 256 + sizeof(SampleItem) + sizeof(FeatItem) + sizeof(SelectItem) +
+                       (size_t)cap * (2 * sizeof(int64_t) + FFC_N_FEATURES * sizeof(float) + sizeof(float)) +
                        (size_t)M * sizeof(int32_t) + 64;
   FFC_CUDA(cudaMallocAsync((void**)&sc.base, bytes, st));
   SampleItem* sitem = sc.take<SampleItem>(1);
@@ -111,6 +114,7 @@ ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int6
   int64_t* s_sel = sc.take<int64_t>(1);
   int32_t* status = sc.take<int32_t>(1);
   int32_t* scratch = sc.take<int32_t>((size_t)M);
+  uint64_t* skeys = sc.take<uint64_t>((size_t)cap);
 
   const double thr = xi * radius;
   FeatItem hf;
@@ -118,7 +122,7 @@ ffc_status ffc_propose_rows(ffc_kernel k, const void* Y_dev, int32_t dtype, int6
   hf.radius = nullptr; hf.radius_host = radius;
   SelectItem hp{};
   hp.pool = pool; hp.count = p_count; hp.P = cap; hp.logits = logits; hp.s = s; hp.stream_id = stream_id;
-  hp.rows_out = rows_dev; hp.s_out = s_sel; hp.keys = nullptr;
+  hp.rows_out = rows_dev; hp.s_out = s_sel; hp.keys = skeys;
   FFC_CUDA(cudaMemcpyAsync(fitem, &hf, sizeof(hf), cudaMemcpyHostToDevice, st));
   FFC_CUDA(cudaMemcpyAsync(pitem, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
   ffc_status rc;

@@ -279,19 +279,28 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_kernel(const float* _
 // h1 to about 2^-22 relative (the FP16 weights are exact in both products):
 // the logits are those of FP32 activations, not of FP16-rounded ones.
 
-constexpr int TC_ROWS = 64;        // rows per tile: 4 row groups of 16, each split over two warps by units
-constexpr int HS = NH + 8;         // FP16 row stride in shared memory (272 B: ldmatrix rows hit distinct banks)
+// Layout: one warp per tile of 16 rows, with no block barrier after the weights are staged.
+// The first layer is computed straight into the A fragments of m16n8k16: lane (g, q) =
+// (lane / 4, lane % 4) owns rows g and g + 8 and, in k-slice ks, units 16 ks + 2q + {0, 1, 8, 9}.
+// Each h1 value is computed once, by the lane whose fragment holds it, so h1 never goes through
+// shared memory. The warp's 16 n-tiles of 8 units (64 FP32 accumulators per lane) cover all 128
+// units of layer 2. Every value is formed with the same operations in the same order as a
+// row-at-a-time evaluation of the network:
+// * z1 = b1 + w1[0] x[0] + ... + w1[11] x[11] (one FMA chain);
+// * per output unit, k-slices in increasing order, the lo plane's product before the hi plane's;
+// * the logit = (sum over units 0..63 + sum over units 64..127) + b3, each half summed over the
+//   n-tiles in order and then across the 4 lanes of a row.
+constexpr int TC_WARPS = 8;
+constexpr int TC_THREADS = 32 * TC_WARPS;
+constexpr int TC_WROWS = 16;       // rows per warp tile
+constexpr int HS = NH + 8;         // FP16 row stride of W2 in shared memory (272 B: ldmatrix rows hit distinct banks)
 
 struct TcSmem {
-  alignas(16) __half W2[NH * HS];        // W2[j][k]: the B operand (k x n, "col")
-  alignas(16) __half H1[TC_ROWS * HS];   // hi plane of h1[r][k]: the A operand (row-major)
-  alignas(16) __half H1L[TC_ROWS * HS];  // lo plane
-  alignas(16) float W1T[NF * NH];
-  alignas(16) float X[TC_ROWS * NF];
+  alignas(16) __half W2[NH * HS];   // W2[j][k]: the B operand (k x n, "col")
+  alignas(16) float W1[NH * NF];    // W1[j][k], FP16-rounded, row-major (48 B per unit)
   alignas(16) float b1[NH];
   alignas(16) float b2[NH];
   alignas(16) float w3[NH];
-  alignas(16) float part[2][TC_ROWS];    // partial logits over units [0, 64) and [64, 128)
   float b3;
 };
 
@@ -309,14 +318,40 @@ __device__ __forceinline__ void mma_16816(float (&d)[4], unsigned a0, unsigned a
                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float* __restrict__ P,
-                                                                     const float* __restrict__ F, int64_t R,
-                                                                     float* __restrict__ logits) {
+// h1 of unit j for two rows (x0, x1): GELU(b1 + w1 . x) in FP32, returned as hi = fp16(h),
+// lo = fp16(h - hi)
+__device__ __forceinline__ void h1_pair(const float* __restrict__ w1row, float b1j, const float (&x0)[NF],
+                                        const float (&x1)[NF], __half& h0, __half& l0, __half& h1, __half& l1) {
+  const float4* w4 = reinterpret_cast<const float4*>(w1row);
+  float za = b1j, zb = b1j;
+#pragma unroll
+  for (int q = 0; q < NF / 4; ++q) {
+    const float4 w = w4[q];
+    za = fmaf(w.x, x0[4 * q], za); zb = fmaf(w.x, x1[4 * q], zb);
+    za = fmaf(w.y, x0[4 * q + 1], za); zb = fmaf(w.y, x1[4 * q + 1], zb);
+    za = fmaf(w.z, x0[4 * q + 2], za); zb = fmaf(w.z, x1[4 * q + 2], zb);
+    za = fmaf(w.w, x0[4 * q + 3], za); zb = fmaf(w.w, x1[4 * q + 3], zb);
+  }
+  const float ga = gelu_inf(za), gb = gelu_inf(zb);
+  h0 = __float2half_rn(ga);
+  l0 = __float2half_rn(ga - __half2float(h0));
+  h1 = __float2half_rn(gb);
+  l1 = __float2half_rn(gb - __half2float(h1));
+}
+
+__device__ __forceinline__ unsigned pack_h2(__half lo_col, __half hi_col) {
+  const __half2 v = __halves2half2(lo_col, hi_col);   // .x (low 16 bits): the lower column
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) mlp_forward_tc_kernel(const float* __restrict__ P,
+                                                                        const float* __restrict__ F, int64_t R,
+                                                                        float* __restrict__ logits) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < NH * NH; e += blockDim.x) S.W2[(e / NH) * HS + (e % NH)] = __float2half_rn(P[OFF_W2 + e]);
-  for (int e = tid; e < NH * NF; e += blockDim.x) S.W1T[(e % NF) * NH + (e / NF)] = half_round(P[OFF_W1 + e]);
+  for (int e = tid; e < NH * NF; e += blockDim.x) S.W1[e] = half_round(P[OFF_W1 + e]);
   for (int j = tid; j < NH; j += blockDim.x) {
     S.b1[j] = half_round(P[OFF_B1 + j]);
     S.b2[j] = half_round(P[OFF_B2 + j]);
@@ -324,86 +359,72 @@ __global__ void __launch_bounds__(NET_THREADS) mlp_forward_tc_kernel(const float
   }
   if (tid == 0) S.b3 = half_round(P[OFF_B3]);
   __syncthreads();
-  // layer 1: thread owns unit j for rows r0, r0 + 2, ...
-  const int j = tid & (NH - 1), r_first = tid >> 7;
-  float w1[NF];
+  const int g = lane >> 2, q = lane & 3;
+  const int64_t tiles = (R + TC_WROWS - 1) / TC_WROWS;
+  const int64_t wstride = (int64_t)gridDim.x * TC_WARPS;
+  for (int64_t t = (int64_t)blockIdx.x * TC_WARPS + warp; t < tiles; t += wstride) {
+    const int64_t ra = t * TC_WROWS + g, rb = ra + 8;
+    float xa[NF], xb[NF];
 #pragma unroll
-  for (int kk = 0; kk < NF; ++kk) w1[kk] = S.W1T[kk * NH + j];
-  const float b1j = S.b1[j];
-  // layer 2: warp w takes rows 16 (w & 3) .. + 15 and units 64 (w >> 2) .. + 63 (8 n-tiles of 8)
-  const int mrow = 16 * (warp & 3), nhalf = warp >> 2, nbase = 64 * nhalf;
-  const int64_t tiles = (R + TC_ROWS - 1) / TC_ROWS;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t row0 = t * TC_ROWS;
-    __syncthreads();
-    for (int e = tid; e < TC_ROWS * NF; e += blockDim.x) {
-      const int64_t r = row0 + e / NF;
-      S.X[e] = r < R ? F[row0 * NF + e] : 0.0f;
+    for (int k = 0; k < NF; ++k) {
+      xa[k] = ra < R ? __ldg(F + ra * NF + k) : 0.0f;
+      xb[k] = rb < R ? __ldg(F + rb * NF + k) : 0.0f;
     }
-    __syncthreads();
-    // two rows per pass (rows r and r + 2): 16-byte loads of the feature rows and two
-    // independent GELUs in flight; the sums keep the order b1 + w1[0] x[0] + ... + w1[11] x[11]
-    for (int r = r_first; r < TC_ROWS; r += 4) {
-      const float4* xa = reinterpret_cast<const float4*>(&S.X[r * NF]);
-      const float4* xb = reinterpret_cast<const float4*>(&S.X[(r + 2) * NF]);
-      float za = b1j, zb = b1j;
+    float acc[16][4];
 #pragma unroll
-      for (int q = 0; q < NF / 4; ++q) {
-        const float4 a = xa[q], b = xb[q];
-        za = fmaf(w1[4 * q], a.x, za); zb = fmaf(w1[4 * q], b.x, zb);
-        za = fmaf(w1[4 * q + 1], a.y, za); zb = fmaf(w1[4 * q + 1], b.y, zb);
-        za = fmaf(w1[4 * q + 2], a.z, za); zb = fmaf(w1[4 * q + 2], b.z, zb);
-        za = fmaf(w1[4 * q + 3], a.w, za); zb = fmaf(w1[4 * q + 3], b.w, zb);
-      }
-      const float ga = gelu_inf(za), gb = gelu_inf(zb);
-      const __half ha = __float2half_rn(ga), hb = __float2half_rn(gb);
-      S.H1[r * HS + j] = ha;
-      S.H1[(r + 2) * HS + j] = hb;
-      S.H1L[r * HS + j] = __float2half_rn(ga - __half2float(ha));
-      S.H1L[(r + 2) * HS + j] = __float2half_rn(gb - __half2float(hb));
-    }
-    __syncthreads();
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) { acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f; }
-    const int q = lane >> 3;   // ldmatrix: the matrix this lane addresses a row of
-#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) { acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f; }
+#pragma unroll 1
     for (int ks = 0; ks < NH / 16; ++ks) {
-      const int aoff = (mrow + (lane & 15)) * HS + ks * 16 + (lane >> 4) * 8;
-      unsigned a0, a1, a2, a3, l0, l1, l2, l3;
-      ldsm_x4(&S.H1[aoff], a0, a1, a2, a3);
-      ldsm_x4(&S.H1L[aoff], l0, l1, l2, l3);
+      // this lane's A fragments of k-slice ks: units u0, u0 + 1 (a0: row g, a1: row g + 8) and
+      // u0 + 8, u0 + 9 (a2, a3)
+      const int u0 = 16 * ks + 2 * q;
+      __half h[4][2], l[4][2];   // [unit][row]
 #pragma unroll
-      for (int np = 0; np < 4; ++np) {
+      for (int c = 0; c < 4; ++c) {
+        const int u = u0 + (c & 1) + 8 * (c >> 1);
+        h1_pair(&S.W1[u * NF], S.b1[u], xa, xb, h[c][0], l[c][0], h[c][1], l[c][1]);
+      }
+      const unsigned a0 = pack_h2(h[0][0], h[1][0]), a1 = pack_h2(h[0][1], h[1][1]);
+      const unsigned a2 = pack_h2(h[2][0], h[3][0]), a3 = pack_h2(h[2][1], h[3][1]);
+      const unsigned l0 = pack_h2(l[0][0], l[1][0]), l1 = pack_h2(l[0][1], l[1][1]);
+      const unsigned l2 = pack_h2(l[2][0], l[3][0]), l3 = pack_h2(l[2][1], l[3][1]);
+      const int qm = lane >> 3;   // ldmatrix: the matrix this lane addresses a row of
+#pragma unroll
+      for (int np = 0; np < 8; ++np) {
         unsigned b0, b1, b2, b3;
-        ldsm_x4(&S.W2[(nbase + np * 16 + (q >> 1) * 8 + (lane & 7)) * HS + ks * 16 + (q & 1) * 8], b0, b1, b2, b3);
+        ldsm_x4(&S.W2[(np * 16 + (qm >> 1) * 8 + (lane & 7)) * HS + ks * 16 + (qm & 1) * 8], b0, b1, b2, b3);
         mma_16816(acc[2 * np], l0, l1, l2, l3, b0, b1);
         mma_16816(acc[2 * np + 1], l0, l1, l2, l3, b2, b3);
         mma_16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
         mma_16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
       }
     }
-    // epilogue: h2 = GELU(z2 + b2), the warp's share of w3 . h2; lane holds rows lane/4 and
-    // lane/4 + 8 of its row group, columns nbase + 8 nt + 2 (lane % 4) + {0, 1}
-    float po0 = 0.0f, po1 = 0.0f;
+    // epilogue: h2 = GELU(z2 + b2) and w3 . h2, per half of the units; lane holds rows g and g + 8,
+    // columns 8 nt + 2q + {0, 1}
+    float pa[2], pb[2];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int c = nbase + nt * 8 + 2 * (lane & 3);
-      po0 = fmaf(S.w3[c], gelu_inf(acc[nt][0] + S.b2[c]), po0);
-      po0 = fmaf(S.w3[c + 1], gelu_inf(acc[nt][1] + S.b2[c + 1]), po0);
-      po1 = fmaf(S.w3[c], gelu_inf(acc[nt][2] + S.b2[c]), po1);
-      po1 = fmaf(S.w3[c + 1], gelu_inf(acc[nt][3] + S.b2[c + 1]), po1);
+    for (int hf = 0; hf < 2; ++hf) {
+      float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int c = 64 * hf + nt * 8 + 2 * q;
+        const float* ac = acc[8 * hf + nt];
+        sa = fmaf(S.w3[c], gelu_inf(ac[0] + S.b2[c]), sa);
+        sa = fmaf(S.w3[c + 1], gelu_inf(ac[1] + S.b2[c + 1]), sa);
+        sb = fmaf(S.w3[c], gelu_inf(ac[2] + S.b2[c]), sb);
+        sb = fmaf(S.w3[c + 1], gelu_inf(ac[3] + S.b2[c + 1]), sb);
+      }
+      sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+      sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+      sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+      pa[hf] = sa;
+      pb[hf] = sb;
     }
-    po0 += __shfl_xor_sync(0xffffffffu, po0, 1);
-    po0 += __shfl_xor_sync(0xffffffffu, po0, 2);
-    po1 += __shfl_xor_sync(0xffffffffu, po1, 1);
-    po1 += __shfl_xor_sync(0xffffffffu, po1, 2);
-    if ((lane & 3) == 0) {
-      S.part[nhalf][mrow + (lane >> 2)] = po0;
-      S.part[nhalf][mrow + (lane >> 2) + 8] = po1;
+    if (q == 0) {
+      if (ra < R) logits[ra] = (pa[0] + pa[1]) + S.b3;
+      if (rb < R) logits[rb] = (pb[0] + pb[1]) + S.b3;
     }
-    __syncthreads();
-    if (tid < TC_ROWS && row0 + tid < R) logits[row0 + tid] = (S.part[0][tid] + S.part[1][tid]) + S.b3;
   }
 }
 
@@ -684,16 +705,130 @@ __device__ __forceinline__ uint64_t es_sort_key(float logit, double mx, double m
 
 // One CTA per pool: the min(s, P) pool rows with the largest keys, in key
 // order, ties to the lower pool position. Pools of at most SEL_CAP rows are
-// sorted whole in shared memory. Larger pools: the sort keys of the whole
-// pool are computed once (kept in it.keys when given, else recomputed per
-// pass); a radix select on their bit patterns (SEL_BITS per level, a
-// histogram in shared memory) narrows a key prefix until the keys at or
-// below it hold the n_keep best and number at most SEL_CAP; those are
+// sorted whole in shared memory. Larger pools with a key buffer (it.keys)
+// take the FP32 pre-selection below: exact keys only for its candidates.
+// Otherwise (no buffer, or more than SEL_CAP candidates) the exact sort keys
+// are recomputed per pass; a radix select on their bit patterns (SEL_BITS per
+// level, a histogram in shared memory) narrows a key prefix until the keys at
+// or below it hold the n_keep best and number at most SEL_CAP; those are
 // gathered and sorted. Only exact ties of more than SEL_CAP keys (not met
 // with distinct draws) take the ordered tie path.
 constexpr int SEL_BITS = 12, SEL_BINS = 1 << SEL_BITS;
 
 size_t select_smem_bytes() { return (size_t)SEL_CAP * (sizeof(uint64_t) + sizeof(uint32_t)) + SEL_BINS * sizeof(int); }
+
+// ---- FP32 pre-selection of large pools with stored weights
+//
+// The n_keep smallest FP64 sort keys k_i are found without computing k_i for every row: an FP32
+// approximation k~_i with |k~_i - k_i| <= DELTA k_i (DELTA = 2^-18) ranks the rows, and the exact
+// keys are computed only for the rows with k~_i <= T, where T bounds t~ (1 + DELTA) / (1 - DELTA)
+// from above and t~ is the n_keep-th smallest k~. That set holds every row of the exact selection:
+// the n_keep rows with k~ <= t~ have exact keys <= t~ / (1 - DELTA), so the exact n_keep-th key t
+// is at most that, and a selected row's k~ <= (1 + DELTA) k <= (1 + DELTA) t <= T. Sorting the
+// set by (exact key, position) then gives the exact selection.
+//
+// Error of k~ = L~ / w~', first order in u = 2^-24 (IEEE FP32 division and conversions; logf and
+// log1pf within 1 ulp, the CUDA maximum-error bound without fast-math):
+// * u_d (the FP64 uniform of the exact key) is rebuilt from the integer draw as a correctly rounded
+//   FP32 value (relative error u). For u_d < 1/2, L~ = -logf(u~): the conversion moves ln u_d by at
+//   most u, and |ln u_d| >= ln 2, so 1.443u, plus 2u for logf. For u_d >= 1/2, L~ = -log1pf(-v~)
+//   with v~ the FP32 value of 1 - u_d (exact as an integer): d(-ln(1-v))/dv * v / (-ln(1-v)) <= 1.443
+//   on [0, 1/2], so again 1.443u + 2u.
+// * w~' = fmaf(0.9f, w~ / m~, 0.1f) with w~, m~ the FP32 values of w and the mean: the ratio 3u,
+//   0.9f 1u, 0.1f 1u, the final rounding 1u: at most 5u relative (both terms are positive; a w
+//   below the FP32 range only drops a term below 1e-37 of w' >= 0.1).
+// * the division: 1u. In all 9.5u ~ 5.7e-7 relative, below DELTA = 64u ~ 3.8e-6.
+constexpr float SEL_DELTA4 = 0x1.0p-16f;   // 4 DELTA: T = U (1 + 4 DELTA) > U (1 + DELTA) / (1 - DELTA)
+
+__device__ __forceinline__ float es_key_f32(double w, float mean_f, uint64_t seed, uint64_t stream_id, int64_t i) {
+  const uint64_t draw = philox_draw(seed, stream_id, DOMAIN_WEIGHTED_KEYS, (uint64_t)i);
+  const uint64_t m = draw >> 11;   // the exact key takes u_d = fl(m + 1/2) 2^-53
+  float L;
+  if (m < (1ull << 52)) {          // m + 1/2 is exact: u_d = (2m + 1) 2^-54 < 1/2
+    L = -logf(__ull2float_rn(2 * m + 1) * 0x1.0p-54f);
+  } else {                         // m + 1/2 rounds to the even neighbour; 1 - u_d = (2^53 - that) 2^-53
+    const uint64_t me = m + (m & 1ull);
+    L = -log1pf(-(__ull2float_rn((1ull << 53) - me) * 0x1.0p-53f));
+  }
+  const float wp = fmaf(0.9f, (float)w / mean_f, 0.1f);
+  return L / wp;
+}
+
+// The exact selection's candidates, gathered into pos[0, m) with their exact keys in key[0, m);
+// false (and nothing usable in it.keys) when more than SEL_CAP rows pass the threshold.
+__device__ bool select_prefiltered(const SelectItem& it, int64_t P, int64_t n_keep, double dmx, double mean,
+                                   uint64_t seed, uint64_t* key, uint32_t* pos, int* hist, int& m_out) {
+  __shared__ int f_bin, f_fill;
+  __shared__ long long f_lt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float mean_f = (float)mean;
+  uint64_t* kb = it.keys;   // holds w_i (FP64 bits); overwritten with the bits of k~_i
+  unsigned pv = 0;
+  long long c_lt = 0;
+  for (int level = 0; level < 2; ++level) {   // key bits [31, 20), then [20, 8)
+    const int sh = 20 - 12 * level;
+    for (int b = tid; b < SEL_BINS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < P; i += blockDim.x) {
+      unsigned k;
+      if (level == 0) {
+        k = __float_as_uint(es_key_f32(__longlong_as_double((long long)kb[i]), mean_f, seed, it.stream_id, i));
+        kb[i] = k;
+      } else {
+        k = (unsigned)kb[i];
+      }
+      if (level == 0 || (k >> 20) == pv) atomicAdd(&hist[(k >> sh) & (SEL_BINS - 1)], 1);
+    }
+    __syncthreads();
+    if (warp == 0) {   // the bin where the count of smaller keys first reaches n_keep
+      constexpr int per = SEL_BINS / 32;
+      const int b0 = lane * per;
+      long long own = 0;
+      for (int b = b0; b < b0 + per; ++b) own += hist[b];
+      long long inc = own;
+      for (int off = 1; off < 32; off <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += v;
+      }
+      const long long excl = inc - own;
+      if (c_lt + excl < n_keep && c_lt + inc >= n_keep) {
+        long long run = c_lt + excl;
+        for (int b = b0; b < b0 + per; ++b) {
+          if (run + hist[b] >= n_keep) {
+            f_bin = b;
+            f_lt = run;
+            break;
+          }
+          run += hist[b];
+        }
+      }
+    }
+    __syncthreads();
+    pv = (pv << 12) | (unsigned)f_bin;
+    c_lt = f_lt;
+    __syncthreads();
+  }
+  // t~ lies in the bin of the 24-bit prefix pv, below U; keys are below 400, so pv + 1 does not carry out
+  const float U = __uint_as_float((pv + 1u) << 8);
+  const unsigned Tb = __float_as_uint(U * (1.0f + SEL_DELTA4));
+  if (tid == 0) f_fill = 0;
+  __syncthreads();
+  for (int64_t i = tid; i < P; i += blockDim.x) {
+    if ((unsigned)kb[i] <= Tb) {
+      const int slot = atomicAdd(&f_fill, 1);
+      if (slot < SEL_CAP) pos[slot] = (uint32_t)i;
+    }
+  }
+  __syncthreads();
+  const int m = f_fill;
+  if (m > SEL_CAP) return false;
+  for (int e = tid; e < m; e += blockDim.x)
+    key[e] = es_sort_key(it.logits[pos[e]], dmx, mean, seed, it.stream_id, (int64_t)pos[e]);
+  __syncthreads();
+  m_out = m;
+  return true;
+}
+
 
 // The selection with the ascending sort keys given (it.given): the n_keep smallest keys, in key order,
 // ties to the lower pool position (radix narrowing and a shared-memory sort as in select_kernel).
@@ -842,33 +977,29 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
   const double dmx = (double)mx;
   auto key_of = [&](int64_t i) -> uint64_t { return es_sort_key(it.logits[i], dmx, mean, seed, it.stream_id, i); };
   int m = 0;
-  if (P <= SEL_CAP) {
+  // large pools with a key buffer: FP32 pre-selection, exact keys for the candidates only; when it
+  // overflows, the exact radix selection below recomputes every key (the buffer no longer holds w)
+  const bool pre = keep_w && select_prefiltered(it, P, n_keep, dmx, mean, seed, key, pos, hist, m);
+  if (pre) {
+  } else if (P <= SEL_CAP) {
     m = (int)P;
     for (int e = tid; e < m; e += blockDim.x) {
       key[e] = key_of(e);
       pos[e] = (uint32_t)e;
     }
   } else {
-    const bool stored = it.keys != nullptr;
     uint64_t pv = 0;        // the top pl bits of the selected prefix
     int pl = 0;
     long long c_lt = 0;     // keys below the prefix range
     long long c_in = P;     // keys inside it
-    for (int level = 0; pl < 64 && c_lt + c_in > SEL_CAP; ++level) {
+    while (pl < 64 && c_lt + c_in > SEL_CAP) {
       const int nb = min(SEL_BITS, 64 - pl);
       const int sh = 64 - pl - nb;
       const int bins = 1 << nb;
       for (int b = tid; b < bins; b += blockDim.x) hist[b] = 0;
       __syncthreads();
       for (int64_t i = tid; i < P; i += blockDim.x) {
-        uint64_t k;
-        if (level == 0) {
-          k = stored ? es_sort_key_w(__longlong_as_double((long long)it.keys[i]), mean, seed, it.stream_id, i)
-                     : key_of(i);
-          if (stored) it.keys[i] = k;
-        } else {
-          k = stored ? it.keys[i] : key_of(i);
-        }
+        const uint64_t k = key_of(i);
         if (pl == 0 || (k >> (64 - pl)) == pv) atomicAdd(&hist[(int)((k >> sh) & (uint64_t)(bins - 1))], 1);
       }
       __syncthreads();
@@ -909,7 +1040,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
     __syncthreads();
     const bool ties = c_lt + c_in > SEL_CAP;   // pl == 64: more than SEL_CAP keys equal pv
     for (int64_t i = tid; i < P; i += blockDim.x) {
-      const uint64_t k = stored ? it.keys[i] : key_of(i);
+      const uint64_t k = key_of(i);
       const bool take = ties ? k < pv : (k >> (64 - pl)) <= pv;
       if (take) {
         const int slot = atomicAdd(&s_fill, 1);
@@ -923,7 +1054,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelectItem* i
       int fill = s_fill;
       for (int64_t base = 0; base < P && fill < n_keep; base += 32) {
         const int64_t i = base + lane;
-        const bool eq = i < P && (stored ? it.keys[i] : key_of(i)) == pv;
+        const bool eq = i < P && key_of(i) == pv;
         const unsigned bal = __ballot_sync(0xffffffffu, eq);
         const int rank = __popc(bal & ((1u << lane) - 1u));
         if (eq && fill + rank < n_keep) {
@@ -1001,9 +1132,9 @@ ffc_status launch_mlp_forward(const float* params, const float* feats, int64_t R
   if (R <= 0) return FFC_OK;
   const size_t smem = sizeof(TcSmem);
   FFC_CUDA(cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t tiles = (R + TC_ROWS - 1) / TC_ROWS;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 2));
-  mlp_forward_tc_kernel<<<grid, NET_THREADS, smem, st>>>(params, feats, R, logits);
+  const int64_t ctas = (R + TC_WROWS * TC_WARPS - 1) / (TC_WROWS * TC_WARPS);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)sm_count() * 2));
+  mlp_forward_tc_kernel<<<grid, TC_THREADS, smem, st>>>(params, feats, R, logits);
   FFC_CUDA(cudaGetLastError());
   return FFC_OK;
 }

@@ -163,6 +163,38 @@ def test_weighted_draw_matches_oracle(ffc, P, s):
         assert np.min(np.abs(np.diff(srt[:min(s, P) + 1]))) < 1e-14 * np.abs(srt[0]), "selection differs"
 
 
+def test_weighted_draw_with_clustered_keys_is_the_exact_selection(ffc):
+    """Logits that put most keys ln(u_i) / w'_i within about 1e-7 of one value: the FP32 pre-selection's
+    window (about 5e-5 relative around the cut) then holds far more rows than the shared-memory sort, so
+    the draw takes the exact radix selection over FP64 keys. It must be the oracle's selection, and in
+    the oracle's key order, wherever the FP64 keys differ by more than their rounding (1e-15)."""
+    from oracle.philox import DOMAIN_WEIGHTED_KEYS, draws, to_unit_double
+    P, s, seed, stream_id = 40000, 8192, 5, 17
+    L = -np.log(to_unit_double(draws(seed, stream_id, DOMAIN_WEIGHTED_KEYS, 0, P)))
+    # w'_i = 0.9 r_i + 0.1 with r_i = w_i / mean(w); r_i = (L_i / c - 0.1) / 0.9 makes key_i = -c, and
+    # mean(r) = 1 fixes c (bisection; rows with L_i < 0.1 c take r = 1e-3 and rank above the cluster)
+    def mean_r(c):
+        return np.mean(np.maximum((L / c - 0.1) / 0.9, 1e-3))
+    lo_c, hi_c = 0.25 * L.mean(), 4.0 * L.mean()
+    for _ in range(100):
+        mid = 0.5 * (lo_c + hi_c)
+        lo_c, hi_c = (mid, hi_c) if mean_r(mid) > 1.0 else (lo_c, mid)
+    r = np.maximum((L / lo_c - 0.1) / 0.9, 1e-3)
+    logits = np.log(r).astype(np.float32)
+    pool = np.arange(P, dtype=np.int64) * 3 + 1
+    rows_o, keys = oprop.weighted_select(pool, logits.astype(np.float64), s, seed, stream_id)
+    cut = np.sort(keys)[::-1][s - 1]
+    assert np.sum(np.abs(keys - cut) <= 5e-5 * abs(cut)) > 16384   # the window overflows the sort
+    rows_g = ffc.ffc_sample_weighted(_t(pool), _t(logits), s, seed, stream_id).cpu().numpy()
+    assert rows_g.size == s and np.unique(rows_g).size == s
+    kg = keys[(rows_g - 1) // 3]
+    tol = 1e-15 * np.abs(keys).max()
+    assert np.all(np.diff(kg) <= tol), "not in decreasing key order"
+    rest = np.setdiff1d(np.arange(P), (rows_g - 1) // 3)
+    assert np.max(keys[rest]) <= kg.min() + tol, "a better row was left out"
+    print(f"identical to the oracle: {np.array_equal(rows_g, rows_o)}")
+
+
 @pytest.mark.parametrize("pool_rows", [0, 3000])
 def test_proposal_is_a_valid_draw_from_the_oracle_pool(ffc, pool_rows):
     Y, x_c, rho = _node(seed=2, N=8192)
