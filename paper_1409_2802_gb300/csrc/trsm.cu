@@ -52,6 +52,11 @@ finalize_kernel(const TrsmItem* __restrict__ items) {
     // FP32 copy, column-major with the leading dimension r rounded up to 4 (exact off the diagonal)
     if (it.R11f) it.R11f[(int64_t)kk * ((r + 3) & ~3) + i] = (float)v;
   }
+  // zeros in the copy's padding rows r .. ld - 1 (read by the residual's 16-byte loads)
+  if (it.R11f) {
+    const int ldf = (r + 3) & ~3, pad = ldf - r;
+    for (int e = threadIdx.x; e < r * pad; e += blockDim.x) it.R11f[(int64_t)(e / pad) * ldf + r + e % pad] = 0.0f;
+  }
 }
 
 // -------- T = R11^-1 R12 (FP64) -----------------------------------------------
@@ -170,6 +175,14 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
   hi = t;
 }
 
+// (hi, lo) -= a t, with a t = p + pe exactly (fmaf)
+__device__ __forceinline__ void residual_term(float& hi, float& lo, float a, float t) {
+  const float p = a * t;
+  const float pe = fmaf(a, t, -p);
+  df_add(hi, lo, -p);
+  lo -= pe;
+}
+
 // Blocked back-substitution of X (r x nc, shared memory, row stride TS_COLS) with the FP32 copy of R11
 // (column-major, leading dimension ldf = r rounded up to 4: exact off the diagonal, beta rounded on it);
 // Rd, dinv: shared scratch of the diagonal block.
@@ -205,18 +218,22 @@ __device__ void solve_f32_block(float* X, const float* __restrict__ R11, int r, 
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = j0 + u < i0 ? X[(j0 + u) * TS_COLS + cg + v] : 0.0f;
+        // rows j0 .. j0 + 3 of column i0 + ii: one 16-byte load; only a group that reaches past i0 (r not
+        // a multiple of 4) masks the rows of the diagonal block it reads
+        const bool full = j0 + 4 <= i0;
         for (int ii = 0; ii < nb; ++ii) {
           const float4 t4 = *reinterpret_cast<const float4*>(&X[(i0 + ii) * TS_COLS + cg]);
           const float t[4] = {t4.x, t4.y, t4.z, t4.w};
-          // rows j0 .. j0 + 3 of column i0 + ii: one 16-byte load (rows past i0 are read and not used)
           const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11 + (int64_t)(i0 + ii) * ldf + j0));
-          const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+          float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+          if (!full) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float rr = j0 + u < i0 ? rv[u] : 0.0f;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(-rr, t[v], acc[u][v]);
+            for (int u = 0; u < 4; ++u) rv[u] = j0 + u < i0 ? rv[u] : 0.0f;
           }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(-rv[u], t[v], acc[u][v]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -281,21 +298,30 @@ trsm_refine_kernel(const TrsmItem* __restrict__ items, int n_items) {
             }
           }
         }
-        for (int k = j0 + 1; k < r; ++k) {
+        // k <= j0 + 3 meets the group's diagonal (in s0) and the zeros below it: masked. Past it every
+        // entry of rows j0 .. j0 + 3 is above the diagonal or a zero (lower part, padding rows), and the
+        // rows >= r are never stored
+        const int kp = min(j0 + 4, r);
+        for (int k = j0 + 1; k < kp; ++k) {
           const float2 t2 = *reinterpret_cast<const float2*>(&Tf[k * TS_COLS + cg]);
           const float t[2] = {t2.x, t2.y};
           const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)k * ldf + j0));
           const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const float a = (j0 + u < r && k > j0 + u) ? rv[u] : 0.0f;
+            const float a = k > j0 + u ? rv[u] : 0.0f;
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
-              const float p = a * t[v];
-              const float pe = fmaf(a, t[v], -p);   // a t = p + pe exactly
-              df_add(hi[u][v], lo[u][v], -p);
-              lo[u][v] -= pe;
-            }
+            for (int v = 0; v < 2; ++v) residual_term(hi[u][v], lo[u][v], a, t[v]);
+          }
+        }
+        for (int k = kp; k < r; ++k) {
+          const float2 t2 = *reinterpret_cast<const float2*>(&Tf[k * TS_COLS + cg]);
+          const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)k * ldf + j0));
+          const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            residual_term(hi[u][0], lo[u][0], rv[u], t2.x);
+            residual_term(hi[u][1], lo[u][1], rv[u], t2.y);
           }
         }
 #pragma unroll
