@@ -223,10 +223,10 @@ ffc_status ffc_id(void* K_dev, int64_t s, int64_t n, int64_t ldk, int32_t precis
  * n <= FFC_NOALLOC_MAX_COLS, min(r_max, s, n) <= FFC_NOALLOC_MAX_RANK,
  * s <= 2048; larger problems return FFC_E_INVALID before anything is
  * enqueued. The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture. All calls share the one array and the next call
- * overwrites it: calls that overlap on the GPU (other streams, other host
- * threads on the same device) race. Synchronises `stream`.
+ * (once per device, with that device current). All calls share the one
+ * array and the next call overwrites it: calls that overlap on the GPU
+ * (other streams, other host threads on the same device) race. Synchronises
+ * `stream`.
  */
 #define FFC_NOALLOC_MAX_COLS 16384
 #define FFC_NOALLOC_MAX_RANK 256
