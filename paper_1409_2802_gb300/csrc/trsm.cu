@@ -183,6 +183,56 @@ __device__ __forceinline__ void residual_term(float& hi, float& lo, float a, flo
   lo -= pe;
 }
 
+// X[0:i0, :] -= R11[0:i0, i0:i0+nb] X[i0:i0+nb, :]: each thread a tile of RU rows x CV columns, one
+// CV-wide shared load of X and one RU-wide 16- or 8-byte load of a column of R11 per step. Every entry
+// takes the same FMAs in the same order whatever the tile shape. Only a row group reaching past i0 (the
+// rows of the diagonal block, read by the vector load) masks its R11 values.
+template <int RU, int CV>
+__device__ __forceinline__ void solve_update(float* X, const float* __restrict__ R11, int64_t ldf, int i0, int nb) {
+  constexpr int CG = TS_COLS / CV;
+  const int tid = threadIdx.x;
+  const int cg = CV * (tid % CG);
+  const int rstep = RU * (int)(blockDim.x / CG);
+  for (int j0 = RU * (tid / CG); j0 < i0; j0 += rstep) {
+    float acc[RU][CV];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < CV; ++v) acc[u][v] = j0 + u < i0 ? X[(j0 + u) * TS_COLS + cg + v] : 0.0f;
+    const bool full = j0 + RU <= i0;
+    for (int ii = 0; ii < nb; ++ii) {
+      float t[CV], rv[RU];
+      if constexpr (CV == 4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(&X[(i0 + ii) * TS_COLS + cg]);
+        t[0] = t4.x; t[1] = t4.y; t[2] = t4.z; t[3] = t4.w;
+      } else {
+        const float2 t2 = *reinterpret_cast<const float2*>(&X[(i0 + ii) * TS_COLS + cg]);
+        t[0] = t2.x; t[1] = t2.y;
+      }
+      if constexpr (RU == 4) {
+        const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11 + (int64_t)(i0 + ii) * ldf + j0));
+        rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+      } else {
+        const float2 r2 = __ldg(reinterpret_cast<const float2*>(R11 + (int64_t)(i0 + ii) * ldf + j0));
+        rv[0] = r2.x; rv[1] = r2.y;
+      }
+      if (!full) {
+#pragma unroll
+        for (int u = 0; u < RU; ++u) rv[u] = j0 + u < i0 ? rv[u] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < RU; ++u)
+#pragma unroll
+        for (int v = 0; v < CV; ++v) acc[u][v] = fmaf(-rv[u], t[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+      if (j0 + u < i0)
+#pragma unroll
+        for (int v = 0; v < CV; ++v) X[(j0 + u) * TS_COLS + cg + v] = acc[u][v];
+  }
+}
+
 // Blocked back-substitution of X (r x nc, shared memory, row stride TS_COLS) with the FP32 copy of R11
 // (column-major, leading dimension ldf = r rounded up to 4: exact off the diagonal, beta rounded on it);
 // Rd, dinv: shared scratch of the diagonal block.
@@ -210,38 +260,10 @@ __device__ void solve_f32_block(float* X, const float* __restrict__ R11, int r, 
       if (lane < nb) X[(i0 + lane) * TS_COLS + c] = t;
     }
     __syncthreads();
-    {
-      const int cg = 4 * (tid & 3);
-      for (int j0 = 4 * (tid >> 2); j0 < i0; j0 += 4 * (int)(blockDim.x >> 2)) {
-        float acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = j0 + u < i0 ? X[(j0 + u) * TS_COLS + cg + v] : 0.0f;
-        // rows j0 .. j0 + 3 of column i0 + ii: one 16-byte load; only a group that reaches past i0 (r not
-        // a multiple of 4) masks the rows of the diagonal block it reads
-        const bool full = j0 + 4 <= i0;
-        for (int ii = 0; ii < nb; ++ii) {
-          const float4 t4 = *reinterpret_cast<const float4*>(&X[(i0 + ii) * TS_COLS + cg]);
-          const float t[4] = {t4.x, t4.y, t4.z, t4.w};
-          const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11 + (int64_t)(i0 + ii) * ldf + j0));
-          float rv[4] = {r4.x, r4.y, r4.z, r4.w};
-          if (!full) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) rv[u] = j0 + u < i0 ? rv[u] : 0.0f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(-rv[u], t[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (j0 + u < i0)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) X[(j0 + u) * TS_COLS + cg + v] = acc[u][v];
-      }
-    }
+    // rows above the block, 16 i0 outputs: the thread's tile shrinks with i0 so that every thread has one
+    if (i0 >= (int)blockDim.x) solve_update<4, 4>(X, R11, ldf, i0, nb);
+    else if (2 * i0 >= (int)blockDim.x) solve_update<2, 4>(X, R11, ldf, i0, nb);
+    else solve_update<2, 2>(X, R11, ldf, i0, nb);
     __syncthreads();
     i1 = i0;
   }
@@ -314,9 +336,19 @@ trsm_refine_kernel(const TrsmItem* __restrict__ items, int n_items) {
             for (int v = 0; v < 2; ++v) residual_term(hi[u][v], lo[u][v], a, t[v]);
           }
         }
+        // the next step's loads are issued before this step's arithmetic (the last step reloads its own)
+        float4 rn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float2 tn = make_float2(0.0f, 0.0f);
+        if (kp < r) {
+          rn = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)kp * ldf + j0));
+          tn = *reinterpret_cast<const float2*>(&Tf[kp * TS_COLS + cg]);
+        }
         for (int k = kp; k < r; ++k) {
-          const float2 t2 = *reinterpret_cast<const float2*>(&Tf[k * TS_COLS + cg]);
-          const float4 r4 = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)k * ldf + j0));
+          const float4 r4 = rn;
+          const float2 t2 = tn;
+          const int kn = min(k + 1, r - 1);
+          rn = __ldg(reinterpret_cast<const float4*>(R11f + (int64_t)kn * ldf + j0));
+          tn = *reinterpret_cast<const float2*>(&Tf[kn * TS_COLS + cg]);
           const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
