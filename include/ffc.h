@@ -556,8 +556,8 @@ ffc_status ffc_mlp_forward(const float* params_dev, const float* feats_dev, int6
  * keys within a proven relative error of 2^-18 of the FP64 ones, and only
  * the rows that can be among the selection get their FP64 key, so the result
  * is the FP64 keys' selection. min(s, P) <= FFC_MAX_DRAW; any P.
- * rows_dev: capacity min(s, P). Allocates P + 256 words of stream-ordered
- * device memory for the call. Asynchronous.
+ * rows_dev: capacity min(s, P). Allocates 8 P + 256 bytes of stream-ordered
+ * device memory for the call (the draw's item and a key buffer). Asynchronous.
  */
 ffc_status ffc_sample_weighted(const int64_t* pool_dev, const float* logits_dev, int64_t P, int64_t s,
                                uint64_t seed, uint64_t stream_id, int64_t* rows_dev, void* stream);

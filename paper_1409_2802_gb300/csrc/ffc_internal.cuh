@@ -176,7 +176,7 @@ struct SelectItem {
   uint64_t stream_id;
   int64_t* rows_out;     // capacity s
   int64_t* s_out;        // device: rows written (may be NULL)
-  uint64_t* keys;        // capacity P: sort keys kept between passes, or NULL (recomputed)
+  uint64_t* keys;        // capacity P: w_i, then the FP32 pre-selection keys (pools above 16,384 rows), or NULL
   const uint64_t* given; // or: ascending sort keys per pool position, computed elsewhere (logits unused)
 };
 
